@@ -1,0 +1,55 @@
+"""Pins of the seeded input generators (no index arithmetic here)."""
+import numpy as np
+
+from paper_2601_05347_gb300 import gen
+
+
+def test_splitmix64_published_vectors():
+    # First outputs of SplitMix64 seeded with 1234567, as published with the
+    # reference implementation of Steele, Lea and Flood's generator.
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+            4593380528125082431, 16408922859458223821]
+    got = gen.splitmix64(1234567, np.arange(5, dtype=np.uint64))
+    assert [int(v) for v in got] == want
+
+
+def test_uniform_range_and_determinism():
+    a = gen.uniform(10000, 2, 30, 7)
+    b = gen.uniform(10000, 2, 30, 7)
+    assert a.dtype == np.int32 and a.shape == (10000, 2)
+    assert (a == b).all()
+    assert a.min() >= 0 and a.max() < (1 << 30)
+    # roughly uniform: each quarter of the x range gets about a quarter
+    q = np.bincount(a[:, 0] >> 28, minlength=4)
+    assert (abs(q - 2500) < 300).all()
+
+
+def test_varden_shape():
+    n = 200000
+    p = gen.varden(n, 2, 30, 3, clusters=100, x_range=(0, 1 << 29))
+    assert p.shape == (n, 2) and p.dtype == np.int32
+    assert p[:, 0].min() >= 0 and p[:, 0].max() < (1 << 29)
+    assert p[:, 1].min() >= 0 and p[:, 1].max() < (1 << 30)
+    # consecutive points of one walker are within one step unless a restart or a fold happened
+    dx = np.abs(np.diff(p[:, 0].astype(np.int64)))
+    assert np.mean(dx <= 1024) > 0.99
+    # clustered: a 2^20 grid is mostly empty
+    cells = np.unique((p[:, 0] >> 20).astype(np.int64) * 1024 + (p[:, 1] >> 20))
+    assert len(cells) < 0.2 * 512 * 1024
+    q = gen.varden(1000, 3, 21, 3)
+    assert q.max() < (1 << 21) and q.min() >= 0
+
+
+def test_sampling_without_replacement():
+    s = gen.sample_without_replacement(1000, 100, 5)
+    assert len(np.unique(s)) == 100 and s.min() >= 0 and s.max() < 1000
+    s = gen.sample_without_replacement(1000, 1000, 5)
+    assert sorted(s.tolist()) == list(range(1000))
+    s = gen.sample_without_replacement(10 ** 7, 1000, 9)
+    assert len(np.unique(s)) == 1000
+
+
+def test_boxes():
+    b = gen.square_boxes(100, 2, 30, 1000, 1)
+    assert (b[:, 2:] - b[:, :2] == 999).all()
+    assert b.min() >= 0 and b.max() < (1 << 30)
