@@ -1,0 +1,438 @@
+"""Benchmark of the GB300 spatial-index hot path.
+
+One step = one pass of the whole path over one batch of synthetic input, on
+the 2D clustered workload (Varden-style random walks, n = 1e8 int32 points in
+[0, 2^30), SPaC-H tree, leaf size 32):
+    build (1e8 points) -> insert 1e6 in-distribution points -> delete 1e6 live
+    points -> 1e7 10-NN queries at data points -> 5e4 range lists (boxes
+    holding about 1e3 points) -> 5e4 range counts on the same boxes.
+Inputs are resident in HBM before the timed region and larger than L2.
+
+Prints one JSON line.  ``value`` is the build throughput (Mpts/s, whole job);
+every phase's throughput is under ``phases``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--small]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2601_05347_gb300 import gen  # noqa: E402
+
+METRIC = "build/update Mpts/s, kNN & range queries/s at 1e8 2D pts; served p50/p99 latency"
+BITS = 30
+
+
+def workload(small: bool):
+    if small:
+        return dict(name="2D clustered (Varden), n=1e6, SPaC-H", n=1_000_000, m_ins=10_000, m_del=10_000,
+                    n_knn=100_000, k=10, n_box=5_000, box_target=1000)
+    return dict(name="2D clustered (Varden), n=1e8, SPaC-H", n=100_000_000, m_ins=1_000_000, m_del=1_000_000,
+                n_knn=10_000_000, k=10, n_box=50_000, box_target=1000)
+
+
+def make_inputs(w, rank: int):
+    """Seeded host arrays of one step (identical every step)."""
+    cfg = 1  # workload index of the 2D clustered configuration
+    half = 1 << (BITS - 1)
+    n = w["n"]
+    pts = gen.varden(n, 2, BITS, gen.config_seed(cfg, 0, rank), x_range=(0, half))
+    ids = np.arange(n, dtype=np.uint32)
+    ins = gen.varden(w["m_ins"], 2, BITS, gen.config_seed(cfg, 1, rank), x_range=(0, half))
+    ins_ids = np.arange(n, n + w["m_ins"], dtype=np.uint32)
+    dsel = gen.sample_without_replacement(n, w["m_del"], gen.config_seed(cfg, 2, rank))
+    qsel = gen.sample_with_replacement(n, w["n_knn"], gen.config_seed(cfg, 3, rank))
+    q = pts[qsel]
+    h = gen.half_side_for_count(pts, w["box_target"], gen.config_seed(cfg, 4, rank))
+    csel = gen.sample_with_replacement(n, w["n_box"], gen.config_seed(cfg, 5, rank))
+    boxes = gen.centred_boxes(pts[csel], h, BITS)
+    return dict(pts=pts, ids=ids, ins=ins, ins_ids=ins_ids, del_pts=pts[dsel], del_ids=ids[dsel], q=q, boxes=boxes,
+                half_side=h)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# per-kernel algorithmic byte model (2D, per launch)
+# ---------------------------------------------------------------------------
+def kernel_bytes(name: str, w, launches: int) -> float | None:
+    """Algorithmic HBM bytes of all launches of a kernel in one step.
+
+    k_onesweep   one digit pass over (key 8 B, value 4 B): read + write 24 B per
+                 pair; the first pass of an encoding sort reads the 8-B point
+                 instead of the key and value (20 B).
+    k_sort_hist  reads each key (or 8-B point) once: 8 B per item.
+    k_leaf_gather reads sorted key + position (12 B) and gathers point + id
+                 (12 B), writes x, y, id, key (20 B): 44 B per point.
+    """
+    n, mi, md = w["n"], w["m_ins"], w["m_del"]
+    if name == "k_onesweep":
+        # sorts per step: build (n), insert batch (mi), delete batch (md), query order (n_knn); 8 passes each
+        items = [n, mi, md, w["n_knn"]]
+        per_sort = [20 + 7 * 24 for _ in items]
+        return float(sum(i * b for i, b in zip(items, per_sort)))
+    if name == "k_sort_hist":
+        return float(8 * (n + mi + md + w["n_knn"]))
+    if name == "k_leaf_gather":
+        return float(44 * n)
+    return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_05347_gb300 import psi
+
+    w = workload(args.small)
+    t0 = time.time()
+    host = make_inputs(w, rank)
+    gen_s = time.time() - t0
+
+    def T(a):
+        a = np.ascontiguousarray(a)
+        if a.dtype == np.uint32:
+            a = a.view(np.int32)
+        return torch.from_numpy(a).to(dev)
+
+    d = {k: T(v) for k, v in host.items() if isinstance(v, np.ndarray)}
+    n = w["n"]
+    k = w["k"]
+    out_ids = torch.empty((w["n_knn"], k), dtype=torch.int32, device=dev)
+    out_d2 = torch.empty((w["n_knn"], k), dtype=torch.int64, device=dev)
+    counts = torch.empty(w["n_box"], dtype=torch.int64, device=dev)
+    ndel = torch.zeros(1, dtype=torch.int64, device=dev)
+    report_cap = w["n_box"] * w["box_target"] * 8
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        ix = psi.Index(d["pts"], d["ids"], kind="spac_h", leaf_size=32)
+        mark(1)
+        ix.insert(d["ins"], d["ins_ids"])
+        mark(2)
+        ix.delete(d["del_pts"], d["del_ids"], ndel)
+        mark(3)
+        ix.knn(d["q"], k, out_ids, out_d2)
+        mark(4)
+        off, rid = ix.range_report(d["boxes"], capacity=report_cap)
+        mark(5)
+        ix.range_count(d["boxes"], counts)
+        mark(6)
+        ix.close()
+        return int(rid.shape[0])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ix_chk = psi.Index(d["pts"], d["ids"], kind="spac_h", leaf_size=32)
+    ix_chk.sync()
+    ix_chk.close()
+
+    phases = ["build", "insert", "delete", "knn", "range_report", "range_count"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    psi.profile_enable(True)
+    psi.profile_reset()
+    launches0 = psi.launch_count()
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    total_reported = 0
+    for s in range(args.steps):
+        total_reported += step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = psi.launch_count() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    prof = psi.profile_dump()
+    psi.profile_enable(False)
+    phase_ms = {p: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, p in enumerate(phases)}
+
+    if world > 1:
+        t = torch.tensor([total_ms] + [phase_ms[p] for p in phases], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t[0])
+        phase_ms = {p: float(t[i + 1]) for i, p in enumerate(phases)}
+
+    # e2e: the build metric through the public API from pinned host buffers,
+    # H2D of the step's build inputs and D2H of a result inside the timed region
+    pin_pts = torch.from_numpy(host["pts"]).pin_memory()
+    pin_ids = torch.from_numpy(host["ids"].view(np.int32)).pin_memory()
+    dev_pts = torch.empty_like(d["pts"])
+    dev_ids = torch.empty_like(d["ids"])
+    e2e_ms = []
+    for it in range(args.steps + 1):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        dev_pts.copy_(pin_pts, non_blocking=True)
+        dev_ids.copy_(pin_ids, non_blocking=True)
+        ix = psi.Index(dev_pts, dev_ids, kind="spac_h", leaf_size=32)
+        leaves = ix.leaves()["count"][:1].cpu()
+        torch.cuda.synchronize()
+        if it:
+            e2e_ms.append((time.perf_counter() - a) * 1e3)
+        ix.close()
+        del leaves
+    e2e_build = statistics.mean(e2e_ms)
+
+    # roofline of the dominant kernel (largest share of the timed steps)
+    total_prof = sum(v[1] for v in prof.values()) or 1.0
+    ranked = sorted(prof.items(), key=lambda kv: -kv[1][1])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    roof = None
+    for name, (cnt, ms) in ranked:
+        b = kernel_bytes(name, w, cnt // max(args.steps, 1))
+        if b is None:
+            continue
+        per_step_ms = ms / args.steps
+        ach = b / (per_step_ms * 1e-3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
+                "share_of_step": round(ms / total_prof, 4), "launches_per_step": cnt // max(args.steps, 1),
+                "algorithmic_bytes_per_step": b}
+        break
+    top = [{"kernel": nm, "launches": c, "ms_per_step": round(m / args.steps, 4), "share": round(m / total_prof, 4)}
+           for nm, (c, m) in ranked[:12]]
+
+    ms_step = total_ms / args.steps
+    build_ms = phase_ms["build"]
+    value = world * n / (build_ms * 1e-3) / 1e6
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "Mpts/s (build)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int64",
+        "data": "synthetic (seeded Varden-style random walks, SplitMix64)",
+        "config": {"workload": w["name"], "n": n, "dim": 2, "coord_bits": BITS, "leaf_size": 32, "k": k,
+                   "insert": w["m_ins"], "delete": w["m_del"], "knn_queries": w["n_knn"],
+                   "range_boxes": w["n_box"], "box_half_side": host["half_side"],
+                   "l2": "inputs larger than L2 (800 MB of points per step)", "parallelism": f"replicas x{world}"},
+        "phases": {
+            "build": {"ms": round(build_ms, 3), "value": round(n / build_ms / 1e3, 2), "unit": "Mpts/s"},
+            "insert": {"ms": round(phase_ms["insert"], 3), "value": round(w["m_ins"] / phase_ms["insert"] / 1e3, 2),
+                       "unit": "Mpts/s"},
+            "delete": {"ms": round(phase_ms["delete"], 3), "value": round(w["m_del"] / phase_ms["delete"] / 1e3, 2),
+                       "unit": "Mpts/s"},
+            "knn": {"ms": round(phase_ms["knn"], 3), "value": round(w["n_knn"] / phase_ms["knn"] * 1e3, 1),
+                    "unit": "queries/s"},
+            "range_report": {"ms": round(phase_ms["range_report"], 3),
+                             "value": round(w["n_box"] / phase_ms["range_report"] * 1e3, 1), "unit": "queries/s",
+                             "reported_per_query": round(total_reported / args.steps / w["n_box"], 1)},
+            "range_count": {"ms": round(phase_ms["range_count"], 3),
+                            "value": round(w["n_box"] / phase_ms["range_count"] * 1e3, 1), "unit": "queries/s"},
+        },
+        "e2e": {"value": round(world * n / (e2e_build * 1e-3) / 1e6, 2), "unit": "Mpts/s (build)",
+                "h2d_bytes_per_step": int(host["pts"].nbytes + host["ids"].nbytes), "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernels": top,
+        "clocks": clk,
+        "input_generation_s": round(gen_s, 1),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, host, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# oracle timings (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_step(w, host, frac: float):
+    """Times the oracle on a bounded sample of the step's workload."""
+    from oracle import oracle as O
+    n = max(1000, int(w["n"] * frac))
+    pts = host["pts"][:n]
+    ids = host["ids"][:n]
+    mi = max(10, int(w["m_ins"] * frac))
+    md = max(10, int(w["m_del"] * frac))
+    nq = max(100, int(w["n_knn"] * frac))
+    nb = max(50, int(w["n_box"] * frac))
+    dsel = gen.sample_without_replacement(n, md, 17)
+    t = {}
+    a = time.perf_counter()
+    ix = O.Index(pts, ids, kind=O.SPAC_H, phi=32)
+    t["build"] = time.perf_counter() - a
+    a = time.perf_counter()
+    ix.insert(host["ins"][:mi], host["ins_ids"][:mi])
+    t["insert"] = time.perf_counter() - a
+    a = time.perf_counter()
+    ix.delete(pts[dsel], ids[dsel])
+    t["delete"] = time.perf_counter() - a
+    q = pts[gen.sample_with_replacement(n, nq, 18)]
+    a = time.perf_counter()
+    ix.knn(q, w["k"])
+    t["knn"] = time.perf_counter() - a
+    # boxes sized for ~box_target points in the sample (same shape, scaled)
+    side = int(host["half_side"] * np.sqrt(w["n"] / n))
+    boxes = gen.centred_boxes(pts[gen.sample_with_replacement(n, nb, 19)], side, BITS)
+    a = time.perf_counter()
+    ix.range_report(boxes)
+    t["range_report"] = time.perf_counter() - a
+    a = time.perf_counter()
+    ix.range_count(boxes)
+    t["range_count"] = time.perf_counter() - a
+    sizes = dict(build=n, insert=mi, delete=md, knn=nq, range_report=nb, range_count=nb)
+    return t, sizes
+
+
+def cpu_baseline(w, host, budget_s: float = 20.0):
+    frac = 0.02 if w["n"] >= 10_000_000 else 1.0
+    t, sizes = oracle_sample_step(w, host, frac)
+    phases = {p: {"value": round(sizes[p] / t[p] / (1e6 if p in ("build", "insert", "delete") else 1), 2),
+                  "unit": "Mpts/s" if p in ("build", "insert", "delete") else "queries/s", "sample": sizes[p]}
+              for p in t}
+    return {"value": phases["build"]["value"], "unit": "Mpts/s (build)", "cores": 1, "kind": "oracle",
+            "sample": f"{frac:.0%} of every phase of the step (build of the first {sizes['build']} points), "
+                      f"single-threaded sequential C oracle", "seconds": round(sum(t.values()), 1),
+            "phases": phases}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.small)
+    host = make_inputs(w, 0)
+    frac = 0.01 if w["n"] >= 10_000_000 else 0.5
+    for _ in range(args.warmup):
+        oracle_sample_step(w, host, frac / 4)
+    times = []
+    sizes = None
+    for _ in range(args.steps):
+        t, sizes = oracle_sample_step(w, host, frac)
+        times.append(t)
+    build_s = statistics.mean(t["build"] for t in times)
+    value = sizes["build"] / build_s / 1e6
+    step_s = statistics.mean(sum(t.values()) for t in times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpts/s (build)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded Varden-style random walks, SplitMix64)",
+        "config": {"workload": w["name"], "sample_fraction": frac},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mpts/s (build)", "cores": 1, "kind": "oracle",
+                         "sample": f"{frac:.0%} of every phase of the step, single-threaded sequential C oracle"},
+        "e2e": {"value": round(value, 3), "unit": "Mpts/s (build)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--small", action="store_true", help="1e6-point workload (quick check)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

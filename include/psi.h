@@ -1,0 +1,186 @@
+/*
+ * psi.h -- C ABI of the GB300 (sm_103a) spatial-index library.
+ *
+ * The library builds and maintains the two index families of "Parallel Dynamic
+ * Spatial Indexes" (PPoPP '26, arXiv 2601.05347) on one GPU:
+ *   - SPaC-Z / SPaC-H (Sec 4): points ordered by a Morton (Z) or Hilbert key,
+ *     wrapped into leaves of at most `leaf_size` points, with bounding boxes and
+ *     counts summarised bottom-up;
+ *   - P-Orth (Sec 3): the orth-tree (quadtree/octree) that splits a region at its
+ *     midpoint in every dimension until a node holds at most `leaf_size` points.
+ * and answers the queries of Sec 2.2 on them: k-nearest neighbours, range count
+ * and range list ("report").
+ *
+ * Conventions shared by every call:
+ *   - Coordinates are int32 in [0, 2^coord_bits); points are AoS, `dim` int32
+ *     per point ([n][dim]).  Ids are uint32 chosen by the caller and must be
+ *     unique among the live points of an index (not checked).
+ *   - Every pointer argument named d_* is DEVICE memory owned by the caller.
+ *     The library reads inputs and writes outputs only in stream order on the
+ *     given stream; it keeps no reference to them after the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous unless stated otherwise.
+ *   - The library owns the index memory (stream-ordered allocations on the
+ *     current device); psi_destroy releases it.
+ *   - Errors: every call returns a psi_status; psi_last_error() gives a message
+ *     for the calling thread.  Errors detected on the device (a coordinate out
+ *     of range, a bounded wait that timed out) are recorded in the index and
+ *     returned by the next psi_sync() (and by synchronising calls).
+ *   - Squared distances are exact int64; k-NN ties are broken by smaller id.
+ *     Range boxes are closed ([lo, hi] in every dimension); a box with
+ *     lo > hi in some dimension is empty.
+ */
+#ifndef PSI_H
+#define PSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PSI_OK = 0,
+  PSI_ERR_INVALID = 1,        /* bad argument: null pointer, n < 0, k < 1, unsupported config */
+  PSI_ERR_RANGE = 2,          /* a coordinate outside [0, 2^coord_bits) (device-detected) */
+  PSI_ERR_OOM = 3,            /* a device allocation failed */
+  PSI_ERR_CAPACITY = 4,       /* psi_range_report: output capacity too small */
+  PSI_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up */
+  PSI_ERR_CUDA = 6            /* any other CUDA error */
+} psi_status;
+
+typedef enum {
+  PSI_SPAC_Z = 0, /* SPaC-tree on the Morton (Z) curve, Sec 4 */
+  PSI_SPAC_H = 1, /* SPaC-tree on the Hilbert curve (2D), Sec 4 */
+  PSI_PORTH = 2   /* P-Orth tree, Sec 3 */
+} psi_kind;
+
+typedef struct {
+  int32_t dim;        /* 2 or 3 */
+  int32_t kind;       /* psi_kind */
+  int32_t leaf_size;  /* leaf wrap phi, 1..64 (Table 1 "leaf wrap"; the paper uses 32-40) */
+  int32_t coord_bits; /* b: 1..31 in 2D, 1..21 in 3D; keys have dim*b bits */
+  int32_t fanout;     /* fanout of the SPaC summary tree over the leaves, 2..32 (0 = 32) */
+  int32_t radix_bits; /* digit width of the key sort: 8 (0 = 8) */
+} psi_config;
+
+typedef struct psi_index psi_index;
+
+/* Batch construction.  SPaC (Algorithm 3): each point's curve key is computed
+ * on first touch inside the key sort, (key, id) pairs are sorted (ties in key by
+ * id), and the sorted sequence is cut into leaves of exactly leaf_size points
+ * (the last may be shorter) with their boxes, counts and first (key, id); a
+ * summary tree of the given fanout is built over the leaves.  P-Orth
+ * (Algorithm 1): the same key sort on Morton keys, then the orth-tree whose
+ * nodes split by key bits.  d_pts is [n][dim], d_ids is [n]; n may be 0.
+ * On success *out receives a new index. */
+psi_status psi_build(const psi_config *cfg, const int32_t *d_pts, const uint32_t *d_ids, int64_t n,
+                     void *stream, psi_index **out);
+
+/* Batch insertion (SPaC: Algorithm 4; P-Orth: Algorithm 2).  The batch is
+ * key-sorted and each point is routed to the leaf whose key range holds it.
+ * SPaC: a leaf whose points fit its block (2*leaf_size slots) takes them
+ * unsorted; an overflowing leaf is merged with its slice and re-wrapped into
+ * leaves of at most leaf_size.  P-Orth: a leaf that exceeds leaf_size is split
+ * by the next key bits, so the tree equals a fresh build of the same points.
+ * Synchronises `stream` once to size the new leaf list. */
+psi_status psi_insert_batch(psi_index *ix, const int32_t *d_pts, const uint32_t *d_ids, int64_t m,
+                            void *stream);
+
+/* Batch deletion (Sec 4.2 deletion paragraph; Sec 3.2).  Removes every live
+ * point whose coordinates AND id equal a batch entry; absent entries are
+ * ignored.  d_num_deleted (device int64, may be NULL) receives the number of
+ * points removed.  Empty leaves are dropped; P-Orth subtrees left with at most
+ * leaf_size points are flattened into one leaf.  Synchronises `stream` once. */
+psi_status psi_delete_batch(psi_index *ix, const int32_t *d_pts, const uint32_t *d_ids, int64_t m,
+                            int64_t *d_num_deleted, void *stream);
+
+/* k-nearest neighbours (Sec 2.2).  For each of the q query points d_q[q][dim]
+ * writes the min(k, size) live points smallest in (squared distance, id),
+ * ascending, to d_ids[q][k] and d_d2[q][k]; slots past the index size get
+ * id 0xFFFFFFFF and d2 INT64_MAX.  1 <= k <= 128. */
+psi_status psi_knn(const psi_index *ix, const int32_t *d_q, int64_t q, int32_t k, uint32_t *d_ids,
+                   int64_t *d_d2, void *stream);
+
+/* Range count (Sec 2.2).  d_boxes is [q][2][dim] (lo corner, then hi corner);
+ * d_counts[q] receives the number of live points inside each closed box. */
+psi_status psi_range_count(const psi_index *ix, const int32_t *d_boxes, int64_t q, int64_t *d_counts,
+                           void *stream);
+
+#define PSI_REPORT_SORTED 1 /* sort each query's ids ascending */
+
+/* Range list (Sec 2.2).  Writes d_offsets[q+1] (exclusive prefix of the
+ * per-query counts) and, if the total fits in `capacity`, the ids of the
+ * points inside each box to d_ids[offsets[i] .. offsets[i+1]).  Order within a
+ * query is unspecified unless flags has PSI_REPORT_SORTED.  Synchronises
+ * `stream`; *h_total (host) receives the total.  Returns PSI_ERR_CAPACITY
+ * (offsets written, ids not) if total > capacity. */
+psi_status psi_range_report(const psi_index *ix, const int32_t *d_boxes, int64_t q, int64_t *d_offsets,
+                            uint32_t *d_ids, int64_t capacity, int64_t *h_total, int32_t flags,
+                            void *stream);
+
+/* Waits for the index's outstanding work on `stream` and returns any
+ * device-detected error (PSI_ERR_RANGE, PSI_ERR_DEVICE_TIMEOUT), clearing it. */
+psi_status psi_sync(psi_index *ix, void *stream);
+
+/* Releases the index (synchronises the device first). */
+psi_status psi_destroy(psi_index *ix);
+
+/* Number of live points (host-side; exact after every call returns). */
+int64_t psi_size(const psi_index *ix);
+
+/* Number of leaves and of tree nodes (leaves included). */
+int64_t psi_num_leaves(const psi_index *ix);
+int64_t psi_num_nodes(const psi_index *ix);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *psi_last_error(void);
+
+/* ---- Inspection (tests, tools) --------------------------------------- */
+
+/* Leaves in key order: counts[L], lo[L][dim], hi[L][dim], first key and first
+ * id of each leaf's key range (for a freshly built SPaC tree: of its first
+ * point).  Any pointer may be NULL.  Device pointers; asynchronous. */
+psi_status psi_export_leaves(const psi_index *ix, int32_t *d_counts, int32_t *d_lo, int32_t *d_hi,
+                             uint64_t *d_sep_key, uint32_t *d_sep_id, void *stream);
+
+/* All live points, leaf by leaf in key order (within a leaf: storage order):
+ * d_pts[n][dim], d_ids[n], d_keys[n], d_leaf[n] (leaf number).  Any may be NULL. */
+psi_status psi_export_points(const psi_index *ix, int32_t *d_pts, uint32_t *d_ids, uint64_t *d_keys,
+                             int32_t *d_leaf, void *stream);
+
+/* Tree nodes in preorder: depth (P-Orth: cell depth; SPaC: height above the
+ * root), P-Orth cell prefix (SPaC: 0), subtree count, box, is_leaf.  Arrays of
+ * psi_num_nodes() entries; any may be NULL. */
+psi_status psi_export_nodes(const psi_index *ix, int32_t *d_depth, uint64_t *d_prefix, int64_t *d_count,
+                            int32_t *d_lo, int32_t *d_hi, int32_t *d_is_leaf, void *stream);
+
+/* Curve keys of n points under cfg (Morton for SPAC_Z/PORTH, Hilbert for
+ * SPAC_H), as used by the index.  Out-of-range coordinates are reported by the
+ * returned status after the call synchronises `stream`. */
+psi_status psi_encode(const psi_config *cfg, const int32_t *d_pts, int64_t n, uint64_t *d_keys, void *stream);
+
+/* Sorts n (key, value) pairs ascending by key with the library's onesweep LSD
+ * radix sort (stable: equal keys keep their input order).  key_bits limits the
+ * digits sorted (1..64).  In-place on the caller's arrays; uses library scratch. */
+psi_status psi_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bits, void *stream);
+
+/* ---- Instrumentation ---------------------------------------------------- */
+
+/* Number of kernels this library has launched in the process. */
+int64_t psi_launch_count(void);
+
+/* When on, every launch of a library kernel is bracketed by CUDA events on its
+ * stream; psi_profile_read() synchronises and reports, for the kernel named
+ * `name`, the number of launches and their summed duration since the last
+ * psi_profile_reset().  Names are those in the ncu launch list. */
+void psi_profile_enable(int on);
+void psi_profile_reset(void);
+int psi_profile_read(const char *name, int64_t *launches, double *total_ms);
+/* Writes "name launches total_ms\n" lines for every kernel seen into buf. */
+int psi_profile_dump(char *buf, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSI_H */

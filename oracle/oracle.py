@@ -72,6 +72,8 @@ def lib():
             f.argtypes = [P, P, i64, P]
         L.or_range_report.restype = i64
         L.or_range_report.argtypes = [P, P, i64, P, P, i64]
+        L.or_knn_brute_raw.argtypes = [P, P, i64, ctypes.c_int, P, i64, ctypes.c_int, P, P]
+        L.or_range_count_brute_raw.argtypes = [P, i64, ctypes.c_int, P, i64, P]
         L.or_porth.restype = i64
         L.or_porth.argtypes = [P, i64, P, P, P, P, P, P]
         _lib = L
@@ -101,6 +103,27 @@ def keys(pts, dim: int, kind: int, bits: int) -> np.ndarray:
     cfg = _Cfg(dim, kind, 32, bits, 32)
     if lib().or_keys(ctypes.byref(cfg), _ptr(pts), len(pts), _ptr(out)) != 0:
         raise ValueError("coordinate outside [0, 2^bits)")
+    return out
+
+
+def knn_brute_raw(pts, ids, q, k):
+    """k-NN by definition over raw arrays (no index)."""
+    pts = _c(pts, np.int32)
+    dim = pts.shape[1]
+    ids = _c(ids, np.uint32)
+    q = _c(q, np.int32).reshape(-1, dim)
+    oi = np.empty((len(q), k), np.uint32)
+    od = np.empty((len(q), k), np.int64)
+    lib().or_knn_brute_raw(_ptr(pts), _ptr(ids), len(pts), dim, _ptr(q), len(q), k, _ptr(oi), _ptr(od))
+    return oi, od
+
+
+def range_count_brute_raw(pts, boxes):
+    pts = _c(pts, np.int32)
+    dim = pts.shape[1]
+    boxes = _c(boxes, np.int32).reshape(-1, 2 * dim)
+    out = np.empty(len(boxes), np.int64)
+    lib().or_range_count_brute_raw(_ptr(pts), len(pts), dim, _ptr(boxes), len(boxes), _ptr(out))
     return out
 
 

@@ -692,3 +692,33 @@ int64_t or_porth(const or_index *ix, int64_t cap, int32_t *depth, uint64_t *pref
   free(C.tmp);
   return C.n;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Definitions over raw point arrays (for sampled checks at full size)        */
+/* ------------------------------------------------------------------------- */
+
+/* k-NN by definition over n points pts[n][dim] with ids[n]. */
+void or_knn_brute_raw(const int32_t *pts, const uint32_t *ids, int64_t n, int dim, const int32_t *q, int64_t nq,
+                      int k, uint32_t *out_ids, int64_t *out_d2) {
+  topk h;
+  h.a = (cand *)malloc(sizeof(cand) * (k > 0 ? k : 1));
+  h.k = k;
+  for (int64_t t = 0; t < nq; ++t) {
+    h.n = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      cand c = {sqdist(q + t * dim, pts + j * dim, dim), ids[j]};
+      topk_push(&h, c);
+    }
+    topk_emit(&h, out_ids + t * (int64_t)k, out_d2 + t * (int64_t)k);
+  }
+  free(h.a);
+}
+
+/* Range count by definition over raw points. */
+void or_range_count_brute_raw(const int32_t *pts, int64_t n, int dim, const int32_t *boxes, int64_t nq,
+                              int64_t *counts) {
+  for (int64_t t = 0; t < nq; ++t) {
+    counts[t] = 0;
+    for (int64_t j = 0; j < n; ++j) counts[t] += pt_in_box(pts + j * dim, boxes + t * 2 * dim, dim);
+  }
+}

@@ -70,6 +70,12 @@ int64_t or_range_report(const or_index *ix, const int32_t *boxes, int64_t nq, in
 int64_t or_porth(const or_index *ix, int64_t cap, int32_t *depth, uint64_t *prefix, int64_t *count,
                  int32_t *lo, int32_t *hi, int32_t *is_leaf);
 
+/* Definitions over raw arrays (no index): k-NN and range count. */
+void or_knn_brute_raw(const int32_t *pts, const uint32_t *ids, int64_t n, int dim, const int32_t *q, int64_t nq,
+                      int k, uint32_t *out_ids, int64_t *out_d2);
+void or_range_count_brute_raw(const int32_t *pts, int64_t n, int dim, const int32_t *boxes, int64_t nq,
+                              int64_t *counts);
+
 #ifdef __cplusplus
 }
 #endif

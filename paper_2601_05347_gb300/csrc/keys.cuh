@@ -1,0 +1,101 @@
+// keys.cuh -- space-filling-curve keys on the device (Sec 2.2).
+//
+// Morton (Z) keys: bit i of coordinate d goes to key bit dim*i + d.  The bits
+// are spread with the usual shift-and-mask ladder (each step doubles the gap
+// between the groups of bits that are still together).
+//
+// Hilbert keys (2D): a four-state automaton read top level first.  The state
+// is the symmetry that maps the current sub-square onto the canonical curve:
+// bit 0 = the axes are exchanged, bit 1 = both axes are reversed.  At each
+// level the quadrant bits (rx, ry) of the point are mapped through the state,
+// the canonical quadrant (cx, cy) gives the base-4 digit
+// (0,0)->0, (0,1)->1, (1,1)->2, (1,0)->3, and the sub-curve of that quadrant
+// composes its own symmetry into the state: digit 0 exchanges the axes,
+// digit 3 exchanges and reverses them, digits 1 and 2 leave the state alone.
+// The four symmetries form a Klein four-group, so composition is XOR of the
+// two state bits.  Three levels are consumed per step through a 256-entry
+// table (state, 3 x-bits, 3 y-bits) -> (6 key bits, next state) that every
+// thread block derives from the automaton into shared memory.
+#pragma once
+#include <stdint.h>
+
+namespace psi {
+
+__device__ __forceinline__ uint64_t spread_bits2(uint32_t v) {
+  uint64_t x = v;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t spread_bits3(uint32_t v) {
+  uint64_t x = v & 0x1FFFFFu;
+  x = (x | (x << 32)) & 0x001F00000000FFFFull;
+  x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+  x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+  x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t morton2_key(uint32_t x, uint32_t y) {
+  return spread_bits2(x) | (spread_bits2(y) << 1);
+}
+
+__device__ __forceinline__ uint64_t morton3_key(uint32_t x, uint32_t y, uint32_t z) {
+  return spread_bits3(x) | (spread_bits3(y) << 1) | (spread_bits3(z) << 2);
+}
+
+// One level of the Hilbert automaton: returns the digit, updates the state.
+__device__ __forceinline__ uint32_t hilbert_step(uint32_t &state, uint32_t rx, uint32_t ry) {
+  uint32_t cx = (state & 1) ? ry : rx;
+  uint32_t cy = (state & 1) ? rx : ry;
+  if (state & 2) {
+    cx ^= 1u;
+    cy ^= 1u;
+  }
+  uint32_t digit = (cx << 1) | (cx ^ cy);
+  state ^= (digit == 0) ? 1u : (digit == 3 ? 3u : 0u);
+  return digit;
+}
+
+// Fills the 256-entry three-level table; call with all threads, then sync.
+__device__ __forceinline__ void hilbert_table_init(uint8_t *tab) {
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    uint32_t st = (uint32_t)e >> 6, xb = ((uint32_t)e >> 3) & 7u, yb = (uint32_t)e & 7u, d = 0;
+    for (int l = 2; l >= 0; --l) d = (d << 2) | hilbert_step(st, (xb >> l) & 1u, (yb >> l) & 1u);
+    tab[e] = (uint8_t)((d << 2) | st);
+  }
+}
+
+__device__ __forceinline__ uint64_t hilbert2_key(const uint8_t *tab, uint32_t x, uint32_t y, int bits) {
+  uint32_t st = 0;
+  uint64_t d = 0;
+  int l = bits - 1;
+  for (; l >= 0 && ((l + 1) % 3) != 0; --l) d = (d << 2) | hilbert_step(st, (x >> l) & 1u, (y >> l) & 1u);
+  for (; l >= 2; l -= 3) {
+    uint32_t e = tab[(st << 6) | (((x >> (l - 2)) & 7u) << 3) | ((y >> (l - 2)) & 7u)];
+    d = (d << 6) | (e >> 2);
+    st = e & 3u;
+  }
+  return d;
+}
+
+// Key of point p (dim coordinates) under the encode spec; sets *bad if a
+// coordinate lies outside [0, 2^bits).
+template <int D, int CURVE>
+__device__ __forceinline__ uint64_t point_key(const uint8_t *htab, const int32_t *c, int bits, bool &bad) {
+  uint32_t lim = 1u << bits;  // bits <= 31
+  bool b = false;
+#pragma unroll
+  for (int d = 0; d < D; ++d) b |= (uint32_t)c[d] >= lim;
+  bad = b;
+  if (CURVE == 1) return hilbert2_key(htab, (uint32_t)c[0], (uint32_t)c[1], bits);
+  if (D == 2) return morton2_key((uint32_t)c[0], (uint32_t)c[1]);
+  return morton3_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2]);
+}
+
+}  // namespace psi

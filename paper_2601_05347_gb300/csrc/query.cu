@@ -1,0 +1,467 @@
+// query.cu -- batched k-NN, range count and range list (Sec 2.2) on either
+// tree layout (SPaC summary tree or P-Orth), one warp per query.
+//
+// k-NN: depth-first traversal that visits children in increasing order of
+// their box distance (Appendix "Implementation Details": subtrees are visited
+// in increasing minimum distance to the query) and prunes a subtree whose box
+// is farther than the current k-th best.  The k best (d2, id) pairs are kept
+// sorted across the warp: entry e = r*32 + lane lives in register r of lane
+// `lane`; a candidate is inserted by one ballot per register and one shuffle
+// shift.  Squared distances are exact int64 (|dx| < 2^31 for coordinates in
+// [0, 2^31)).  A node's children are evaluated one per lane and ordered with a
+// warp bitonic sort before they are pushed on the warp's shared-memory stack.
+//
+// Range count: children inside the box add their subtree count; children that
+// straddle the box are descended; straddling leaves are scanned.
+// Range list: the same traversal counts first; after an exclusive scan of the
+// counts a second traversal writes each query's ids at its offset (a
+// subtree inside the box is enumerated without further box tests).
+#include "bitonic.cuh"
+#include "index.cuh"
+#include "keys.cuh"
+
+namespace psi {
+namespace {
+
+constexpr int QW = 4;         // warps per block
+constexpr int STACK = 256;    // stack entries per warp (>= depth * fanout)
+constexpr uint32_t INSIDE = 0x80000000u;
+
+template <int D>
+__device__ __forceinline__ int64_t box_mindist(const TreeView &t, uint32_t node, const int32_t *qc) {
+  int64_t s = 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int64_t lo = t.lo[d][node], hi = t.hi[d][node], q = qc[d];
+    const int64_t dd = q < lo ? lo - q : (q > hi ? q - hi : 0);
+    s += dd * dd;
+  }
+  return s;
+}
+
+// 0: disjoint, 1: straddles, 2: node box inside the query box.
+template <int D>
+__device__ __forceinline__ int box_relation(const TreeView &t, uint32_t node, const int32_t *blo, const int32_t *bhi) {
+  bool inside = true, disjoint = false;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int32_t lo = t.lo[d][node], hi = t.hi[d][node];
+    disjoint |= hi < blo[d] || lo > bhi[d];
+    inside &= blo[d] <= lo && hi <= bhi[d];
+  }
+  return disjoint ? 0 : (inside ? 2 : 1);
+}
+
+__device__ __forceinline__ bool pair_less(int64_t da, uint32_t ia, int64_t db, uint32_t ib) {
+  return da < db || (da == db && ia < ib);
+}
+
+// Ascending warp sort of (key, val) pairs, one per lane.
+__device__ __forceinline__ void warp_sort_asc(int64_t &key, uint32_t &val) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int64_t ok = __shfl_xor_sync(0xFFFFFFFFu, key, j);
+      const uint32_t ov = __shfl_xor_sync(0xFFFFFFFFu, val, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take = (lower == up) ? pair_less(ok, ov, key, val) : pair_less(key, val, ok, ov);
+      if (take) {
+        key = ok;
+        val = ov;
+      }
+    }
+  }
+}
+
+struct KnnArgs {
+  TreeView t;
+  const int32_t *q;
+  int64_t nq;
+  int k;
+  const uint32_t *order;
+  uint32_t *out_id;
+  int64_t *out_d2;
+  int *status;
+};
+
+template <int KPL>
+struct KList {
+  int64_t d[KPL];
+  uint32_t i[KPL];
+  int64_t kd;  // k-th entry (warp-uniform)
+  uint32_t ki;
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+      d[r] = INT64_MAX;
+      i[r] = 0xFFFFFFFFu;
+    }
+    kd = INT64_MAX;
+    ki = 0xFFFFFFFFu;
+  }
+  __device__ __forceinline__ bool admits(int64_t cd, uint32_t ci) const { return pair_less(cd, ci, kd, ki); }
+
+  // Insert a warp-uniform candidate into the sorted list of k entries.
+  __device__ __forceinline__ void insert(int64_t cd, uint32_t ci, int k) {
+    const int lane = threadIdx.x & 31;
+    int pos = 32 * KPL;
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, pair_less(cd, ci, d[r], i[r]));
+      if (m && pos == 32 * KPL) pos = r * 32 + __ffs(m) - 1;
+    }
+    if (pos >= k) return;
+#pragma unroll
+    for (int r = KPL - 1; r >= 0; --r) {
+      int64_t ud = __shfl_up_sync(0xFFFFFFFFu, d[r], 1);
+      uint32_t ui = __shfl_up_sync(0xFFFFFFFFu, i[r], 1);
+      if (r > 0) {
+        const int64_t cd2 = __shfl_sync(0xFFFFFFFFu, d[r > 0 ? r - 1 : 0], 31);
+        const uint32_t ci2 = __shfl_sync(0xFFFFFFFFu, i[r > 0 ? r - 1 : 0], 31);
+        if (lane == 0) {
+          ud = cd2;
+          ui = ci2;
+        }
+      }
+      const int e = r * 32 + lane;
+      if (e > pos) {
+        d[r] = ud;
+        i[r] = ui;
+      } else if (e == pos) {
+        d[r] = cd;
+        i[r] = ci;
+      }
+    }
+    const int rk = (k - 1) >> 5, lk = (k - 1) & 31;
+    int64_t vd = d[0];
+    uint32_t vi = i[0];
+#pragma unroll
+    for (int r = 1; r < KPL; ++r)
+      if (r == rk) {
+        vd = d[r];
+        vi = i[r];
+      }
+    kd = __shfl_sync(0xFFFFFFFFu, vd, lk);
+    ki = __shfl_sync(0xFFFFFFFFu, vi, lk);
+  }
+};
+
+template <int D, int KPL>
+__device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, const int32_t *qc, KList<KPL> &kl,
+                                              int k) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t s0 = t.ref[node];
+  const int cnt = t.cnt[node];
+  for (int b = 0; b < cnt; b += 32) {
+    const int s = b + lane;
+    int64_t d2 = INT64_MAX;
+    uint32_t id = 0xFFFFFFFFu;
+    const bool valid = s < cnt;
+    if (valid) {
+      const uint32_t slot = s0 + (uint32_t)s;
+      id = t.pid[slot];
+      d2 = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int64_t dd = (int64_t)t.px[d][slot] - qc[d];
+        d2 += dd * dd;
+      }
+    }
+    uint32_t m = __ballot_sync(0xFFFFFFFFu, valid && kl.admits(d2, id));
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t cd = __shfl_sync(0xFFFFFFFFu, d2, src);
+      const uint32_t ci = __shfl_sync(0xFFFFFFFFu, id, src);
+      if (kl.admits(cd, ci)) kl.insert(cd, ci, k);
+    }
+  }
+}
+
+template <int D, int KPL>
+__global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a) {
+  __shared__ uint32_t s_node[QW][STACK];
+  __shared__ int64_t s_md[QW][STACK];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nw = (int64_t)gridDim.x * QW;
+  const TreeView &t = a.t;
+  for (int64_t qi = (int64_t)blockIdx.x * QW + w; qi < a.nq; qi += nw) {
+    const int64_t q = a.order ? (int64_t)a.order[qi] : qi;
+    int32_t qc[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) qc[d] = a.q[q * D + d];
+    KList<KPL> kl;
+    kl.init();
+    int sp = 0;
+    if (t.root >= 0) {
+      if (lane == 0) {
+        s_node[w][0] = (uint32_t)t.root;
+        s_md[w][0] = 0;
+      }
+      sp = 1;
+    }
+    __syncwarp();
+    while (sp > 0) {
+      --sp;
+      const uint32_t node = s_node[w][sp];
+      const int64_t md = s_md[w][sp];
+      __syncwarp();
+      if (md > kl.kd) continue;
+      const int nk = t.kids[node];
+      if (nk == 0) {
+        knn_scan_leaf<D, KPL>(t, node, qc, kl, a.k);
+        continue;
+      }
+      const uint32_t c0 = t.ref[node];
+      for (int cb = 0; cb < nk; cb += 32) {
+        int64_t cmd = INT64_MAX;
+        uint32_t cn = 0xFFFFFFFFu;
+        if (cb + lane < nk) {
+          cn = c0 + (uint32_t)(cb + lane);
+          cmd = box_mindist<D>(t, cn, qc);
+          if (cmd > kl.kd || t.cnt[cn] == 0) {
+            cmd = INT64_MAX;
+            cn = 0xFFFFFFFFu;
+          }
+        }
+        warp_sort_asc(cmd, cn);
+        const int nok = __popc(__ballot_sync(0xFFFFFFFFu, cn != 0xFFFFFFFFu));
+        if (sp + nok > STACK) {
+          if (lane == 0) atomicOr(a.status, ST_STACK);
+          break;
+        }
+        if (lane < nok) {
+          s_node[w][sp + nok - 1 - lane] = cn;
+          s_md[w][sp + nok - 1 - lane] = cmd;
+        }
+        sp += nok;
+        __syncwarp();
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+      const int e = r * 32 + lane;
+      if (e < a.k) {
+        a.out_id[q * a.k + e] = kl.i[r];
+        a.out_d2[q * a.k + e] = kl.d[r];
+      }
+    }
+  }
+}
+
+struct RangeArgs {
+  TreeView t;
+  const int32_t *boxes;
+  int64_t nq;
+  int64_t *counts;          // count pass
+  const int64_t *offsets;   // emit pass
+  uint32_t *out_ids;
+  int *status;
+};
+
+template <int D>
+__device__ __forceinline__ bool point_in(const TreeView &t, uint32_t slot, const int32_t *blo, const int32_t *bhi) {
+  bool in = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int32_t c = t.px[d][slot];
+    in &= c >= blo[d] && c <= bhi[d];
+  }
+  return in;
+}
+
+// EMIT = false: count; EMIT = true: write ids.
+template <int D, bool EMIT>
+__global__ __launch_bounds__(QW * 32) void k_range(RangeArgs a) {
+  __shared__ uint32_t s_node[QW][STACK];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nw = (int64_t)gridDim.x * QW;
+  const TreeView &t = a.t;
+  for (int64_t q = (int64_t)blockIdx.x * QW + w; q < a.nq; q += nw) {
+    int32_t blo[D], bhi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      blo[d] = a.boxes[q * 2 * D + d];
+      bhi[d] = a.boxes[q * 2 * D + D + d];
+    }
+    int64_t acc = 0;                               // count pass: per-lane partial
+    int64_t cursor = EMIT ? a.offsets[q] : 0;      // emit pass: warp-uniform
+    int sp = 0;
+    if (t.root >= 0) {
+      const int rel = box_relation<D>(t, (uint32_t)t.root, blo, bhi);
+      if (rel == 2 && !EMIT) {
+        if (lane == 0) acc += t.cnt[t.root];
+      } else if (rel != 0) {
+        if (lane == 0) s_node[w][0] = (uint32_t)t.root | (rel == 2 ? INSIDE : 0u);
+        sp = 1;
+      }
+    }
+    __syncwarp();
+    while (sp > 0) {
+      --sp;
+      const uint32_t e = s_node[w][sp];
+      __syncwarp();
+      const uint32_t node = e & ~INSIDE;
+      const bool inside = (e & INSIDE) != 0;
+      const int nk = t.kids[node];
+      if (nk == 0) {
+        const uint32_t s0 = t.ref[node];
+        const int cnt = t.cnt[node];
+        for (int b = 0; b < cnt; b += 32) {
+          const int s = b + lane;
+          const bool hit = s < cnt && (inside || point_in<D>(t, s0 + (uint32_t)s, blo, bhi));
+          if (!EMIT) {
+            acc += hit;
+          } else {
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+            if (hit) a.out_ids[cursor + __popc(m & lanemask_lt())] = t.pid[s0 + s];
+            cursor += __popc(m);
+          }
+        }
+        continue;
+      }
+      const uint32_t c0 = t.ref[node];
+      for (int cb = 0; cb < nk; cb += 32) {
+        uint32_t push = 0xFFFFFFFFu;
+        if (cb + lane < nk) {
+          const uint32_t c = c0 + (uint32_t)(cb + lane);
+          const int rel = inside ? 2 : box_relation<D>(t, c, blo, bhi);
+          if (rel == 2 && !EMIT)
+            acc += t.cnt[c];
+          else if (rel != 0)
+            push = c | (rel == 2 ? INSIDE : 0u);
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, push != 0xFFFFFFFFu);
+        if (sp + __popc(m) > STACK) {
+          if (lane == 0) atomicOr(a.status, ST_STACK);
+          break;
+        }
+        if (push != 0xFFFFFFFFu) s_node[w][sp + __popc(m & lanemask_lt())] = push;
+        sp += __popc(m);
+        __syncwarp();
+      }
+    }
+    if (!EMIT) {
+      for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+      if (lane == 0) a.counts[q] = acc;
+    }
+  }
+}
+
+// One block per query segment: ascending sort of its ids.
+__global__ __launch_bounds__(1024) void k_sort_segments(const int64_t *offsets, int64_t nq, uint32_t *ids) {
+  __shared__ uint32_t sv[4096];
+  for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int64_t b = offsets[q], len = offsets[q + 1] - b;
+    if (len <= 1) continue;
+    if (len <= 4096) {
+      for (int64_t j = threadIdx.x; j < len; j += blockDim.x) sv[j] = ids[b + j];
+      __syncthreads();
+      bitonic_ascending(
+          len, [&](int64_t x, int64_t y) { return sv[x] < sv[y]; },
+          [&](int64_t x, int64_t y) {
+            const uint32_t tmp = sv[x];
+            sv[x] = sv[y];
+            sv[y] = tmp;
+          });
+      for (int64_t j = threadIdx.x; j < len; j += blockDim.x) ids[b + j] = sv[j];
+      __syncthreads();
+    } else {
+      uint32_t *v = ids + b;
+      bitonic_ascending(
+          len, [&](int64_t x, int64_t y) { return v[x] < v[y]; },
+          [&](int64_t x, int64_t y) {
+            const uint32_t tmp = v[x];
+            v[x] = v[y];
+            v[y] = tmp;
+          });
+    }
+  }
+}
+
+int query_grid(int64_t nq) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nq, QW), (int64_t)num_sms() * 16));
+}
+
+}  // namespace
+
+// Sorts the query points along the index's curve so that neighbouring warps
+// traverse neighbouring parts of the tree; returns the permutation in *order.
+psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, Buf<uint32_t> &order_buf, uint32_t **order,
+                       cudaStream_t s) {
+  *order = nullptr;
+  if (nq < 4096) return PSI_OK;
+  Buf<uint64_t> k0, k1;
+  Buf<uint32_t> v1;
+  psi_status st;
+  if ((st = k0.alloc(nq, s)) || (st = k1.alloc(nq, s)) || (st = order_buf.alloc(nq, s)) || (st = v1.alloc(nq, s)))
+    return st;
+  EncodeSpec e = encode_spec(ix, q);
+  SortResult r;
+  if ((st = sort_pairs(e, nullptr, nullptr, nq, ix->key_bits, nullptr, k0.p, order_buf.p, k1.p, v1.p, ix->d_status,
+                       s, &r)))
+    return st;
+  if (r.vals == v1.p) {
+    std::swap(order_buf.p, v1.p);
+  }
+  *order = order_buf.p;
+  return PSI_OK;
+}
+
+psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uint32_t *out_id, int64_t *out_d2,
+                   cudaStream_t s) {
+  if (nq == 0) return PSI_OK;
+  Buf<uint32_t> ob;
+  uint32_t *order = nullptr;
+  psi_status st = query_order(ix, q, nq, ob, &order, s);
+  if (st) return st;
+  KnnArgs a{ix->view(), q, nq, k, order, out_id, out_d2, ix->d_status};
+  const int g = query_grid(nq);
+  const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
+#define KNN_CASE(DD, KK) PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK>), g, QW * 32, 0, s, a)
+  if (ix->D == 2) {
+    if (kpl == 1) KNN_CASE(2, 1);
+    else if (kpl == 2) KNN_CASE(2, 2);
+    else KNN_CASE(2, 4);
+  } else {
+    if (kpl == 1) KNN_CASE(3, 1);
+    else if (kpl == 2) KNN_CASE(3, 2);
+    else KNN_CASE(3, 4);
+  }
+#undef KNN_CASE
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
+}
+
+psi_status run_range_count(const psi_index *ix, const int32_t *boxes, int64_t nq, int64_t *counts, cudaStream_t s) {
+  if (nq == 0) return PSI_OK;
+  RangeArgs a{ix->view(), boxes, nq, counts, nullptr, nullptr, ix->d_status};
+  const int g = query_grid(nq);
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_range_count", (k_range<2, false>), g, QW * 32, 0, s, a);
+  else
+    PSI_LAUNCH_NAMED("k_range_count", (k_range<3, false>), g, QW * 32, 0, s, a);
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
+}
+
+psi_status run_range_emit(const psi_index *ix, const int32_t *boxes, int64_t nq, const int64_t *offsets,
+                          uint32_t *ids, bool sorted, cudaStream_t s) {
+  if (nq == 0) return PSI_OK;
+  RangeArgs a{ix->view(), boxes, nq, nullptr, offsets, ids, ix->d_status};
+  const int g = query_grid(nq);
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_range_emit", (k_range<2, true>), g, QW * 32, 0, s, a);
+  else
+    PSI_LAUNCH_NAMED("k_range_emit", (k_range<3, true>), g, QW * 32, 0, s, a);
+  if (sorted)
+    PSI_LAUNCH(k_sort_segments, (int)std::min<int64_t>(nq, (int64_t)num_sms() * 2), 1024, 0, s, offsets, nq, ids);
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
+}
+
+}  // namespace psi

@@ -1,0 +1,552 @@
+// sort.cu -- onesweep LSD radix sort of (uint64 key, uint32 value) pairs.
+//
+// Role in the method: Algorithm 3 sorts <code, id> pairs only, computing each
+// point's curve code when the point is first touched by the sort.  Here the
+// sort is a least-significant-digit radix sort with 8-bit digits in the
+// "onesweep" arrangement (one upfront histogram pass for all digits, then one
+// pass per digit that ranks a tile in shared memory and obtains the tile's
+// global digit offsets by decoupled look-back over earlier tiles):
+//   * k_sort_hist     reads every key once (computing it from the point when
+//                     encoding) and accumulates all digit histograms;
+//   * k_hist_scan     turns them into per-digit global bases;
+//   * k_onesweep      per digit: warp-level ranking with match.any into per-warp
+//                     shared counters (stable), tile totals published to a
+//                     look-back table, bounded spin on predecessors, shared-
+//                     memory staging so that each digit's run is written out
+//                     contiguously.
+// The first digit pass of an encoding sort reads the points, not keys, so the
+// keys are never written before they are sorted.
+// Equal keys (duplicate points) are then put in id order by k_tie_runs /
+// k_tie_long (a later canonical leaf layout depends on it).
+#include "common.cuh"
+#include "bitonic.cuh"
+#include "keys.cuh"
+
+namespace psi {
+
+namespace {
+
+constexpr int RB = 8;
+constexpr int RADIX = 1 << RB;
+constexpr int ST = 256;        // threads per sort tile
+constexpr int SI = 16;         // keys per thread
+constexpr int TILE = ST * SI;  // 4096 keys per tile
+constexpr int SW = ST / 32;
+constexpr int MAX_PASSES = 8;
+
+constexpr uint32_t LB_AGG = 1u << 30, LB_PRE = 2u << 30, LB_VAL = (1u << 30) - 1;
+
+static_assert(RADIX == ST, "one digit per thread in the tile epilogue");
+
+struct PassArgs {
+  const uint64_t *kin;
+  const uint32_t *vin;
+  uint64_t *kout;
+  uint32_t *vout;
+  const int32_t *pts;
+  int bits;
+  int64_t n;
+  int shift;
+  const uint32_t *gbase;  // [RADIX] global exclusive digit offsets of this pass
+  uint32_t *lookback;     // [tiles][RADIX]
+  uint32_t *tile_ctr;
+  int *status;
+};
+
+template <int MODE, int D, int CURVE>
+__global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const int32_t *pts, int bits, int64_t n,
+                                                   int passes, uint32_t *hist, int *status) {
+  __shared__ uint32_t sh[MAX_PASSES][RADIX];
+  __shared__ uint8_t htab[256];
+  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
+  if (MODE == 1 && CURVE == 1) hilbert_table_init(htab);
+  __syncthreads();
+  bool bad_any = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    int64_t i = i0 + threadIdx.x;
+    if (i < n) {
+      uint64_t k;
+      if (MODE == 0) {
+        k = kin[i];
+      } else {
+        int32_t c[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) c[d] = pts[i * D + d];
+        bool bad;
+        k = point_key<D, CURVE>(htab, c, bits, bad);
+        bad_any |= bad;
+      }
+      const uint32_t act = __activemask();
+      for (int p = 0; p < passes; ++p) {
+        uint32_t dg = (uint32_t)(k >> (p * RB)) & (RADIX - 1);
+        int all_same;
+        __match_all_sync(act, dg, &all_same);
+        if (all_same) {
+          if ((lanemask_lt() & act) == 0) atomicAdd(&sh[p][dg], (uint32_t)__popc(act));
+        } else {
+          atomicAdd(&sh[p][dg], 1u);
+        }
+      }
+    }
+  }
+  if (bad_any) atomicOr(status, ST_RANGE);
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
+    uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&hist[i], v);
+  }
+}
+
+// One block per pass: exclusive scan of the pass's digit counts.
+__global__ void k_hist_scan(const uint32_t *hist, uint32_t *gbase) {
+  __shared__ uint32_t wsum[RADIX / 32];
+  const int p = blockIdx.x, d = threadIdx.x, lane = d & 31, w = d >> 5;
+  uint32_t c = hist[p * RADIX + d], x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int i = 0; i < w; ++i) before += wsum[i];
+  gbase[p * RADIX + d] = before + x - c;
+}
+
+template <int MODE, int D, int CURVE>
+__global__ __launch_bounds__(ST, 2) void k_onesweep(PassArgs a) {
+  __shared__ uint32_t s_wh[SW][RADIX];
+  __shared__ uint32_t s_off[RADIX];
+  __shared__ uint32_t s_glob[RADIX];
+  __shared__ __align__(16) uint64_t s_stage[TILE];
+  __shared__ uint32_t s_wsum[SW];
+  __shared__ uint8_t s_htab[256];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
+  for (int i = tid; i < SW * RADIX; i += ST) (&s_wh[0][0])[i] = 0;
+  if (MODE == 1 && CURVE == 1) hilbert_table_init(s_htab);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t base = (int64_t)tile * TILE;
+  const int tile_n = (int)min((int64_t)TILE, a.n - base);
+  const int wbase = w * (SI * 32);
+
+  uint64_t key[SI];
+#pragma unroll
+  for (int j = 0; j < SI; ++j) {
+    const int li = wbase + j * 32 + lane;
+    key[j] = ~0ull;
+    if (li < tile_n) {
+      const int64_t gi = base + li;
+      if (MODE == 0) {
+        key[j] = a.kin[gi];
+      } else {
+        int32_t c[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) c[d] = a.pts[gi * D + d];
+        bool bad;
+        key[j] = point_key<D, CURVE>(s_htab, c, a.bits, bad);
+      }
+    }
+  }
+
+  // Stable rank of each key among equal digits of its warp (items in
+  // (item, lane) order = input order).
+  uint32_t rank[SI];
+#pragma unroll
+  for (int j = 0; j < SI; ++j) {
+    const int li = wbase + j * 32 + lane;
+    const bool valid = li < tile_n;
+    const uint32_t dg = valid ? ((uint32_t)(key[j] >> a.shift) & (RADIX - 1)) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+    const uint32_t before = __popc(peers & lanemask_lt());
+    const uint32_t wb = valid ? s_wh[w][dg] : 0u;
+    __syncwarp();
+    if (valid && before == 0) s_wh[w][dg] = wb + __popc(peers);
+    __syncwarp();
+    rank[j] = wb + before;
+  }
+  __syncthreads();
+
+  // Epilogue per digit (thread = digit): per-warp offsets, tile total,
+  // look-back publication, tile-local and global offsets.
+  {
+    const uint32_t d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < SW; ++ww) {
+      const uint32_t c = s_wh[ww][d];
+      s_wh[ww][d] = run;
+      run += c;
+    }
+    const uint32_t cnt = run;
+    uint32_t *my = a.lookback + (size_t)tile * RADIX + d;
+    st_relaxed_u32(my, (tile == 0 ? LB_PRE : LB_AGG) | cnt);
+
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[w] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int i = 0; i < w; ++i) before += s_wsum[i];
+    const uint32_t excl = before + x - cnt;
+    s_off[d] = excl;
+
+    uint32_t prev = 0;
+    if (tile > 0) {
+      int64_t t = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      while (t >= 0) {
+        const uint32_t v = ld_relaxed_u32(a.lookback + (size_t)t * RADIX + d);
+        if ((v & (LB_AGG | LB_PRE)) == 0) {
+          if (++spins > kSpinLimit) {
+            atomicOr(a.status, ST_TIMEOUT);
+            break;
+          }
+          if (spins > 64) __nanosleep(64);
+          continue;
+        }
+        prev += v & LB_VAL;
+        if (v & LB_PRE) break;
+        --t;
+      }
+      st_relaxed_u32(my, LB_PRE | ((prev + cnt) & LB_VAL));
+    }
+    s_glob[d] = a.gbase[d] + prev - excl;
+  }
+  __syncthreads();
+
+  // Stage keys at their tile-local positions, then write each digit's run out.
+#pragma unroll
+  for (int j = 0; j < SI; ++j) {
+    const int li = wbase + j * 32 + lane;
+    if (li < tile_n) {
+      const uint32_t dg = (uint32_t)(key[j] >> a.shift) & (RADIX - 1);
+      const uint32_t lp = s_off[dg] + s_wh[w][dg] + rank[j];
+      s_stage[lp] = key[j];
+      rank[j] = lp;
+    }
+  }
+  __syncthreads();
+  uint32_t gpos[SI];
+#pragma unroll
+  for (int i = 0; i < SI; ++i) {
+    const int p = tid + i * ST;
+    if (p < tile_n) {
+      const uint64_t k = s_stage[p];
+      gpos[i] = s_glob[(uint32_t)(k >> a.shift) & (RADIX - 1)] + p;
+      a.kout[gpos[i]] = k;
+    }
+  }
+  __syncthreads();
+  uint32_t *s_v = reinterpret_cast<uint32_t *>(s_stage);
+#pragma unroll
+  for (int j = 0; j < SI; ++j) {
+    const int li = wbase + j * 32 + lane;
+    if (li < tile_n) s_v[rank[j]] = (MODE == 1) ? (uint32_t)(base + li) : a.vin[base + li];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < SI; ++i) {
+    const int p = tid + i * ST;
+    if (p < tile_n) a.vout[gpos[i]] = s_v[p];
+  }
+}
+
+// ---- Ties: runs of equal keys ordered by id ------------------------------
+
+constexpr int kShortRun = 32;
+
+__global__ void k_tie_runs(const uint64_t *keys, uint32_t *vals, const uint32_t *ids, int64_t n, int64_t *long_runs,
+                           uint32_t *n_long, int64_t cap_long) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i + 1 >= n) return;
+  const uint64_t k = keys[i];
+  if (keys[i + 1] != k || (i > 0 && keys[i - 1] == k)) return;
+  int64_t e = i + 2;
+  while (e < n && keys[e] == k && e - i <= kShortRun) ++e;
+  const int len = (int)(e - i);
+  if (len > kShortRun) {
+    const uint32_t slot = atomicAdd(n_long, 1u);
+    if (slot < cap_long) long_runs[slot] = i;
+    return;
+  }
+  uint32_t v[kShortRun], id[kShortRun];
+  for (int j = 0; j < len; ++j) {
+    v[j] = vals[i + j];
+    id[j] = ids[v[j]];
+  }
+  for (int j = 1; j < len; ++j) {
+    const uint32_t cv = v[j], ci = id[j];
+    int t = j - 1;
+    while (t >= 0 && id[t] > ci) {
+      v[t + 1] = v[t];
+      id[t + 1] = id[t];
+      --t;
+    }
+    v[t + 1] = cv;
+    id[t + 1] = ci;
+  }
+  for (int j = 0; j < len; ++j) vals[i + j] = v[j];
+}
+
+// One block per long run: sort of the run's values by id (ids are unique, so
+// no stability is needed).  Runs up to 4096 sort in shared memory; longer ones
+// (pathological piles of duplicate points) sort in place in global memory.
+constexpr int kSmemRun = 4096;
+
+__global__ __launch_bounds__(1024) void k_tie_long(const uint64_t *keys, uint32_t *vals, const uint32_t *ids,
+                                                   int64_t n, const int64_t *long_runs, const uint32_t *n_long,
+                                                   int64_t cap_long) {
+  __shared__ uint32_t sv[kSmemRun], si[kSmemRun];
+  const int64_t runs = min((int64_t)*n_long, cap_long);
+  for (int64_t r = blockIdx.x; r < runs; r += gridDim.x) {
+    const int64_t s = long_runs[r];
+    const uint64_t k = keys[s];
+    int64_t lo = s, hi = n;  // first index past the run
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (keys[mid] == k)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int64_t len = lo - s;
+    if (len <= kSmemRun) {
+      for (int64_t j = threadIdx.x; j < len; j += blockDim.x) {
+        sv[j] = vals[s + j];
+        si[j] = ids[sv[j]];
+      }
+      __syncthreads();
+      bitonic_ascending(
+          len, [&](int64_t a, int64_t b) { return si[a] < si[b]; },
+          [&](int64_t a, int64_t b) {
+            uint32_t x = si[a];
+            si[a] = si[b];
+            si[b] = x;
+            x = sv[a];
+            sv[a] = sv[b];
+            sv[b] = x;
+          });
+      for (int64_t j = threadIdx.x; j < len; j += blockDim.x) vals[s + j] = sv[j];
+      __syncthreads();
+    } else {
+      uint32_t *v = vals + s;
+      bitonic_ascending(
+          len, [&](int64_t a, int64_t b) { return ids[v[a]] < ids[v[b]]; },
+          [&](int64_t a, int64_t b) {
+            const uint32_t x = v[a];
+            v[a] = v[b];
+            v[b] = x;
+          });
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+template <int MODE, int D, int CURVE>
+static void launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_t n, int passes, uint32_t *hist,
+                        int *status, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
+  PSI_LAUNCH_NAMED("k_sort_hist", (k_sort_hist<MODE, D, CURVE>), std::max(grid, 1), 256, 0, s, kin, enc.pts,
+                   enc.bits, n, passes, hist, status);
+}
+
+template <int MODE, int D, int CURVE>
+static void launch_pass(const PassArgs &a, int64_t tiles, cudaStream_t s) {
+  PSI_LAUNCH_NAMED("k_onesweep", (k_onesweep<MODE, D, CURVE>), (unsigned)tiles, ST, 0, s, a);
+}
+
+psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint32_t *vals_in, int64_t n,
+                      int key_bits, const uint32_t *tie_ids, uint64_t *kbuf0, uint32_t *vbuf0, uint64_t *kbuf1,
+                      uint32_t *vbuf1, int *d_status, cudaStream_t s, SortResult *out) {
+  out->keys = kbuf0;
+  out->vals = vbuf0;
+  if (n <= 0) return PSI_OK;
+  if (n >= (int64_t)LB_VAL) {
+    set_error("sort: more than 2^30-1 pairs in one sort");
+    return PSI_ERR_INVALID;
+  }
+  const bool encode = enc.pts != nullptr;
+  if (encode && (enc.dim != 2 && enc.dim != 3)) return PSI_ERR_INVALID;
+  if (encode && enc.curve == CURVE_HILBERT && enc.dim != 2) return PSI_ERR_INVALID;
+  key_bits = std::max(1, std::min(64, key_bits));
+  const int passes = (key_bits + RB - 1) / RB;
+  const int64_t tiles = ceil_div(n, TILE);
+
+  Buf<uint32_t> hist, gbase, lookback, ctr;
+  psi_status st;
+  if ((st = hist.alloc((size_t)passes * RADIX, s))) return st;
+  if ((st = gbase.alloc((size_t)passes * RADIX, s))) return st;
+  if ((st = lookback.alloc((size_t)passes * tiles * RADIX, s))) return st;
+  if ((st = ctr.alloc(passes, s))) return st;
+  PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * passes * RADIX, s));
+  PSI_CK(cudaMemsetAsync(lookback.p, 0, sizeof(uint32_t) * passes * tiles * RADIX, s));
+  PSI_CK(cudaMemsetAsync(ctr.p, 0, sizeof(uint32_t) * passes, s));
+
+  if (!encode)
+    launch_hist<0, 2, 0>(keys_in, enc, n, passes, hist.p, d_status, s);
+  else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
+    launch_hist<1, 2, 0>(nullptr, enc, n, passes, hist.p, d_status, s);
+  else if (enc.dim == 2)
+    launch_hist<1, 2, 1>(nullptr, enc, n, passes, hist.p, d_status, s);
+  else
+    launch_hist<1, 3, 0>(nullptr, enc, n, passes, hist.p, d_status, s);
+  PSI_LAUNCH(k_hist_scan, passes, RADIX, 0, s, hist.p, gbase.p);
+
+  uint64_t *kb[2] = {kbuf0, kbuf1};
+  uint32_t *vb[2] = {vbuf0, vbuf1};
+  for (int p = 0; p < passes; ++p) {
+    PassArgs a;
+    a.kin = p == 0 ? keys_in : kb[(p - 1) & 1];
+    a.vin = p == 0 ? vals_in : vb[(p - 1) & 1];
+    a.kout = kb[p & 1];
+    a.vout = vb[p & 1];
+    a.pts = enc.pts;
+    a.bits = enc.bits;
+    a.n = n;
+    a.shift = p * RB;
+    a.gbase = gbase.p + p * RADIX;
+    a.lookback = lookback.p + (size_t)p * tiles * RADIX;
+    a.tile_ctr = ctr.p + p;
+    a.status = d_status;
+    if (p > 0 || !encode)
+      launch_pass<0, 2, 0>(a, tiles, s);
+    else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
+      launch_pass<1, 2, 0>(a, tiles, s);
+    else if (enc.dim == 2)
+      launch_pass<1, 2, 1>(a, tiles, s);
+    else
+      launch_pass<1, 3, 0>(a, tiles, s);
+  }
+  out->keys = kb[(passes - 1) & 1];
+  out->vals = vb[(passes - 1) & 1];
+
+  if (tie_ids) {
+    const int64_t cap_long = n / (kShortRun + 1) + 1;
+    Buf<int64_t> runs;
+    Buf<uint32_t> nlong;
+    if ((st = runs.alloc(cap_long, s))) return st;
+    if ((st = nlong.alloc(1, s))) return st;
+    PSI_CK(cudaMemsetAsync(nlong.p, 0, sizeof(uint32_t), s));
+    PSI_LAUNCH(k_tie_runs, (unsigned)ceil_div(n, 256), 256, 0, s, out->keys, out->vals, tie_ids, n, runs.p, nlong.p,
+               cap_long);
+    PSI_LAUNCH(k_tie_long, num_sms(), 1024, 0, s, out->keys, out->vals, tie_ids, n, runs.p, nlong.p, cap_long);
+  }
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan (reduce, scan of block sums, apply)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int SCAN_T = 512, SCAN_I = 8, SCAN_CHUNK = SCAN_T * SCAN_I;
+
+template <class T>
+__global__ void k_scan_reduce(const T *in, int64_t n, int64_t *sums) {
+  __shared__ int64_t ws[SCAN_T / 32];
+  const int64_t b = (int64_t)blockIdx.x * SCAN_CHUNK;
+  int64_t acc = 0;
+  for (int i = threadIdx.x; i < SCAN_CHUNK; i += SCAN_T)
+    if (b + i < n) acc += (int64_t)in[b + i];
+  for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int i = 0; i < SCAN_T / 32; ++i) t += ws[i];
+    sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_scan_sums(int64_t *sums, int64_t nb, int64_t *total) {
+  __shared__ int64_t carry;
+  __shared__ int64_t ws[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    const int64_t i = b0 + threadIdx.x;
+    const int64_t v = i < nb ? sums[i] : 0;
+    int64_t x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    int64_t before = carry;
+    for (int j = 0; j < w; ++j) before += ws[j];
+    if (i < nb) sums[i] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <class T>
+__global__ void k_scan_apply(const T *in, int64_t *out, int64_t n, const int64_t *sums) {
+  __shared__ int64_t ws[SCAN_T / 32];
+  __shared__ int64_t carry;
+  const int64_t b = (int64_t)blockIdx.x * SCAN_CHUNK;
+  if (threadIdx.x == 0) carry = sums[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int r = 0; r < SCAN_I; ++r) {
+    const int64_t i = b + (int64_t)r * SCAN_T + threadIdx.x;
+    const int64_t v = i < n ? (int64_t)in[i] : 0;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    int64_t before = carry;
+    for (int j = 0; j < w; ++j) before += ws[j];
+    if (i < n) out[i] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == SCAN_T - 1) carry = before + x;
+    __syncthreads();
+  }
+}
+
+template <class T>
+psi_status scan_impl(const T *in, int64_t *out, int64_t n, int64_t *d_total, cudaStream_t s) {
+  if (n <= 0) {
+    if (d_total) PSI_CK(cudaMemsetAsync(d_total, 0, sizeof(int64_t), s));
+    return PSI_OK;
+  }
+  const int64_t nb = ceil_div(n, SCAN_CHUNK);
+  Buf<int64_t> sums;
+  psi_status st = sums.alloc(nb, s);
+  if (st) return st;
+  PSI_LAUNCH_NAMED("k_scan_reduce", k_scan_reduce<T>, (unsigned)nb, SCAN_T, 0, s, in, n, sums.p);
+  PSI_LAUNCH(k_scan_sums, 1, 1024, 0, s, sums.p, nb, d_total);
+  PSI_LAUNCH_NAMED("k_scan_apply", k_scan_apply<T>, (unsigned)nb, SCAN_T, 0, s, in, out, n, sums.p);
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
+}
+}  // namespace
+
+psi_status scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *d_total, cudaStream_t s) {
+  return scan_impl<int64_t>(in, out, n, d_total, s);
+}
+psi_status scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *d_total, cudaStream_t s) {
+  return scan_impl<int32_t>(in, out, n, d_total, s);
+}
+
+}  // namespace psi

@@ -1,0 +1,598 @@
+// update.cu -- SPaC batch insertion and deletion (Algorithm 4; Sec 4.2).
+//
+// The batch is sorted by (key, id) with the same onesweep sort as the build,
+// and every batch point is routed to the leaf whose (key, id) range holds it:
+// leaf j covers [sep_j, sep_{j+1}) where sep_j is the first (key, id) the leaf
+// was created with (leaf 0 extends down to -infinity).  Because the batch is
+// sorted, each leaf receives one contiguous slice of it.  Then, per leaf:
+//   insert: if the leaf's points plus its slice fit the leaf's block (2*phi
+//           slots), the slice is appended unsorted and the box widened
+//           (Algorithm 4: append and mark unsorted); otherwise the leaf is
+//           sorted, merged with its slice (merge path) and re-wrapped into
+//           ceil(c / phi) leaves of balanced size in fresh blocks (Algorithm 4:
+//           rebuild when the leaf would exceed the wrap).
+//   delete: every leaf point whose (key, id) occurs in the slice (and whose
+//           coordinates match) is removed; survivors are compacted in place
+//           and the box recomputed; empty leaves are dropped.
+// Only touched leaves move data.  The leaf list is then rewritten from a scan
+// of per-leaf output counts and the summary tree rebuilt over it -- the
+// paper's join-based rebalancing is replaced by this relayout of the (small)
+// leaf directory.
+#include "index.cuh"
+
+namespace psi {
+int64_t summary_capacity(int64_t L, int F);
+
+namespace {
+
+struct Batch {
+  Buf<uint64_t> k0, k1;
+  Buf<uint32_t> v0, v1;
+  const uint64_t *keys = nullptr;  // sorted keys
+  const uint32_t *vals = nullptr;  // positions into the caller's batch arrays
+};
+
+psi_status sort_batch(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, cudaStream_t s, Batch &b) {
+  psi_status st;
+  if ((st = b.k0.alloc(m, s)) || (st = b.k1.alloc(m, s)) || (st = b.v0.alloc(m, s)) || (st = b.v1.alloc(m, s)))
+    return st;
+  SortResult r;
+  if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, m, ix->key_bits, ids, b.k0.p, b.v0.p, b.k1.p, b.v1.p,
+                       ix->d_status, s, &r)))
+    return st;
+  b.keys = r.keys;
+  b.vals = r.vals;
+  return PSI_OK;
+}
+
+int grid_for(int64_t n, int threads = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 32));
+}
+
+// Leaf of each batch point: the last leaf whose separator is <= (key, id).
+__global__ void k_locate(const uint64_t *bkeys, const uint32_t *bvals, const uint32_t *ids, int64_t m,
+                         const uint64_t *sep_key, const uint32_t *sep_id, int64_t L, int32_t *bleaf) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = bkeys[i];
+    const uint32_t id = ids[bvals[i]];
+    int64_t lo = 0, hi = L;  // first separator greater than (k, id)
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (kid_less(k, id, sep_key[mid], sep_id[mid]))
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    bleaf[i] = (int32_t)max((int64_t)0, lo - 1);
+  }
+}
+
+// Slice [sbeg[j], send[j]) of the sorted batch routed to leaf j.
+__global__ void k_slices(const int32_t *bleaf, int64_t m, int32_t *sbeg, int32_t *send) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t j = bleaf[i];
+    if (i == 0 || bleaf[i - 1] != j) sbeg[j] = (int32_t)i;
+    if (i == m - 1 || bleaf[i + 1] != j) send[j] = (int32_t)(i + 1);
+  }
+}
+
+__global__ void k_insert_plan(const int32_t *cnt, const int32_t *sbeg, const int32_t *send, int64_t L, int C, int phi,
+                              int32_t *outl, int32_t *nblk) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+    const int len = send[j] - sbeg[j];
+    const int c = cnt[j] + len;
+    if (len == 0 || c <= C) {
+      outl[j] = 1;
+      nblk[j] = 0;
+    } else {
+      const int r = (c + phi - 1) / phi;
+      outl[j] = r;
+      nblk[j] = r;
+    }
+  }
+}
+
+constexpr int MAXPL = 4;  // points per lane in one block (C <= 128)
+
+// Sorts, in place, the block of every leaf that will be re-wrapped.
+__global__ void k_sort_overflow_leaves(const int32_t *ncnt, const uint32_t *nref, const int32_t *sbeg,
+                                       const int32_t *send, int64_t L, int C, int D, Pool pool) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < L; j += warps) {
+    const int len = send[j] - sbeg[j];
+    const int cnt = ncnt[j];
+    if (len == 0 || cnt + len <= C) continue;
+    const uint32_t s0 = nref[j];
+    uint64_t k[MAXPL];
+    uint32_t id[MAXPL];
+    int32_t c[MAXPL][3];
+#pragma unroll
+    for (int r = 0; r < MAXPL; ++r) {
+      const int e = r * 32 + lane;
+      k[r] = ~0ull;
+      id[r] = 0xFFFFFFFFu;
+      if (e < cnt) {
+        k[r] = pool.pkey[s0 + e];
+        id[r] = pool.pid[s0 + e];
+        for (int d = 0; d < D; ++d) c[r][d] = pool.px[d][s0 + e];
+      }
+    }
+    int rank[MAXPL] = {0, 0, 0, 0};
+    for (int r2 = 0; r2 < MAXPL; ++r2) {
+      if (r2 * 32 >= cnt) break;
+      for (int sl = 0; sl < 32; ++sl) {
+        const uint64_t kf = __shfl_sync(0xFFFFFFFFu, k[r2], sl);
+        const uint32_t idf = __shfl_sync(0xFFFFFFFFu, id[r2], sl);
+        if (r2 * 32 + sl >= cnt) break;
+#pragma unroll
+        for (int r = 0; r < MAXPL; ++r) rank[r] += kid_less(kf, idf, k[r], id[r]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < MAXPL; ++r) {
+      const int e = r * 32 + lane;
+      if (e < cnt) {
+        pool.pkey[s0 + rank[r]] = k[r];
+        pool.pid[s0 + rank[r]] = id[r];
+        for (int d = 0; d < D; ++d) pool.px[d][s0 + rank[r]] = c[r][d];
+      }
+    }
+  }
+}
+
+struct Leaves {  // leaf directory (node arrays of the leaves) + separators
+  int32_t *lo[3], *hi[3], *cnt, *kids, *depth;
+  uint32_t *ref;
+  uint64_t *sk;
+  uint32_t *si;
+};
+
+Leaves leaves_of(NodeArrays &a, uint64_t *sk, uint32_t *si) {
+  Leaves l;
+  for (int d = 0; d < 3; ++d) {
+    l.lo[d] = a.lo[d];
+    l.hi[d] = a.hi[d];
+  }
+  l.cnt = a.cnt;
+  l.kids = a.kids;
+  l.depth = a.depth;
+  l.ref = a.ref;
+  l.sk = sk;
+  l.si = si;
+  return l;
+}
+
+struct InsertArgs {
+  Leaves old, nw;
+  Pool pool;
+  const int32_t *sbeg, *send, *outl;
+  const int64_t *pos, *boff;
+  int64_t L, Lnew;
+  int64_t base_block;
+  const uint64_t *bkeys;
+  const uint32_t *bvals;
+  const int32_t *pts;
+  const uint32_t *ids;
+  int C, phi;
+};
+
+// Merged element order: leaf points first on equality.
+__device__ __forceinline__ bool leaf_before_slice(const InsertArgs &a, uint32_t ls, int64_t bi) {
+  const uint64_t lk = a.pool.pkey[ls], sk = a.bkeys[bi];
+  if (lk != sk) return lk < sk;
+  return a.pool.pid[ls] <= a.ids[a.bvals[bi]];
+}
+
+// One warp per new leaf position.
+template <int D>
+__global__ void k_insert_apply(InsertArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < a.Lnew; o += warps) {
+    int64_t lo = 0, hi = a.L;  // owner j: last old leaf with pos[j] <= o
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (a.pos[mid] <= o)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int64_t j = lo - 1;
+    const int t = (int)(o - a.pos[j]);
+    const int len = a.send[j] - a.sbeg[j];
+    const int cnt = a.old.cnt[j];
+    const uint32_t s0 = a.old.ref[j];
+    int32_t blo[D], bhi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      blo[d] = INT32_MAX;
+      bhi[d] = INT32_MIN;
+    }
+    if (len == 0 || cnt + len <= a.C) {
+      // untouched or append: the leaf keeps its block and separator
+      for (int s = lane; s < len; s += 32) {
+        const int64_t bi = a.sbeg[j] + s;
+        const uint32_t v = a.bvals[bi];
+        const uint32_t slot = s0 + (uint32_t)(cnt + s);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int32_t c = a.pts[(int64_t)v * D + d];
+          a.pool.px[d][slot] = c;
+          blo[d] = min(blo[d], c);
+          bhi[d] = max(bhi[d], c);
+        }
+        a.pool.pid[slot] = a.ids[v];
+        a.pool.pkey[slot] = a.bkeys[bi];
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        blo[d] = __reduce_min_sync(0xFFFFFFFFu, blo[d]);
+        bhi[d] = __reduce_max_sync(0xFFFFFFFFu, bhi[d]);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          a.nw.lo[d][o] = min(a.old.lo[d][j], blo[d]);
+          a.nw.hi[d][o] = max(a.old.hi[d][j], bhi[d]);
+        }
+        a.nw.cnt[o] = cnt + len;
+        a.nw.ref[o] = s0;
+        a.nw.kids[o] = 0;
+        a.nw.depth[o] = 0;
+        a.nw.sk[o] = a.old.sk[j];
+        a.nw.si[o] = a.old.si[j];
+      }
+      continue;
+    }
+    // re-wrap: part t of the merge of the (sorted) leaf and its slice
+    const int64_t c = (int64_t)cnt + len;
+    const int r = a.outl[j];
+    const int64_t pa = (int64_t)t * c / r, pb = (int64_t)(t + 1) * c / r;
+    const int64_t blk = a.base_block + a.boff[j] + t;
+    const uint32_t d0 = (uint32_t)(blk * a.C);
+    const int64_t sb = a.sbeg[j];
+    for (int64_t p = pa + lane; p < pb; p += 32) {
+      int64_t l = max((int64_t)0, p - len), h = min(p, (int64_t)cnt);
+      while (l < h) {
+        const int64_t mid = (l + h) >> 1;
+        if (leaf_before_slice(a, s0 + (uint32_t)mid, sb + (p - mid - 1)))
+          l = mid + 1;
+        else
+          h = mid;
+      }
+      const int64_t li = l, si = p - l;
+      const bool from_leaf = li < cnt && (si >= len || leaf_before_slice(a, s0 + (uint32_t)li, sb + si));
+      const uint32_t dst = d0 + (uint32_t)(p - pa);
+      if (from_leaf) {
+        const uint32_t src = s0 + (uint32_t)li;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int32_t cc = a.pool.px[d][src];
+          a.pool.px[d][dst] = cc;
+          blo[d] = min(blo[d], cc);
+          bhi[d] = max(bhi[d], cc);
+        }
+        a.pool.pid[dst] = a.pool.pid[src];
+        a.pool.pkey[dst] = a.pool.pkey[src];
+      } else {
+        const uint32_t v = a.bvals[sb + si];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int32_t cc = a.pts[(int64_t)v * D + d];
+          a.pool.px[d][dst] = cc;
+          blo[d] = min(blo[d], cc);
+          bhi[d] = max(bhi[d], cc);
+        }
+        a.pool.pid[dst] = a.ids[v];
+        a.pool.pkey[dst] = a.bkeys[sb + si];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      blo[d] = __reduce_min_sync(0xFFFFFFFFu, blo[d]);
+      bhi[d] = __reduce_max_sync(0xFFFFFFFFu, bhi[d]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        a.nw.lo[d][o] = blo[d];
+        a.nw.hi[d][o] = bhi[d];
+      }
+      a.nw.cnt[o] = (int32_t)(pb - pa);
+      a.nw.ref[o] = d0;
+      a.nw.kids[o] = 0;
+      a.nw.depth[o] = 0;
+      // the first part keeps the old lower end (leaf 0 stays open below);
+      // later parts start at their first element
+      if (t == 0) {
+        a.nw.sk[o] = a.old.sk[j];
+        a.nw.si[o] = a.old.si[j];
+      } else {
+        a.nw.sk[o] = a.pool.pkey[d0];
+        a.nw.si[o] = a.pool.pid[d0];
+      }
+    }
+  }
+}
+
+// One warp per touched leaf: remove the points named by its slice.
+template <int D>
+__global__ void k_delete_leaves(Leaves lv, Pool pool, const int32_t *sbeg, const int32_t *send, int64_t L,
+                                const uint64_t *bkeys, const uint32_t *bvals, const int32_t *pts,
+                                const uint32_t *ids, unsigned long long *deleted) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < L; j += warps) {
+    const int64_t b = sbeg[j], e = send[j];
+    if (e == b) continue;
+    const int cnt = lv.cnt[j];
+    const uint32_t s0 = lv.ref[j];
+    uint64_t k[MAXPL];
+    uint32_t id[MAXPL];
+    int32_t c[MAXPL][D];
+    bool keep[MAXPL];
+#pragma unroll
+    for (int r = 0; r < MAXPL; ++r) {
+      const int x = r * 32 + lane;
+      keep[r] = false;
+      if (x < cnt) {
+        k[r] = pool.pkey[s0 + x];
+        id[r] = pool.pid[s0 + x];
+#pragma unroll
+        for (int d = 0; d < D; ++d) c[r][d] = pool.px[d][s0 + x];
+        // is (k, id) in the slice?
+        int64_t lo = b, hi = e;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (kid_less(bkeys[mid], ids[bvals[mid]], k[r], id[r]))
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        bool hit = false;
+        if (lo < e && bkeys[lo] == k[r] && ids[bvals[lo]] == id[r]) {
+          hit = true;
+          const uint32_t v = bvals[lo];
+#pragma unroll
+          for (int d = 0; d < D; ++d) hit &= pts[(int64_t)v * D + d] == c[r][d];
+        }
+        keep[r] = !hit;
+      }
+    }
+    __syncwarp();
+    int out = 0;
+    int32_t blo[D], bhi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      blo[d] = INT32_MAX;
+      bhi[d] = INT32_MIN;
+    }
+#pragma unroll
+    for (int r = 0; r < MAXPL; ++r) {
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep[r]);
+      if (keep[r]) {
+        const uint32_t dst = s0 + (uint32_t)(out + __popc(m & lanemask_lt()));
+        pool.pkey[dst] = k[r];
+        pool.pid[dst] = id[r];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          pool.px[d][dst] = c[r][d];
+          blo[d] = min(blo[d], c[r][d]);
+          bhi[d] = max(bhi[d], c[r][d]);
+        }
+      }
+      out += __popc(m);
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      blo[d] = __reduce_min_sync(0xFFFFFFFFu, blo[d]);
+      bhi[d] = __reduce_max_sync(0xFFFFFFFFu, bhi[d]);
+    }
+    if (lane == 0) {
+      lv.cnt[j] = out;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        lv.lo[d][j] = blo[d];
+        lv.hi[d][j] = bhi[d];
+      }
+      if (cnt - out) atomicAdd(deleted, (unsigned long long)(cnt - out));
+    }
+  }
+}
+
+__global__ void k_nonempty(const int32_t *cnt, int64_t L, int32_t *keep) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x)
+    keep[j] = cnt[j] > 0;
+}
+
+template <int D>
+__global__ void k_compact_leaves(Leaves old, Leaves nw, const int32_t *keep, const int64_t *pos, int64_t L) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+    if (!keep[j]) continue;
+    const int64_t o = pos[j];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      nw.lo[d][o] = old.lo[d][j];
+      nw.hi[d][o] = old.hi[d][j];
+    }
+    nw.cnt[o] = old.cnt[j];
+    nw.ref[o] = old.ref[j];
+    nw.kids[o] = 0;
+    nw.depth[o] = 0;
+    // a leaf that becomes the first keeps its own lower end; leaf 0 is open below anyway
+    nw.sk[o] = old.sk[j];
+    nw.si[o] = old.si[j];
+  }
+}
+
+__global__ void k_copy_i64(const unsigned long long *src, int64_t *dst) { *dst = (int64_t)*src; }
+
+// Grows the pool to hold at least `slots` slots, keeping the used prefix.
+psi_status grow_pool(psi_index *ix, int64_t slots_needed, int64_t used_slots, cudaStream_t s) {
+  if (slots_needed <= ix->pool.cap_slots) return PSI_OK;
+  Pool np;
+  const int64_t cap = std::max(slots_needed + slots_needed / 4, ix->pool.cap_slots * 3 / 2);
+  psi_status st = alloc_pool(np, ix->D, cap, s);
+  if (st) {
+    free_pool(np, s);
+    return st;
+  }
+  if (used_slots > 0) {
+    for (int d = 0; d < ix->D; ++d)
+      PSI_CK(cudaMemcpyAsync(np.px[d], ix->pool.px[d], sizeof(int32_t) * used_slots, cudaMemcpyDeviceToDevice, s));
+    PSI_CK(cudaMemcpyAsync(np.pid, ix->pool.pid, sizeof(uint32_t) * used_slots, cudaMemcpyDeviceToDevice, s));
+    PSI_CK(cudaMemcpyAsync(np.pkey, ix->pool.pkey, sizeof(uint64_t) * used_slots, cudaMemcpyDeviceToDevice, s));
+  }
+  free_pool(ix->pool, s);
+  ix->pool = np;
+  return PSI_OK;
+}
+
+int warp_grid(int64_t warps) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps, 8), (int64_t)num_sms() * 32));
+}
+
+}  // namespace
+
+psi_status spac_build_fresh(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t n, cudaStream_t s);
+
+psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, cudaStream_t s) {
+  if (ix->L == 0) return spac_build_fresh(ix, pts, ids, m, s);
+  psi_status st;
+  Batch b;
+  if ((st = sort_batch(ix, pts, ids, m, s, b))) return st;
+  const int64_t L = ix->L;
+  Buf<int32_t> bleaf, sbeg, send, outl, nblk;
+  Buf<int64_t> pos, boff, tot;
+  if ((st = bleaf.alloc(m, s)) || (st = sbeg.alloc(L, s)) || (st = send.alloc(L, s)) || (st = outl.alloc(L, s)) ||
+      (st = nblk.alloc(L, s)) || (st = pos.alloc(L, s)) || (st = boff.alloc(L, s)) || (st = tot.alloc(2, s)))
+    return st;
+  PSI_CK(cudaMemsetAsync(sbeg.p, 0, sizeof(int32_t) * L, s));
+  PSI_CK(cudaMemsetAsync(send.p, 0, sizeof(int32_t) * L, s));
+  PSI_LAUNCH(k_locate, grid_for(m), 256, 0, s, b.keys, b.vals, ids, m, ix->sep_key, ix->sep_id, L, bleaf.p);
+  PSI_LAUNCH(k_slices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p);
+  PSI_LAUNCH(k_insert_plan, grid_for(L), 256, 0, s, ix->nodes.cnt, sbeg.p, send.p, L, ix->C, ix->phi, outl.p, nblk.p);
+  if ((st = scan_i32_to_i64(outl.p, pos.p, L, tot.p, s))) return st;
+  if ((st = scan_i32_to_i64(nblk.p, boff.p, L, tot.p + 1, s))) return st;
+  int64_t h[2];
+  PSI_CK(cudaMemcpyAsync(h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  const int64_t Lnew = h[0], NB = h[1];
+
+  const int64_t base_block = ix->pool_used;
+  if ((st = grow_pool(ix, (base_block + NB) * ix->C, base_block * ix->C, s))) return st;
+  PSI_LAUNCH(k_sort_overflow_leaves, warp_grid(L), 256, 0, s, ix->nodes.cnt, ix->nodes.ref, sbeg.p, send.p, L, ix->C,
+             ix->D, ix->pool);
+
+  NodeArrays na;
+  uint64_t *nsk = nullptr;
+  uint32_t *nsi = nullptr;
+  if ((st = alloc_nodes(na, ix->D, summary_capacity(Lnew, ix->F), false, s)) ||
+      (st = DevMem::alloc((void **)&nsk, sizeof(uint64_t) * Lnew, s)) ||
+      (st = DevMem::alloc((void **)&nsi, sizeof(uint32_t) * Lnew, s))) {
+    free_nodes(na, s);
+    DevMem::free(nsk, s);
+    DevMem::free(nsi, s);
+    return st;
+  }
+  InsertArgs a;
+  a.old = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
+  a.nw = leaves_of(na, nsk, nsi);
+  a.pool = ix->pool;
+  a.sbeg = sbeg.p;
+  a.send = send.p;
+  a.outl = outl.p;
+  a.pos = pos.p;
+  a.boff = boff.p;
+  a.L = L;
+  a.Lnew = Lnew;
+  a.base_block = base_block;
+  a.bkeys = b.keys;
+  a.bvals = b.vals;
+  a.pts = pts;
+  a.ids = ids;
+  a.C = ix->C;
+  a.phi = ix->phi;
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_insert_apply", k_insert_apply<2>, warp_grid(Lnew), 256, 0, s, a);
+  else
+    PSI_LAUNCH_NAMED("k_insert_apply", k_insert_apply<3>, warp_grid(Lnew), 256, 0, s, a);
+  free_nodes(ix->nodes, s);
+  DevMem::free(ix->sep_key, s);
+  DevMem::free(ix->sep_id, s);
+  ix->nodes = na;
+  ix->sep_key = nsk;
+  ix->sep_id = nsi;
+  ix->L = Lnew;
+  ix->n += m;
+  ix->pool_used = base_block + NB;
+  if ((st = build_spac_summary(ix, s))) return st;
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
+}
+
+psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, int64_t *d_deleted,
+                       cudaStream_t s) {
+  psi_status st;
+  Batch b;
+  if ((st = sort_batch(ix, pts, ids, m, s, b))) return st;
+  const int64_t L = ix->L;
+  Buf<int32_t> bleaf, sbeg, send, keep;
+  Buf<int64_t> pos, tot;
+  Buf<unsigned long long> del;
+  if ((st = bleaf.alloc(m, s)) || (st = sbeg.alloc(L, s)) || (st = send.alloc(L, s)) || (st = keep.alloc(L, s)) ||
+      (st = pos.alloc(L, s)) || (st = tot.alloc(2, s)) || (st = del.alloc(1, s)))
+    return st;
+  PSI_CK(cudaMemsetAsync(sbeg.p, 0, sizeof(int32_t) * L, s));
+  PSI_CK(cudaMemsetAsync(send.p, 0, sizeof(int32_t) * L, s));
+  PSI_CK(cudaMemsetAsync(del.p, 0, sizeof(unsigned long long), s));
+  PSI_LAUNCH(k_locate, grid_for(m), 256, 0, s, b.keys, b.vals, ids, m, ix->sep_key, ix->sep_id, L, bleaf.p);
+  PSI_LAUNCH(k_slices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p);
+  Leaves lv = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<2>, warp_grid(L), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+                     b.keys, b.vals, pts, ids, del.p);
+  else
+    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<3>, warp_grid(L), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+                     b.keys, b.vals, pts, ids, del.p);
+  PSI_LAUNCH(k_nonempty, grid_for(L), 256, 0, s, ix->nodes.cnt, L, keep.p);
+  if ((st = scan_i32_to_i64(keep.p, pos.p, L, tot.p, s))) return st;
+  PSI_LAUNCH(k_copy_i64, 1, 1, 0, s, del.p, tot.p + 1);
+  if (d_deleted) PSI_CK(cudaMemcpyAsync(d_deleted, tot.p + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  int64_t h[2];
+  PSI_CK(cudaMemcpyAsync(h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  const int64_t Lnew = h[0];
+  NodeArrays na;
+  uint64_t *nsk = nullptr;
+  uint32_t *nsi = nullptr;
+  if ((st = alloc_nodes(na, ix->D, summary_capacity(Lnew, ix->F), false, s)) ||
+      (st = DevMem::alloc((void **)&nsk, sizeof(uint64_t) * std::max<int64_t>(Lnew, 1), s)) ||
+      (st = DevMem::alloc((void **)&nsi, sizeof(uint32_t) * std::max<int64_t>(Lnew, 1), s))) {
+    free_nodes(na, s);
+    DevMem::free(nsk, s);
+    DevMem::free(nsi, s);
+    return st;
+  }
+  Leaves nl = leaves_of(na, nsk, nsi);
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_compact_leaves", k_compact_leaves<2>, grid_for(L), 256, 0, s, lv, nl, keep.p, pos.p, L);
+  else
+    PSI_LAUNCH_NAMED("k_compact_leaves", k_compact_leaves<3>, grid_for(L), 256, 0, s, lv, nl, keep.p, pos.p, L);
+  free_nodes(ix->nodes, s);
+  DevMem::free(ix->sep_key, s);
+  DevMem::free(ix->sep_id, s);
+  ix->nodes = na;
+  ix->sep_key = nsk;
+  ix->sep_id = nsi;
+  ix->L = Lnew;
+  ix->n -= h[1];
+  if ((st = build_spac_summary(ix, s))) return st;
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
+}
+
+}  // namespace psi

@@ -1,0 +1,288 @@
+"""Thin Python binding of the C ABI in include/psi.h.
+
+Argument marshalling only: every step of build, update and query runs in the
+CUDA library (_build/libpsi.so).  PyTorch provides device memory (tensors) and
+streams.  There is no CPU fallback: if the library is missing, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+SPAC_Z, SPAC_H, PORTH = 0, 1, 2
+KINDS = {"spac_z": SPAC_Z, "spac_h": SPAC_H, "porth": PORTH}
+REPORT_SORTED = 1
+
+OK, ERR_INVALID, ERR_RANGE, ERR_OOM, ERR_CAPACITY, ERR_DEVICE_TIMEOUT, ERR_CUDA = range(7)
+_STATUS = {1: "PSI_ERR_INVALID", 2: "PSI_ERR_RANGE", 3: "PSI_ERR_OOM", 4: "PSI_ERR_CAPACITY",
+           5: "PSI_ERR_DEVICE_TIMEOUT", 6: "PSI_ERR_CUDA"}
+
+
+class PsiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("kind", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("coord_bits", ctypes.c_int32), ("fanout", ctypes.c_int32), ("radix_bits", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
+        L = ctypes.CDLL(_build.LIB)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        st = ctypes.c_int
+        sig = {
+            "psi_build": (st, [P, P, P, i64, P, P]),
+            "psi_insert_batch": (st, [P, P, P, i64, P]),
+            "psi_delete_batch": (st, [P, P, P, i64, P, P]),
+            "psi_knn": (st, [P, P, i64, i32, P, P, P]),
+            "psi_range_count": (st, [P, P, i64, P, P]),
+            "psi_range_report": (st, [P, P, i64, P, P, i64, P, i32, P]),
+            "psi_sync": (st, [P, P]),
+            "psi_destroy": (st, [P]),
+            "psi_size": (i64, [P]),
+            "psi_num_leaves": (i64, [P]),
+            "psi_num_nodes": (i64, [P]),
+            "psi_last_error": (ctypes.c_char_p, []),
+            "psi_export_leaves": (st, [P, P, P, P, P, P, P]),
+            "psi_export_points": (st, [P, P, P, P, P, P]),
+            "psi_export_nodes": (st, [P, P, P, P, P, P, P, P]),
+            "psi_encode": (st, [P, P, i64, P, P]),
+            "psi_sort_pairs": (st, [P, P, i64, i32, P]),
+            "psi_launch_count": (i64, []),
+            "psi_profile_enable": (None, [ctypes.c_int]),
+            "psi_profile_reset": (None, []),
+            "psi_profile_read": (ctypes.c_int, [ctypes.c_char_p, P, P]),
+            "psi_profile_dump": (ctypes.c_int, [ctypes.c_char_p, i64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise PsiError(status, lib().psi_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _u32(t: torch.Tensor) -> torch.Tensor:
+    """4-byte integer tensor viewed for the ABI (uint32 bit pattern)."""
+    if t.element_size() != 4:
+        raise ValueError("ids must be a 4-byte integer tensor")
+    return t
+
+
+class Index:
+    """A device-resident spatial index (SPaC-Z, SPaC-H or P-Orth)."""
+
+    def __init__(self, pts: torch.Tensor, ids: torch.Tensor, *, kind: int | str = SPAC_Z, leaf_size: int = 32,
+                 coord_bits: int | None = None, fanout: int = 32, stream=None):
+        if isinstance(kind, str):
+            kind = KINDS[kind]
+        dim = int(pts.shape[1]) if pts.dim() == 2 else 2
+        if coord_bits is None:
+            coord_bits = 30 if dim == 2 else 21
+        self.dim, self.kind, self.leaf_size, self.coord_bits, self.fanout = dim, kind, leaf_size, coord_bits, fanout
+        self.cfg = Config(dim, kind, leaf_size, coord_bits, fanout, 0)
+        h = ctypes.c_void_p()
+        pts = pts.contiguous()
+        ids = _u32(ids).contiguous()
+        _check(lib().psi_build(ctypes.byref(self.cfg), _ptr(pts), _ptr(ids), int(pts.shape[0]), _stream(stream),
+                               ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self) -> int:
+        return int(lib().psi_size(self._h))
+
+    @property
+    def num_leaves(self) -> int:
+        return int(lib().psi_num_leaves(self._h))
+
+    @property
+    def num_nodes(self) -> int:
+        return int(lib().psi_num_nodes(self._h))
+
+    def sync(self, stream=None):
+        _check(lib().psi_sync(self._h, _stream(stream)))
+
+    def insert(self, pts: torch.Tensor, ids: torch.Tensor, stream=None):
+        pts, ids = pts.contiguous(), _u32(ids).contiguous()
+        _check(lib().psi_insert_batch(self._h, _ptr(pts), _ptr(ids), int(pts.shape[0]), _stream(stream)))
+
+    def delete(self, pts: torch.Tensor, ids: torch.Tensor, num_deleted: torch.Tensor | None = None, stream=None):
+        pts, ids = pts.contiguous(), _u32(ids).contiguous()
+        _check(lib().psi_delete_batch(self._h, _ptr(pts), _ptr(ids), int(pts.shape[0]), _ptr(num_deleted),
+                                      _stream(stream)))
+
+    def knn(self, q: torch.Tensor, k: int, out_ids: torch.Tensor | None = None, out_d2: torch.Tensor | None = None,
+            stream=None):
+        q = q.contiguous()
+        nq = int(q.shape[0])
+        if out_ids is None:
+            out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        if out_d2 is None:
+            out_d2 = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        _check(lib().psi_knn(self._h, _ptr(q), nq, k, _ptr(out_ids), _ptr(out_d2), _stream(stream)))
+        return out_ids, out_d2
+
+    def range_count(self, boxes: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        boxes = boxes.contiguous()
+        nq = int(boxes.shape[0])
+        if out is None:
+            out = torch.empty(nq, dtype=torch.int64, device=boxes.device)
+        _check(lib().psi_range_count(self._h, _ptr(boxes), nq, _ptr(out), _stream(stream)))
+        return out
+
+    def range_report(self, boxes: torch.Tensor, capacity: int | None = None, sort: bool = False, stream=None):
+        """(offsets[q+1], ids[total]); grows the output once if capacity is too small."""
+        boxes = boxes.contiguous()
+        nq = int(boxes.shape[0])
+        off = torch.empty(nq + 1, dtype=torch.int64, device=boxes.device)
+        cap = capacity if capacity is not None else max(1024, 64 * nq)
+        total = ctypes.c_int64(0)
+        for _ in range(2):
+            ids = torch.empty(max(cap, 1), dtype=torch.int32, device=boxes.device)
+            st = lib().psi_range_report(self._h, _ptr(boxes), nq, _ptr(off), _ptr(ids), cap, ctypes.byref(total),
+                                        REPORT_SORTED if sort else 0, _stream(stream))
+            if st == ERR_CAPACITY:
+                cap = int(total.value)
+                continue
+            _check(st)
+            return off, ids[:total.value]
+        _check(st)
+
+    # ---- inspection ----
+    def leaves(self, stream=None):
+        L, D = self.num_leaves, self.dim
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cnt = torch.empty(L, dtype=torch.int32, device=dev)
+        lo = torch.empty((L, D), dtype=torch.int32, device=dev)
+        hi = torch.empty((L, D), dtype=torch.int32, device=dev)
+        sk = torch.empty(L, dtype=torch.int64, device=dev)
+        si = torch.empty(L, dtype=torch.int32, device=dev)
+        if L:
+            _check(lib().psi_export_leaves(self._h, _ptr(cnt), _ptr(lo), _ptr(hi), _ptr(sk), _ptr(si),
+                                           _stream(stream)))
+        return {"count": cnt, "lo": lo, "hi": hi, "sep_key": sk, "sep_id": si}
+
+    def points(self, stream=None):
+        n, D = len(self), self.dim
+        dev = torch.device("cuda", torch.cuda.current_device())
+        pts = torch.empty((n, D), dtype=torch.int32, device=dev)
+        ids = torch.empty(n, dtype=torch.int32, device=dev)
+        keys = torch.empty(n, dtype=torch.int64, device=dev)
+        leaf = torch.empty(n, dtype=torch.int32, device=dev)
+        if n:
+            _check(lib().psi_export_points(self._h, _ptr(pts), _ptr(ids), _ptr(keys), _ptr(leaf), _stream(stream)))
+        return {"pts": pts, "ids": ids, "keys": keys, "leaf": leaf}
+
+    def nodes(self, stream=None):
+        N, D = self.num_nodes, self.dim
+        dev = torch.device("cuda", torch.cuda.current_device())
+        depth = torch.empty(N, dtype=torch.int32, device=dev)
+        prefix = torch.empty(N, dtype=torch.int64, device=dev)
+        cnt = torch.empty(N, dtype=torch.int64, device=dev)
+        lo = torch.empty((N, D), dtype=torch.int32, device=dev)
+        hi = torch.empty((N, D), dtype=torch.int32, device=dev)
+        leaf = torch.empty(N, dtype=torch.int32, device=dev)
+        if N:
+            _check(lib().psi_export_nodes(self._h, _ptr(depth), _ptr(prefix), _ptr(cnt), _ptr(lo), _ptr(hi),
+                                          _ptr(leaf), _stream(stream)))
+        return {"depth": depth, "prefix": prefix, "count": cnt, "lo": lo, "hi": hi, "is_leaf": leaf}
+
+
+def encode(pts: torch.Tensor, kind: int | str = SPAC_Z, coord_bits: int | None = None, stream=None) -> torch.Tensor:
+    if isinstance(kind, str):
+        kind = KINDS[kind]
+    dim = int(pts.shape[1])
+    coord_bits = coord_bits or (30 if dim == 2 else 21)
+    cfg = Config(dim, kind, 32, coord_bits, 32, 0)
+    pts = pts.contiguous()
+    keys = torch.empty(pts.shape[0], dtype=torch.int64, device=pts.device)
+    _check(lib().psi_encode(ctypes.byref(cfg), _ptr(pts), int(pts.shape[0]), _ptr(keys), _stream(stream)))
+    return keys
+
+
+def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 64, stream=None):
+    """In-place stable sort of (uint64 key, uint32 value) pairs by key."""
+    _check(lib().psi_sort_pairs(_ptr(keys), _ptr(vals), int(keys.shape[0]), key_bits, _stream(stream)))
+    return keys, vals
+
+
+def launch_count() -> int:
+    return int(lib().psi_launch_count())
+
+
+def profile_enable(on: bool = True):
+    lib().psi_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().psi_profile_reset()
+
+
+def profile_read(name: str):
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0)
+    lib().psi_profile_read(name.encode(), ctypes.byref(n), ctypes.byref(ms))
+    return int(n.value), float(ms.value)
+
+
+def profile_dump() -> dict:
+    size = lib().psi_profile_dump(None, 0)
+    buf = ctypes.create_string_buffer(size + 1)
+    lib().psi_profile_dump(buf, size + 1)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.rsplit(" ", 2)
+        out[name] = (int(cnt), float(ms))
+    return out

@@ -1,0 +1,352 @@
+"""GPU vs oracle parity: every step of the path through the C ABI, compared
+element by element with the oracle on the same seeded inputs.  All arithmetic
+is integer, so the bar is bit-exact equality everywhere."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2601_05347_gb300 import gen  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2601_05347_gb300 import psi
+DEV = "cuda"
+KIND = {"spac_z": O.SPAC_Z, "spac_h": O.SPAC_H, "porth": O.PORTH}
+
+
+def T(a):
+    """numpy -> device tensor (uint32 travels as int32 bits)."""
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).to(DEV)
+
+
+def U32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def U64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def points(n, dim, bits, seed, dup=False, clustered=False):
+    if clustered:
+        p = gen.varden(n, dim, bits, seed)
+    else:
+        p = gen.uniform(n, dim, bits, seed)
+    if dup and n:
+        p = (p >> (bits - 6)).astype(np.int32)  # 64 values per axis: many duplicate points
+    # unique ids in shuffled order: an odd multiplier is a bijection mod 2^32
+    perm = np.argsort(gen.splitmix64(seed ^ 77, np.arange(n, dtype=np.uint64)), kind="stable").astype(np.uint64)
+    with np.errstate(over="ignore"):
+        ids = (perm * np.uint64(2654435761) + np.uint64(12345)) & np.uint64(0xFFFFFFFF)
+    return p, ids.astype(np.uint32)
+
+
+# ---------------------------------------------------------------- keys, sort
+
+@pytest.mark.parametrize("dim,bits,kind", [(2, 30, "spac_z"), (2, 30, "spac_h"), (3, 21, "spac_z"), (2, 31, "spac_h"),
+                                           (2, 7, "spac_h"), (2, 1, "spac_h"), (3, 5, "porth"), (2, 31, "spac_z")])
+def test_encode_matches_oracle(dim, bits, kind):
+    p = gen.uniform(5000, dim, bits, 3)
+    p[:4] = 0
+    p[4:8] = (1 << bits) - 1
+    got = U64(psi.encode(T(p), kind, bits))
+    want = O.keys(p, dim, KIND[kind], bits)
+    assert (got == want).all()
+
+
+def test_encode_rejects_out_of_range():
+    p = np.array([[0, 0], [1 << 30, 5]], np.int32)
+    with pytest.raises(psi.PsiError) as e:
+        psi.encode(T(p), "spac_z", 30)
+    assert e.value.status == psi.ERR_RANGE
+
+
+@pytest.mark.parametrize("n,bits", [(1, 64), (4095, 60), (4096, 60), (4097, 60), (100003, 64), (250000, 23)])
+def test_sort_pairs_is_stable_sort(n, bits):
+    k = gen.splitmix64(n, np.arange(n, dtype=np.uint64)) >> np.uint64(64 - bits)
+    k[: n // 3] = k[n // 3: 2 * (n // 3)]  # duplicates
+    v = np.arange(n, dtype=np.uint32)
+    kt, vt = T(k), T(v)
+    psi.sort_pairs(kt, vt, bits)
+    order = np.argsort(k, kind="stable")
+    assert (U64(kt) == k[order]).all()
+    assert (U32(vt) == v[order]).all()
+
+
+# ---------------------------------------------------------------- build layout
+
+def check_spac_layout(ix, o):
+    lv = o.levels()
+    gl = ix.leaves()
+    assert ix.num_leaves == len(lv[0]["count"]) if lv else ix.num_leaves == 0
+    if not lv:
+        return
+    assert (gl["count"].cpu().numpy() == lv[0]["count"]).all()
+    assert (gl["lo"].cpu().numpy() == lv[0]["lo"]).all()
+    assert (gl["hi"].cpu().numpy() == lv[0]["hi"]).all()
+    assert (U64(gl["sep_key"]) == lv[0]["first_key"]).all()
+    assert (U32(gl["sep_id"]) == lv[0]["first_id"]).all()
+    # points: leaf by leaf the same sets as the oracle's canonical leaves
+    gp = ix.points()
+    gk, gi, gpts = U64(gp["keys"]), U32(gp["ids"]), gp["pts"].cpu().numpy()
+    ok, oi, opts = o.points()
+    leaf = gp["leaf"].cpu().numpy()
+    order = np.lexsort((gi, gk, leaf))
+    assert (gk[order] == ok).all() and (gi[order] == oi).all() and (gpts[order] == opts).all()
+    # summary levels, stored after the leaves
+    nd = ix.nodes()
+    depth = nd["depth"].cpu().numpy()
+    for l, want in enumerate(lv):
+        sel = depth == l
+        assert sel.sum() == len(want["count"])
+        assert (nd["count"].cpu().numpy()[sel] == want["count"]).all()
+        assert (nd["lo"].cpu().numpy()[sel] == want["lo"]).all()
+        assert (nd["hi"].cpu().numpy()[sel] == want["hi"]).all()
+
+
+@pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
+@pytest.mark.parametrize("n,phi,fanout", [(0, 32, 32), (1, 32, 32), (31, 32, 32), (32, 32, 32), (33, 32, 32),
+                                          (5000, 16, 8), (100003, 32, 32), (70001, 64, 32), (20000, 1, 2)])
+def test_spac_build_layout(kind, n, phi, fanout):
+    p, ids = points(n, 2, 30, 11 + n, clustered=n % 2 == 1)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=phi, fanout=fanout)
+    ix.sync()
+    o = O.Index(p, ids, kind=KIND[kind], phi=phi, fanout=fanout)
+    assert len(ix) == n
+    check_spac_layout(ix, o)
+
+
+@pytest.mark.parametrize("dup", [False, True])
+def test_spac_build_layout_3d_and_duplicates(dup):
+    p, ids = points(60000, 3, 21, 5, dup=dup)
+    ix = psi.Index(T(p), T(ids), kind="spac_z", leaf_size=32, coord_bits=21)
+    o = O.Index(p, ids, dim=3, kind=O.SPAC_Z, phi=32, bits=21)
+    check_spac_layout(ix, o)
+
+
+def test_duplicate_pile_longer_than_a_tile():
+    # 9000 copies of one point: equal keys must come out in id order
+    p = np.zeros((9000, 2), np.int32) + 12345
+    ids = np.random.default_rng(0).permutation(9000).astype(np.uint32) * 5
+    ix = psi.Index(T(p), T(ids), kind="spac_z", leaf_size=32)
+    check_spac_layout(ix, O.Index(p, ids, phi=32))
+
+
+def test_build_rejects_out_of_range_coordinates():
+    p = np.array([[0, 0], [1, (1 << 30) + 4]], np.int32)
+    ix = psi.Index(T(p), T(np.arange(2, dtype=np.uint32)), kind="spac_z", coord_bits=30)
+    with pytest.raises(psi.PsiError) as e:
+        ix.sync()
+    assert e.value.status == psi.ERR_RANGE
+
+
+# ---------------------------------------------------------------- queries
+
+def query_points(nq, dim, bits, seed, data):
+    q = gen.uniform(nq, dim, bits, seed)
+    if len(data):
+        take = gen.sample_with_replacement(len(data), nq // 3, seed + 1)
+        q[: nq // 3] = data[take]
+    return q
+
+
+@pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("spac_z", 3, 21),
+                                           ("porth", 3, 21)])
+@pytest.mark.parametrize("k", [1, 10, 32, 33, 100, 128])
+def test_knn_matches_oracle(kind, dim, bits, k):
+    n = 30000
+    p, ids = points(n, dim, bits, 21 + k, clustered=k % 2 == 0)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
+    q = query_points(5000, dim, bits, k, p)  # >= 4096: exercises the curve-sorted query order
+    gi, gd = ix.knn(T(q), k)
+    oi, od = o.knn(q, k)
+    assert (U32(gi) == oi).all()
+    assert (gd.cpu().numpy() == od).all()
+
+
+@pytest.mark.parametrize("n", [0, 1, 7, 40])
+def test_knn_small_and_k_beyond_size(n):
+    p, ids = points(n, 2, 30, 3)
+    ix = psi.Index(T(p), T(ids), kind="spac_h", leaf_size=4, fanout=2)
+    q = query_points(50, 2, 30, 5, p)
+    gi, gd = ix.knn(T(q), 64)
+    oi, od = O.knn_brute_raw(p.reshape(-1, 2), ids, q, 64)
+    assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+def test_knn_ties_by_id():
+    # every point at the same distance from the query
+    p = np.array([[10, 0], [0, 10], [20, 10], [10, 20]] * 50, np.int32)
+    p[4:] += np.repeat(np.arange(1, 50), 4)[:, None].astype(np.int32) * 1000
+    ids = np.random.default_rng(1).permutation(200).astype(np.uint32)
+    ix = psi.Index(T(p), T(ids), kind="spac_z", leaf_size=2, fanout=2)
+    gi, gd = ix.knn(T(np.array([[10, 10]], np.int32)), 4)
+    want = sorted(ids[:4].tolist())
+    assert U32(gi)[0].tolist() == want and gd.cpu().tolist()[0] == [100] * 4
+
+
+@pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("porth", 3, 21)])
+def test_range_count_and_report_match_oracle(kind, dim, bits):
+    n = 40000
+    p, ids = points(n, dim, bits, 31, clustered=True)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
+    nq = 700
+    centres = p[gen.sample_with_replacement(n, nq, 4)].astype(np.int64)
+    half = np.int64(1) << np.int64(bits - 7)
+    boxes = gen.centred_boxes(centres, int(half), bits)
+    boxes[0, :dim], boxes[0, dim:] = 0, (1 << bits) - 1     # everything
+    boxes[1, :dim], boxes[1, dim:] = p[5], p[5]             # a point
+    boxes[2, :dim], boxes[2, dim:] = 9, 8                   # empty (lo > hi)
+    gc = ix.range_count(T(boxes)).cpu().numpy()
+    oc = o.range_count(boxes)
+    assert (gc == oc).all()
+    off, rid = ix.range_report(T(boxes), sort=True)
+    ooff, orid = o.range_report(boxes)
+    assert (off.cpu().numpy() == ooff).all()
+    assert (U32(rid) == orid).all()
+    # unsorted report: same sets
+    off2, rid2 = ix.range_report(T(boxes), capacity=10)  # forces the capacity retry path
+    r2 = U32(rid2)
+    for t in range(0, nq, 37):
+        a, b = ooff[t], ooff[t + 1]
+        assert sorted(r2[a:b].tolist()) == orid[a:b].tolist()
+
+
+# ---------------------------------------------------------------- updates
+
+def spac_invariants(ix):
+    gl = ix.leaves()
+    gp = ix.points()
+    leaf = gp["leaf"].cpu().numpy()
+    keys, ids, pts = U64(gp["keys"]), U32(gp["ids"]), gp["pts"].cpu().numpy()
+    cnt = gl["count"].cpu().numpy()
+    assert (cnt > 0).all() and (cnt <= 2 * ix.leaf_size).all()
+    assert np.bincount(leaf, minlength=len(cnt)).tolist() == cnt.tolist()
+    lo, hi = gl["lo"].cpu().numpy(), gl["hi"].cpu().numpy()
+    for d in range(ix.dim):
+        mn = np.full(len(cnt), np.iinfo(np.int32).max)
+        mx = np.full(len(cnt), np.iinfo(np.int32).min)
+        np.minimum.at(mn, leaf, pts[:, d])
+        np.maximum.at(mx, leaf, pts[:, d])
+        assert (mn == lo[:, d]).all() and (mx == hi[:, d]).all()  # tight boxes
+    # every point lies in its leaf's (key, id) range [sep_j, sep_{j+1})
+    sk, si = U64(gl["sep_key"]), U32(gl["sep_id"])
+    pair = keys.astype(object) * (1 << 32) + ids.astype(object)
+    sep = sk.astype(object) * (1 << 32) + si.astype(object)
+    nxt = np.append(sep[1:], np.array([1 << 100], dtype=object))
+    assert all(sep[1:] > sep[:-1])
+    assert all((pair < nxt[leaf]) & ((pair >= sep[leaf]) | (leaf == 0)))
+
+
+@pytest.mark.parametrize("kind", ["spac_z", "spac_h", "porth"])
+def test_updates_match_oracle(kind):
+    n = 50000
+    p, ids = points(n, 2, 30, 41, clustered=True)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32)
+    o = O.Index(p, ids, kind=KIND[kind], phi=32)
+    live_p, live_i = p, ids
+    rng_seed = 5
+    for step, (m_ins, m_del, ood) in enumerate([(5000, 3000, False), (20000, 1000, True), (100, 30000, False),
+                                                (60000, 0, True), (0, 50000, False)]):
+        newp = gen.varden(m_ins, 2, 30, 1000 + step, x_range=(1 << 29, 1 << 30) if ood else None)
+        newi = (np.arange(m_ins, dtype=np.uint32) + 10_000_000 * (step + 1)).astype(np.uint32)
+        ix.insert(T(newp), T(newi))
+        o.insert(newp, newi)
+        live_p = np.concatenate([live_p, newp])
+        live_i = np.concatenate([live_i, newi])
+        sel = gen.sample_without_replacement(len(live_i), min(m_del, len(live_i)), rng_seed + step)
+        dp = np.concatenate([live_p[sel], [[3, 4]]]).astype(np.int32)   # plus one absent point
+        di = np.concatenate([live_i[sel], [live_i[0]]]).astype(np.uint32)
+        nd = torch.zeros(1, dtype=torch.int64, device=DEV)
+        ix.delete(T(dp), T(di), nd)
+        got_del = int(nd.item())
+        want_del = o.delete(dp, di)
+        assert got_del == want_del == len(sel)
+        keep = np.ones(len(live_i), bool)
+        keep[sel] = False
+        live_p, live_i = live_p[keep], live_i[keep]
+        ix.sync()
+        assert len(ix) == len(o) == len(live_i)
+        # point sets
+        gp = ix.points()
+        ok, oi, op = o.points()
+        gi = U32(gp["ids"])
+        order = np.argsort(gi)
+        oorder = np.argsort(oi)
+        assert (gi[order] == oi[oorder]).all()
+        assert (gp["pts"].cpu().numpy()[order] == op[oorder]).all()
+        if kind != "porth" and len(live_i):
+            spac_invariants(ix)
+        # queries
+        q = query_points(3000, 2, 30, 7 + step, live_p)
+        gi, gd = ix.knn(T(q), 10)
+        oi2, od2 = o.knn(q, 10)
+        assert (U32(gi) == oi2).all() and (gd.cpu().numpy() == od2).all()
+        boxes = gen.square_boxes(300, 2, 30, 1 << 23, 9 + step)
+        assert (ix.range_count(T(boxes)).cpu().numpy() == o.range_count(boxes)).all()
+        if kind == "porth":
+            check_porth_nodes(ix, o)
+
+
+def test_insert_into_empty_and_delete_everything():
+    ix = psi.Index(T(np.zeros((0, 2), np.int32)), T(np.zeros(0, np.uint32)), kind="spac_h")
+    p, ids = points(3000, 2, 30, 8)
+    ix.insert(T(p), T(ids))
+    o = O.Index(p, ids, kind=O.SPAC_H)
+    check_spac_layout(ix, o)
+    ix.delete(T(p), T(ids))
+    ix.sync()
+    assert len(ix) == 0 and ix.num_leaves == 0
+    gi, gd = ix.knn(T(p[:5]), 3)
+    assert (U32(gi) == 0xFFFFFFFF).all()
+
+
+# ---------------------------------------------------------------- P-Orth
+
+def check_porth_nodes(ix, o):
+    want = o.porth()
+    nd = ix.nodes()
+    D, bits = ix.dim, ix.coord_bits
+    depth = nd["depth"].cpu().numpy()
+    prefix = U64(nd["prefix"])
+    start = np.array([int(pr) << (D * (bits - int(dd))) for pr, dd in zip(prefix, depth)], dtype=object)
+    order = sorted(range(len(depth)), key=lambda i: (start[i], depth[i]))
+    assert len(order) == len(want["depth"])
+    o_ = np.array(order, dtype=np.int64)
+    assert (depth[o_] == want["depth"]).all()
+    assert (prefix[o_] == want["prefix"]).all()
+    assert (nd["count"].cpu().numpy()[o_] == want["count"]).all()
+    assert (nd["lo"].cpu().numpy()[o_] == want["lo"]).all()
+    assert (nd["hi"].cpu().numpy()[o_] == want["hi"]).all()
+    assert (nd["is_leaf"].cpu().numpy()[o_] == want["is_leaf"]).all()
+
+
+@pytest.mark.parametrize("dim,bits,phi,clustered,dup", [(2, 30, 32, False, False), (2, 30, 32, True, False),
+                                                        (2, 30, 8, True, True), (3, 21, 32, True, False),
+                                                        (3, 21, 16, False, True), (2, 10, 4, False, False)])
+def test_porth_build_matches_oracle(dim, bits, phi, clustered, dup):
+    p, ids = points(40000, dim, bits, 51 + phi, dup=dup, clustered=clustered)
+    ix = psi.Index(T(p), T(ids), kind="porth", leaf_size=phi, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=O.PORTH, phi=phi, bits=bits)
+    check_porth_nodes(ix, o)
+
+
+def test_porth_tiny():
+    for n in (0, 1, 2, 33):
+        p, ids = points(n, 2, 30, 3 + n)
+        ix = psi.Index(T(p), T(ids), kind="porth", leaf_size=32)
+        o = O.Index(p, ids, kind=O.PORTH, phi=32)
+        if n:
+            check_porth_nodes(ix, o)
+        else:
+            assert ix.num_nodes == 0

@@ -165,3 +165,16 @@ def test_generator_workload_runs():
     i, d = ix.knn(p[:20], 10)
     ni, nd = np_knn(p, np.arange(3000, dtype=np.uint32), p[:20], 10)
     assert (i == ni).all() and (d == nd).all()
+
+
+def test_raw_brute_force_matches_numpy():
+    rng = np.random.default_rng(12)
+    pts = rng.integers(0, 1 << 30, size=(800, 2)).astype(np.int32)
+    ids = (rng.permutation(800) * 7 + 1).astype(np.uint32)
+    q = rng.integers(0, 1 << 30, size=(20, 2)).astype(np.int32)
+    oi, od = O.knn_brute_raw(pts, ids, q, 9)
+    ni, nd = np_knn(pts, ids, q, 9)
+    assert (oi == ni).all() and (od == nd).all()
+    boxes = np.concatenate([q, q + (1 << 27)], axis=1).astype(np.int32)
+    c = O.range_count_brute_raw(pts, boxes)
+    assert c.tolist() == [int(np_inbox(pts, b).sum()) for b in boxes]
