@@ -35,7 +35,10 @@ METRIC = "build/update Mpts/s, kNN & range queries/s at 1e8 2D pts; served p50/p
 BITS = 30
 
 
-def workload(small: bool):
+def workload(small: bool, n: int | None = None):
+    if n:
+        return dict(name=f"2D clustered (Varden), n={n:.0e}, SPaC-H", n=n, m_ins=max(1, n // 100),
+                    m_del=max(1, n // 100), n_knn=max(1, n // 10), k=10, n_box=max(1, n // 2000), box_target=1000)
     if small:
         return dict(name="2D clustered (Varden), n=1e6, SPaC-H", n=1_000_000, m_ins=10_000, m_del=10_000,
                     n_knn=100_000, k=10, n_box=5_000, box_target=1000)
@@ -157,7 +160,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2601_05347_gb300 import psi
 
-    w = workload(args.small)
+    w = workload(args.small, args.n)
     t0 = time.time()
     host = make_inputs(w, rank)
     gen_s = time.time() - t0
@@ -237,6 +240,13 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t[0])
         phase_ms = {p: float(t[i + 1]) for i, p in enumerate(phases)}
+
+    # traversal counters of one instrumented k-NN pass over the same queries
+    ixs = psi.Index(d["pts"], d["ids"], kind="spac_h", leaf_size=32)
+    ixs.insert(d["ins"], d["ins_ids"])
+    ixs.delete(d["del_pts"], d["del_ids"], ndel)
+    _, _, kstats = ixs.knn_stats(d["q"], k)
+    ixs.close()
 
     # e2e: the build metric through the public API from pinned host buffers,
     # H2D of the step's build inputs and D2H of a result inside the timed region
@@ -323,6 +333,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roof,
         "kernels": top,
+        "knn_traversal_per_query": {kk: round(v / max(kstats["queries"], 1), 3) for kk, v in kstats.items()
+                                    if kk != "queries"},
         "clocks": clk,
         "input_generation_s": round(gen_s, 1),
     }
@@ -392,7 +404,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.small)
+    w = workload(args.small, args.n)
     host = make_inputs(w, 0)
     frac = 0.01 if w["n"] >= 10_000_000 else 0.5
     for _ in range(args.warmup):
@@ -425,6 +437,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--small", action="store_true", help="1e6-point workload (quick check)")
+    ap.add_argument("--n", type=int, default=None, help="scaled workload with n points (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()

@@ -167,6 +167,12 @@ psi_status psi_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int32_t
 
 /* ---- Instrumentation ---------------------------------------------------- */
 
+/* psi_knn with traversal counters: d_stats (device, 4 x uint64) receives the
+ * number of internal nodes expanded, leaves scanned, points scanned and
+ * queries answered.  Same results as psi_knn; slower (atomic counters). */
+psi_status psi_knn_instrumented(const psi_index *ix, const int32_t *d_q, int64_t q, int32_t k, uint32_t *d_ids,
+                                int64_t *d_d2, uint64_t *d_stats, void *stream);
+
 /* Number of kernels this library has launched in the process. */
 int64_t psi_launch_count(void);
 

@@ -13,7 +13,7 @@
 namespace psi {
 
 psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uint32_t *out_id, int64_t *out_d2,
-                   cudaStream_t s);
+                   unsigned long long *d_stats, cudaStream_t s);
 psi_status run_range_count(const psi_index *ix, const int32_t *boxes, int64_t nq, int64_t *counts, cudaStream_t s);
 psi_status run_range_emit(const psi_index *ix, const int32_t *boxes, int64_t nq, const int64_t *offsets,
                           uint32_t *ids, bool sorted, cudaStream_t s);
@@ -297,7 +297,19 @@ psi_status psi_knn(const psi_index *ix, const int32_t *d_q, int64_t q, int32_t k
     set_error("at most 2^32 - 1 queries per call");
     return PSI_ERR_INVALID;
   }
-  return run_knn(ix, d_q, q, k, d_ids, d_d2, (cudaStream_t)stream);
+  return run_knn(ix, d_q, q, k, d_ids, d_d2, nullptr, (cudaStream_t)stream);
+}
+
+psi_status psi_knn_instrumented(const psi_index *ix, const int32_t *d_q, int64_t q, int32_t k, uint32_t *d_ids,
+                                int64_t *d_d2, uint64_t *d_stats, void *stream) {
+  g_err.clear();
+  if (!ix || q < 0 || k < 1 || k > 128 || !d_stats || (q > 0 && (!d_q || !d_ids || !d_d2))) {
+    set_error("invalid k-NN arguments (1 <= k <= 128)");
+    return PSI_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  PSI_CK(cudaMemsetAsync(d_stats, 0, 4 * sizeof(uint64_t), s));
+  return run_knn(ix, d_q, q, k, d_ids, d_d2, (unsigned long long *)d_stats, s);
 }
 
 psi_status psi_range_count(const psi_index *ix, const int32_t *d_boxes, int64_t q, int64_t *d_counts, void *stream) {

@@ -56,26 +56,6 @@ __device__ __forceinline__ bool pair_less(int64_t da, uint32_t ia, int64_t db, u
   return da < db || (da == db && ia < ib);
 }
 
-// Ascending warp sort of (key, val) pairs, one per lane.
-__device__ __forceinline__ void warp_sort_asc(int64_t &key, uint32_t &val) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int64_t ok = __shfl_xor_sync(0xFFFFFFFFu, key, j);
-      const uint32_t ov = __shfl_xor_sync(0xFFFFFFFFu, val, j);
-      const bool up = (lane & k) == 0;
-      const bool lower = (lane & j) == 0;
-      const bool take = (lower == up) ? pair_less(ok, ov, key, val) : pair_less(key, val, ok, ov);
-      if (take) {
-        key = ok;
-        val = ov;
-      }
-    }
-  }
-}
-
 struct KnnArgs {
   TreeView t;
   const int32_t *q;
@@ -182,13 +162,42 @@ __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, 
   }
 }
 
-template <int D, int KPL>
-__global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a) {
+// Monotone 32-bit image of a non-negative distance (float bits), used only to
+// choose a visiting order; pruning always compares exact int64 distances.
+__device__ __forceinline__ uint32_t order_key(int64_t md) { return __float_as_uint((float)md); }
+
+// Lane holding the smallest (select_max: largest) order key among the lanes of
+// `mask` (mask != 0).
+__device__ __forceinline__ int select_lane(uint32_t mask, int64_t md, bool select_max) {
+  const int lane = threadIdx.x & 31;
+  const bool in = (mask >> lane) & 1u;
+  uint32_t key = order_key(md);
+  if (select_max) {
+    const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, in ? key : 0u);
+    return __ffs(__ballot_sync(0xFFFFFFFFu, in && key == m)) - 1;
+  }
+  const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, in ? key : 0xFFFFFFFFu);
+  return __ffs(__ballot_sync(0xFFFFFFFFu, in && key == m)) - 1;
+}
+
+struct KnnStats {
+  unsigned long long *c;  // [0] internal nodes expanded, [1] leaves scanned, [2] points scanned, [3] queries
+};
+
+// One warp per query.
+//  1. Greedy descent: from the root, always into the child whose box is
+//     nearest, down to one leaf; scanning it gives a finite k-th distance.
+//  2. Depth-first traversal from the root pruned by the k-th distance: leaf
+//     children are scanned at once in increasing box distance; internal
+//     children are pushed farthest first so that the nearest is popped next.
+template <int D, int KPL, bool STATS>
+__global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
   __shared__ uint32_t s_node[QW][STACK];
   __shared__ int64_t s_md[QW][STACK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nw = (int64_t)gridDim.x * QW;
   const TreeView &t = a.t;
+  unsigned long long n_int = 0, n_leaf = 0, n_pts = 0;
   for (int64_t qi = (int64_t)blockIdx.x * QW + w; qi < a.nq; qi += nw) {
     const int64_t q = a.order ? (int64_t)a.order[qi] : qi;
     int32_t qc[D];
@@ -196,50 +205,100 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a) {
     for (int d = 0; d < D; ++d) qc[d] = a.q[q * D + d];
     KList<KPL> kl;
     kl.init();
-    int sp = 0;
     if (t.root >= 0) {
+      uint32_t node = (uint32_t)t.root;
+      for (int nk = t.kids[node]; nk > 0; nk = t.kids[node]) {
+        const uint32_t c0 = t.ref[node];
+        uint32_t best = 0xFFFFFFFFu;
+        uint32_t best_key = 0xFFFFFFFFu;
+        for (int cb = 0; cb < nk; cb += 32) {
+          int64_t md = INT64_MAX;
+          const uint32_t c = c0 + (uint32_t)(cb + lane);
+          if (cb + lane < nk && t.cnt[c] > 0) md = box_mindist<D>(t, c, qc);
+          const uint32_t key = cb + lane < nk && t.cnt[c] > 0 ? order_key(md) : 0xFFFFFFFFu;
+          const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, key);
+          if (m < best_key) {
+            best_key = m;
+            best = __shfl_sync(0xFFFFFFFFu, c, __ffs(__ballot_sync(0xFFFFFFFFu, key == m)) - 1);
+          }
+        }
+        if (STATS) ++n_int;
+        node = best;
+      }
+      const uint32_t first = node;
+      knn_scan_leaf<D, KPL>(t, first, qc, kl, a.k);
+      if (STATS) {
+        ++n_leaf;
+        n_pts += t.cnt[first];
+      }
+      int sp = 0;
       if (lane == 0) {
         s_node[w][0] = (uint32_t)t.root;
         s_md[w][0] = 0;
       }
       sp = 1;
-    }
-    __syncwarp();
-    while (sp > 0) {
-      --sp;
-      const uint32_t node = s_node[w][sp];
-      const int64_t md = s_md[w][sp];
       __syncwarp();
-      if (md > kl.kd) continue;
-      const int nk = t.kids[node];
-      if (nk == 0) {
-        knn_scan_leaf<D, KPL>(t, node, qc, kl, a.k);
-        continue;
-      }
-      const uint32_t c0 = t.ref[node];
-      for (int cb = 0; cb < nk; cb += 32) {
-        int64_t cmd = INT64_MAX;
-        uint32_t cn = 0xFFFFFFFFu;
-        if (cb + lane < nk) {
-          cn = c0 + (uint32_t)(cb + lane);
-          cmd = box_mindist<D>(t, cn, qc);
-          if (cmd > kl.kd || t.cnt[cn] == 0) {
-            cmd = INT64_MAX;
-            cn = 0xFFFFFFFFu;
-          }
-        }
-        warp_sort_asc(cmd, cn);
-        const int nok = __popc(__ballot_sync(0xFFFFFFFFu, cn != 0xFFFFFFFFu));
-        if (sp + nok > STACK) {
-          if (lane == 0) atomicOr(a.status, ST_STACK);
-          break;
-        }
-        if (lane < nok) {
-          s_node[w][sp + nok - 1 - lane] = cn;
-          s_md[w][sp + nok - 1 - lane] = cmd;
-        }
-        sp += nok;
+      while (sp > 0) {
+        --sp;
+        const uint32_t nd = s_node[w][sp];
+        const int64_t md = s_md[w][sp];
         __syncwarp();
+        if (md > kl.kd) continue;
+        const int nk = t.kids[nd];
+        if (nk == 0) {
+          if (nd != first) {
+            knn_scan_leaf<D, KPL>(t, nd, qc, kl, a.k);
+            if (STATS) {
+              ++n_leaf;
+              n_pts += t.cnt[nd];
+            }
+          }
+          continue;
+        }
+        if (STATS) ++n_int;
+        const uint32_t c0 = t.ref[nd];
+        for (int cb = 0; cb < nk; cb += 32) {
+          const bool valid = cb + lane < nk;
+          const uint32_t c = c0 + (uint32_t)(cb + lane);
+          int64_t cmd = INT64_MAX;
+          bool leafc = false;
+          if (valid && t.cnt[c] > 0) {
+            cmd = box_mindist<D>(t, c, qc);
+            leafc = t.kids[c] == 0;
+          }
+          // leaf children now, nearest first
+          uint32_t lm = __ballot_sync(0xFFFFFFFFu, leafc && cmd <= kl.kd);
+          while (lm) {
+            const int src = select_lane(lm, cmd, false);
+            const int64_t smd = __shfl_sync(0xFFFFFFFFu, cmd, src);
+            if (smd > kl.kd) break;
+            const uint32_t leaf = __shfl_sync(0xFFFFFFFFu, c, src);
+            if (leaf != first) {
+              knn_scan_leaf<D, KPL>(t, leaf, qc, kl, a.k);
+              if (STATS) {
+                ++n_leaf;
+                n_pts += t.cnt[leaf];
+              }
+            }
+            lm &= ~(1u << src);
+          }
+          // internal children, pushed farthest first
+          uint32_t im = __ballot_sync(0xFFFFFFFFu, valid && !leafc && cmd <= kl.kd);
+          if (sp + __popc(im) > STACK) {
+            if (lane == 0) atomicOr(a.status, ST_STACK);
+            im = 0;
+          }
+          while (im) {
+            const int src = __popc(im) == 1 ? __ffs(im) - 1 : select_lane(im, cmd, true);
+            if (lane == src) {
+              s_node[w][sp] = c;
+              s_md[w][sp] = cmd;
+            }
+            ++sp;
+            im &= ~(1u << src);
+          }
+          __syncwarp();
+        }
       }
     }
 #pragma unroll
@@ -250,6 +309,12 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a) {
         a.out_d2[q * a.k + e] = kl.d[r];
       }
     }
+    if (STATS && lane == 0) atomicAdd(&stats.c[3], 1ull);
+  }
+  if (STATS && lane == 0) {
+    atomicAdd(&stats.c[0], n_int);
+    atomicAdd(&stats.c[1], n_leaf);
+    atomicAdd(&stats.c[2], n_pts);
   }
 }
 
@@ -413,16 +478,23 @@ psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, Buf<ui
 }
 
 psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uint32_t *out_id, int64_t *out_d2,
-                   cudaStream_t s) {
+                   unsigned long long *d_stats, cudaStream_t s) {
   if (nq == 0) return PSI_OK;
   Buf<uint32_t> ob;
   uint32_t *order = nullptr;
   psi_status st = query_order(ix, q, nq, ob, &order, s);
   if (st) return st;
   KnnArgs a{ix->view(), q, nq, k, order, out_id, out_d2, ix->d_status};
+  KnnStats stats{d_stats};
   const int g = query_grid(nq);
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
-#define KNN_CASE(DD, KK) PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK>), g, QW * 32, 0, s, a)
+#define KNN_CASE(DD, KK)                                                                     \
+  do {                                                                                       \
+    if (d_stats)                                                                             \
+      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn<DD, KK, true>), g, QW * 32, 0, s, a, stats);   \
+    else                                                                                     \
+      PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK, false>), g, QW * 32, 0, s, a, stats);        \
+  } while (0)
   if (ix->D == 2) {
     if (kpl == 1) KNN_CASE(2, 1);
     else if (kpl == 2) KNN_CASE(2, 2);

@@ -116,11 +116,12 @@ __global__ void k_hist_scan(const uint32_t *hist, uint32_t *gbase) {
 }
 
 template <int MODE, int D, int CURVE>
-__global__ __launch_bounds__(ST, 2) void k_onesweep(PassArgs a) {
+__global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
   __shared__ uint32_t s_wh[SW][RADIX];
   __shared__ uint32_t s_off[RADIX];
   __shared__ uint32_t s_glob[RADIX];
   __shared__ __align__(16) uint64_t s_stage[TILE];
+  __shared__ uint8_t s_dig[TILE];  // digit of each staged position
   __shared__ uint32_t s_wsum[SW];
   __shared__ uint8_t s_htab[256];
   __shared__ uint32_t s_tile;
@@ -236,14 +237,14 @@ __global__ __launch_bounds__(ST, 2) void k_onesweep(PassArgs a) {
     }
   }
   __syncthreads();
-  uint32_t gpos[SI];
 #pragma unroll
   for (int i = 0; i < SI; ++i) {
     const int p = tid + i * ST;
     if (p < tile_n) {
       const uint64_t k = s_stage[p];
-      gpos[i] = s_glob[(uint32_t)(k >> a.shift) & (RADIX - 1)] + p;
-      a.kout[gpos[i]] = k;
+      const uint32_t dg = (uint32_t)(k >> a.shift) & (RADIX - 1);
+      s_dig[p] = (uint8_t)dg;
+      a.kout[s_glob[dg] + p] = k;
     }
   }
   __syncthreads();
@@ -257,7 +258,7 @@ __global__ __launch_bounds__(ST, 2) void k_onesweep(PassArgs a) {
 #pragma unroll
   for (int i = 0; i < SI; ++i) {
     const int p = tid + i * ST;
-    if (p < tile_n) a.vout[gpos[i]] = s_v[p];
+    if (p < tile_n) a.vout[s_glob[s_dig[p]] + p] = s_v[p];
   }
 }
 

@@ -68,6 +68,7 @@ def lib():
             "psi_export_nodes": (st, [P, P, P, P, P, P, P, P]),
             "psi_encode": (st, [P, P, i64, P, P]),
             "psi_sort_pairs": (st, [P, P, i64, i32, P]),
+            "psi_knn_instrumented": (st, [P, P, i64, i32, P, P, P, P]),
             "psi_launch_count": (i64, []),
             "psi_profile_enable": (None, [ctypes.c_int]),
             "psi_profile_reset": (None, []),
@@ -173,6 +174,18 @@ class Index:
             out_d2 = torch.empty((nq, k), dtype=torch.int64, device=q.device)
         _check(lib().psi_knn(self._h, _ptr(q), nq, k, _ptr(out_ids), _ptr(out_d2), _stream(stream)))
         return out_ids, out_d2
+
+    def knn_stats(self, q: torch.Tensor, k: int, stream=None):
+        """k-NN with traversal counters: (ids, d2, {nodes, leaves, points, queries})."""
+        q = q.contiguous()
+        nq = int(q.shape[0])
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        out_d2 = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        st = torch.zeros(4, dtype=torch.int64, device=q.device)
+        _check(lib().psi_knn_instrumented(self._h, _ptr(q), nq, k, _ptr(out_ids), _ptr(out_d2), _ptr(st),
+                                          _stream(stream)))
+        c = st.cpu().tolist()
+        return out_ids, out_d2, {"nodes": c[0], "leaves": c[1], "points": c[2], "queries": c[3]}
 
     def range_count(self, boxes: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         boxes = boxes.contiguous()
