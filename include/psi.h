@@ -165,6 +165,27 @@ psi_status psi_encode(const psi_config *cfg, const int32_t *d_pts, int64_t n, ui
  * digits sorted (1..64).  In-place on the caller's arrays; uses library scratch. */
 psi_status psi_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bits, void *stream);
 
+/* Same sort as psi_sort_pairs, for callers that cannot let a library allocate
+ * device memory: code running inside a host application that owns the whole
+ * device memory budget (an engine that has reserved the memory pool for its
+ * own arena), or a real-time loop where an allocation could block or fail in
+ * the middle of a frame.  This entry point calls no cudaMalloc, cudaFree or
+ * other allocating routine.  (The paper has no counterpart; it is a service of
+ * this library.)
+ *   - Limit: n <= 1048576 pairs; larger n returns PSI_ERR_INVALID and leaves
+ *     the arrays untouched.
+ *   - Scratch: one fixed array of about 14 MB in device memory, defined at
+ *     file scope in the library; every GPU that loads the library holds it
+ *     until the process exits.  All calls share it and it keeps the last
+ *     call's contents; the call clears what must start at zero.  Calls that
+ *     overlap on the GPU (on different streams, or from several host threads)
+ *     race on it and must be serialised by the caller.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Synchronises `stream` at the end (like psi_sort_pairs). */
+psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bits, void *stream);
+
 /* ---- Instrumentation ---------------------------------------------------- */
 
 /* psi_knn with traversal counters: d_stats (device, 4 x uint64) receives the

@@ -19,6 +19,8 @@
 // Equal keys (duplicate points) are then put in id order by k_tie_runs /
 // k_tie_long (a later canonical leaf layout depends on it).
 #include "common.cuh"
+#include <mutex>
+
 #include "bitonic.cuh"
 #include "keys.cuh"
 
@@ -551,3 +553,120 @@ psi_status scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *
 }
 
 }  // namespace psi
+
+// ---------------------------------------------------------------------------
+// The key sort without any allocation: all scratch (the second key/value
+// buffer, digit histograms, look-back table, tile counters, status word) lives
+// in one fixed device array that every GPU loading this library holds until
+// the process exits.
+// ---------------------------------------------------------------------------
+namespace psi {
+namespace {
+
+constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 20;
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxPairs + TILE - 1) / TILE;
+constexpr size_t kOffKeys = 0;
+constexpr size_t kOffVals = kOffKeys + sizeof(uint64_t) * kNoAllocMaxPairs;
+constexpr size_t kOffHist = kOffVals + sizeof(uint32_t) * kNoAllocMaxPairs;
+constexpr size_t kOffBase = kOffHist + sizeof(uint32_t) * MAX_PASSES * RADIX;
+constexpr size_t kOffLook = kOffBase + sizeof(uint32_t) * MAX_PASSES * RADIX;
+constexpr size_t kOffCtr = kOffLook + sizeof(uint32_t) * MAX_PASSES * kNoAllocTiles * RADIX;
+constexpr size_t kOffStatus = kOffCtr + sizeof(uint32_t) * MAX_PASSES;
+constexpr size_t kNoAllocBytes = (kOffStatus + sizeof(int) + 255) / 256 * 256;  // about 14 MB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host code may not use g_noalloc_scratch as a pointer: on the host that name
+// is only a stand-in for the device symbol.  Its device address is looked up
+// once per device, with that device current, and cached here.
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_addr[64] = {};
+
+psi_status noalloc_scratch(unsigned char **out) {
+  int dev = 0;
+  PSI_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal out of range");
+    return PSI_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return PSI_OK;
+}
+
+}  // namespace
+}  // namespace psi
+
+extern "C" psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bits,
+                                             void *stream) {
+  using namespace psi;
+  set_error("");
+  if (n < 0 || (n > 0 && (!d_keys || !d_vals)) || key_bits < 1 || key_bits > 64) {
+    set_error("invalid sort arguments");
+    return PSI_ERR_INVALID;
+  }
+  if (n > kNoAllocMaxPairs) {
+    set_error("psi_sort_pairs_noalloc: at most 1048576 pairs per call (use psi_sort_pairs for more)");
+    return PSI_ERR_INVALID;
+  }
+  if (n == 0) return PSI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *base = nullptr;
+  psi_status st = noalloc_scratch(&base);
+  if (st) return st;
+  uint64_t *skeys = reinterpret_cast<uint64_t *>(base + kOffKeys);
+  uint32_t *svals = reinterpret_cast<uint32_t *>(base + kOffVals);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(base + kOffHist);
+  uint32_t *gbase = reinterpret_cast<uint32_t *>(base + kOffBase);
+  uint32_t *look = reinterpret_cast<uint32_t *>(base + kOffLook);
+  uint32_t *ctr = reinterpret_cast<uint32_t *>(base + kOffCtr);
+  int *status = reinterpret_cast<int *>(base + kOffStatus);
+  const int passes = (key_bits + RB - 1) / RB;
+  const int64_t tiles = ceil_div(n, TILE);
+  // the array keeps the previous call's contents: clear what must start at zero
+  PSI_CK(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * passes * RADIX, s));
+  PSI_CK(cudaMemsetAsync(look, 0, sizeof(uint32_t) * passes * tiles * RADIX, s));
+  PSI_CK(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * passes, s));
+  PSI_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  EncodeSpec none;
+  launch_hist<0, 2, 0>(d_keys, none, n, passes, hist, status, s);
+  PSI_LAUNCH(k_hist_scan, passes, RADIX, 0, s, hist, gbase);
+  // ping-pong between the scratch pair (even passes) and the caller's arrays
+  uint64_t *kb[2] = {skeys, d_keys};
+  uint32_t *vb[2] = {svals, d_vals};
+  for (int p = 0; p < passes; ++p) {
+    PassArgs a;
+    a.kin = p == 0 ? d_keys : kb[(p - 1) & 1];
+    a.vin = p == 0 ? d_vals : vb[(p - 1) & 1];
+    a.kout = kb[p & 1];
+    a.vout = vb[p & 1];
+    a.pts = nullptr;
+    a.bits = 0;
+    a.n = n;
+    a.shift = p * RB;
+    a.gbase = gbase + p * RADIX;
+    a.lookback = look + (size_t)p * tiles * RADIX;
+    a.tile_ctr = ctr + p;
+    a.status = status;
+    launch_pass<0, 2, 0>(a, tiles, s);
+  }
+  if ((passes & 1) == 1) {  // the last pass wrote the scratch pair
+    PSI_CK(cudaMemcpyAsync(d_keys, skeys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+    PSI_CK(cudaMemcpyAsync(d_vals, svals, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  PSI_CK(cudaGetLastError());
+  int h = 0;
+  PSI_CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  if (h & ST_TIMEOUT) {
+    set_error("a bounded device-side wait timed out");
+    return PSI_ERR_DEVICE_TIMEOUT;
+  }
+  return PSI_OK;
+}

@@ -69,6 +69,7 @@ def lib():
             "psi_encode": (st, [P, P, i64, P, P]),
             "psi_sort_pairs": (st, [P, P, i64, i32, P]),
             "psi_knn_instrumented": (st, [P, P, i64, i32, P, P, P, P]),
+            "psi_sort_pairs_noalloc": (st, [P, P, i64, i32, P]),
             "psi_launch_count": (i64, []),
             "psi_profile_enable": (None, [ctypes.c_int]),
             "psi_profile_reset": (None, []),
