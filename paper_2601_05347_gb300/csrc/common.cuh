@@ -128,6 +128,7 @@ struct EncodeSpec {
   int dim = 2;
   int curve = CURVE_MORTON;
   int bits = 30;
+  int key_shift = 0;  // keys are (curve key >> key_shift): sort by the top bits only
 };
 
 // Sort workspace: ping-pong key/value buffers plus look-back and histograms.

@@ -130,6 +130,30 @@ struct KList {
   }
 };
 
+// Ascending warp bitonic sort of (d, i) pairs, one per lane.
+__device__ __forceinline__ void warp_sort_pairs(int64_t &d, uint32_t &i) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int64_t od = __shfl_xor_sync(0xFFFFFFFFu, d, j);
+      const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, i, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+      const bool other_less = pair_less(od, oi, d, i);
+      if (keep_min == other_less) {
+        d = od;
+        i = oi;
+      }
+    }
+  }
+}
+
+// Scan one leaf: every point whose (d2, id) beats the current k-th enters the
+// list.  With a single register per lane (k <= 32) and many entrants -- the
+// first leaf of a query, when the list is still empty -- the entrants are
+// sorted across the warp and merged in one bitonic merge; otherwise they are
+// inserted one at a time.
 template <int D, int KPL>
 __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, const int32_t *qc, KList<KPL> &kl,
                                               int k) {
@@ -151,7 +175,42 @@ __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, 
         d2 += dd * dd;
       }
     }
-    uint32_t m = __ballot_sync(0xFFFFFFFFu, valid && kl.admits(d2, id));
+    const bool in = valid && kl.admits(d2, id);
+    uint32_t m = __ballot_sync(0xFFFFFFFFu, in);
+    if (KPL == 1 && __popc(m) > 6) {
+      int64_t cd = in ? d2 : INT64_MAX;
+      uint32_t ci = in ? id : 0xFFFFFFFFu;
+      warp_sort_pairs(cd, ci);
+      // reverse the sorted entrants against the sorted list: the lane-wise
+      // minimum is a bitonic sequence holding the 32 smallest of the union
+      const int64_t rd = __shfl_sync(0xFFFFFFFFu, cd, 31 - lane);
+      const uint32_t ri = __shfl_sync(0xFFFFFFFFu, ci, 31 - lane);
+      int64_t nd = kl.d[0];
+      uint32_t ni = kl.i[0];
+      if (pair_less(rd, ri, nd, ni)) {
+        nd = rd;
+        ni = ri;
+      }
+#pragma unroll
+      for (int j = 16; j > 0; j >>= 1) {
+        const int64_t od = __shfl_xor_sync(0xFFFFFFFFu, nd, j);
+        const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, ni, j);
+        const bool lower = (lane & j) == 0;
+        if (lower == pair_less(od, oi, nd, ni)) {
+          nd = od;
+          ni = oi;
+        }
+      }
+      if (lane >= k) {
+        nd = INT64_MAX;
+        ni = 0xFFFFFFFFu;
+      }
+      kl.d[0] = nd;
+      kl.i[0] = ni;
+      kl.kd = __shfl_sync(0xFFFFFFFFu, nd, k - 1);
+      kl.ki = __shfl_sync(0xFFFFFFFFu, ni, k - 1);
+      continue;
+    }
     while (m) {
       const int src = __ffs(m) - 1;
       m &= m - 1;
@@ -162,38 +221,32 @@ __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, 
   }
 }
 
-// Monotone 32-bit image of a non-negative distance (float bits), used only to
-// choose a visiting order; pruning always compares exact int64 distances.
+// Monotone non-decreasing 32-bit image of a non-negative distance (its float
+// bits, rounded to nearest).  a <= b implies key(a) <= key(b), so skipping a
+// node whose key exceeds key(k-th distance) never skips one that could hold a
+// neighbour; it may keep a few that cannot, which costs time, not exactness.
 __device__ __forceinline__ uint32_t order_key(int64_t md) { return __float_as_uint((float)md); }
-
-// Lane holding the smallest (select_max: largest) order key among the lanes of
-// `mask` (mask != 0).
-__device__ __forceinline__ int select_lane(uint32_t mask, int64_t md, bool select_max) {
-  const int lane = threadIdx.x & 31;
-  const bool in = (mask >> lane) & 1u;
-  uint32_t key = order_key(md);
-  if (select_max) {
-    const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, in ? key : 0u);
-    return __ffs(__ballot_sync(0xFFFFFFFFu, in && key == m)) - 1;
-  }
-  const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, in ? key : 0xFFFFFFFFu);
-  return __ffs(__ballot_sync(0xFFFFFFFFu, in && key == m)) - 1;
-}
 
 struct KnnStats {
   unsigned long long *c;  // [0] internal nodes expanded, [1] leaves scanned, [2] points scanned, [3] queries
 };
 
-// One warp per query.
-//  1. Greedy descent: from the root, always into the child whose box is
-//     nearest, down to one leaf; scanning it gives a finite k-th distance.
-//  2. Depth-first traversal from the root pruned by the k-th distance: leaf
-//     children are scanned at once in increasing box distance; internal
-//     children are pushed farthest first so that the nearest is popped next.
+constexpr int MAXLVL = 33;  // tree depth bound (P-Orth: 31 levels below the root)
+
+// One warp per query: depth-first search that always enters the nearest
+// not-yet-visited child (Appendix "Implementation Details": children in
+// increasing box distance).  Each level of the current path keeps, in shared
+// memory, its children's distance keys and a bitmask of children still to
+// visit; one ballot prunes every remaining child farther than the current
+// k-th distance, one reduce picks the nearest.  The first path taken is the
+// greedy descent to the nearest leaf, which makes the k-th distance finite
+// early.
 template <int D, int KPL, bool STATS>
 __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
-  __shared__ uint32_t s_node[QW][STACK];
-  __shared__ int64_t s_md[QW][STACK];
+  __shared__ uint32_t s_key[QW][MAXLVL][32];
+  __shared__ uint32_t s_c0[QW][MAXLVL];
+  __shared__ uint32_t s_mask[QW][MAXLVL];
+  __shared__ uint32_t s_leaf[QW][MAXLVL];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nw = (int64_t)gridDim.x * QW;
   const TreeView &t = a.t;
@@ -205,99 +258,62 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     for (int d = 0; d < D; ++d) qc[d] = a.q[q * D + d];
     KList<KPL> kl;
     kl.init();
-    if (t.root >= 0) {
-      uint32_t node = (uint32_t)t.root;
-      for (int nk = t.kids[node]; nk > 0; nk = t.kids[node]) {
-        const uint32_t c0 = t.ref[node];
-        uint32_t best = 0xFFFFFFFFu;
-        uint32_t best_key = 0xFFFFFFFFu;
-        for (int cb = 0; cb < nk; cb += 32) {
-          int64_t md = INT64_MAX;
-          const uint32_t c = c0 + (uint32_t)(cb + lane);
-          if (cb + lane < nk && t.cnt[c] > 0) md = box_mindist<D>(t, c, qc);
-          const uint32_t key = cb + lane < nk && t.cnt[c] > 0 ? order_key(md) : 0xFFFFFFFFu;
-          const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, key);
-          if (m < best_key) {
-            best_key = m;
-            best = __shfl_sync(0xFFFFFFFFu, c, __ffs(__ballot_sync(0xFFFFFFFFu, key == m)) - 1);
-          }
-        }
-        if (STATS) ++n_int;
-        node = best;
+    uint32_t kdk = order_key(kl.kd);
+    auto expand = [&](uint32_t node, int lvl) {
+      const int nk = t.kids[node];
+      const uint32_t c0 = t.ref[node];
+      const uint32_t c = c0 + (uint32_t)lane;
+      uint32_t key = 0xFFFFFFFFu;
+      bool leafc = false;
+      if (lane < nk && t.cnt[c] > 0) {
+        key = order_key(box_mindist<D>(t, c, qc));
+        leafc = t.kids[c] == 0;
       }
-      const uint32_t first = node;
-      knn_scan_leaf<D, KPL>(t, first, qc, kl, a.k);
-      if (STATS) {
-        ++n_leaf;
-        n_pts += t.cnt[first];
-      }
-      int sp = 0;
+      s_key[w][lvl][lane] = key;
+      const uint32_t mk = __ballot_sync(0xFFFFFFFFu, key <= kdk);
+      const uint32_t lf = __ballot_sync(0xFFFFFFFFu, leafc);
       if (lane == 0) {
-        s_node[w][0] = (uint32_t)t.root;
-        s_md[w][0] = 0;
+        s_c0[w][lvl] = c0;
+        s_mask[w][lvl] = mk;
+        s_leaf[w][lvl] = lf;
       }
-      sp = 1;
+      if (STATS) ++n_int;
       __syncwarp();
-      while (sp > 0) {
-        --sp;
-        const uint32_t nd = s_node[w][sp];
-        const int64_t md = s_md[w][sp];
-        __syncwarp();
-        if (md > kl.kd) continue;
-        const int nk = t.kids[nd];
-        if (nk == 0) {
-          if (nd != first) {
-            knn_scan_leaf<D, KPL>(t, nd, qc, kl, a.k);
+    };
+    if (t.root >= 0) {
+      if (t.kids[t.root] == 0) {
+        knn_scan_leaf<D, KPL>(t, (uint32_t)t.root, qc, kl, a.k);
+      } else {
+        int lvl = 0;
+        expand((uint32_t)t.root, 0);
+        while (lvl >= 0) {
+          const uint32_t key = s_key[w][lvl][lane];
+          const uint32_t m = s_mask[w][lvl] & __ballot_sync(0xFFFFFFFFu, key <= kdk);
+          if (m == 0) {
+            --lvl;
+            continue;
+          }
+          const bool in = (m >> lane) & 1u;
+          const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, in ? key : 0xFFFFFFFFu);
+          const int src = __ffs(__ballot_sync(0xFFFFFFFFu, in && key == mn)) - 1;
+          const uint32_t child = s_c0[w][lvl] + (uint32_t)src;
+          const bool is_leaf = (s_leaf[w][lvl] >> src) & 1u;
+          __syncwarp();
+          if (lane == 0) s_mask[w][lvl] = m & ~(1u << src);
+          __syncwarp();
+          if (is_leaf) {
+            knn_scan_leaf<D, KPL>(t, child, qc, kl, a.k);
+            kdk = order_key(kl.kd);
             if (STATS) {
               ++n_leaf;
-              n_pts += t.cnt[nd];
+              n_pts += t.cnt[child];
             }
+          } else if (lvl + 1 < MAXLVL) {
+            ++lvl;
+            expand(child, lvl);
+          } else if (lane == 0) {
+            atomicOr(a.status, ST_STACK);
           }
-          continue;
-        }
-        if (STATS) ++n_int;
-        const uint32_t c0 = t.ref[nd];
-        for (int cb = 0; cb < nk; cb += 32) {
-          const bool valid = cb + lane < nk;
-          const uint32_t c = c0 + (uint32_t)(cb + lane);
-          int64_t cmd = INT64_MAX;
-          bool leafc = false;
-          if (valid && t.cnt[c] > 0) {
-            cmd = box_mindist<D>(t, c, qc);
-            leafc = t.kids[c] == 0;
-          }
-          // leaf children now, nearest first
-          uint32_t lm = __ballot_sync(0xFFFFFFFFu, leafc && cmd <= kl.kd);
-          while (lm) {
-            const int src = select_lane(lm, cmd, false);
-            const int64_t smd = __shfl_sync(0xFFFFFFFFu, cmd, src);
-            if (smd > kl.kd) break;
-            const uint32_t leaf = __shfl_sync(0xFFFFFFFFu, c, src);
-            if (leaf != first) {
-              knn_scan_leaf<D, KPL>(t, leaf, qc, kl, a.k);
-              if (STATS) {
-                ++n_leaf;
-                n_pts += t.cnt[leaf];
-              }
-            }
-            lm &= ~(1u << src);
-          }
-          // internal children, pushed farthest first
-          uint32_t im = __ballot_sync(0xFFFFFFFFu, valid && !leafc && cmd <= kl.kd);
-          if (sp + __popc(im) > STACK) {
-            if (lane == 0) atomicOr(a.status, ST_STACK);
-            im = 0;
-          }
-          while (im) {
-            const int src = __popc(im) == 1 ? __ffs(im) - 1 : select_lane(im, cmd, true);
-            if (lane == src) {
-              s_node[w][sp] = c;
-              s_md[w][sp] = cmd;
-            }
-            ++sp;
-            im &= ~(1u << src);
-          }
-          __syncwarp();
         }
       }
     }
@@ -465,9 +481,12 @@ psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, Buf<ui
   psi_status st;
   if ((st = k0.alloc(nq, s)) || (st = k1.alloc(nq, s)) || (st = order_buf.alloc(nq, s)) || (st = v1.alloc(nq, s)))
     return st;
+  // locality only needs the top bits of the curve key: 48 bits, 6 digit passes
   EncodeSpec e = encode_spec(ix, q);
+  const int order_bits = std::min(48, ix->key_bits);
+  e.key_shift = ix->key_bits - order_bits;
   SortResult r;
-  if ((st = sort_pairs(e, nullptr, nullptr, nq, ix->key_bits, nullptr, k0.p, order_buf.p, k1.p, v1.p, ix->d_status,
+  if ((st = sort_pairs(e, nullptr, nullptr, nq, order_bits, nullptr, k0.p, order_buf.p, k1.p, v1.p, ix->d_status,
                        s, &r)))
     return st;
   if (r.vals == v1.p) {

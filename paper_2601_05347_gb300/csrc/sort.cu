@@ -47,6 +47,7 @@ struct PassArgs {
   uint32_t *vout;
   const int32_t *pts;
   int bits;
+  int key_shift;
   int64_t n;
   int shift;
   const uint32_t *gbase;  // [RADIX] global exclusive digit offsets of this pass
@@ -55,12 +56,17 @@ struct PassArgs {
   int *status;
 };
 
+// Digit histograms go to HIST_PARTS copies in shared memory (lane % HIST_PARTS
+// picks the copy), so lanes of a warp that hit the same digit -- the common case
+// for the top digits of clustered input -- rarely collide on one address.
+constexpr int HIST_PARTS = 4;
+
 template <int MODE, int D, int CURVE>
-__global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const int32_t *pts, int bits, int64_t n,
-                                                   int passes, uint32_t *hist, int *status) {
-  __shared__ uint32_t sh[MAX_PASSES][RADIX];
+__global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const int32_t *pts, int bits, int key_shift,
+                                                   int64_t n, int passes, uint32_t *hist, int *status) {
+  __shared__ uint32_t shp[HIST_PARTS][MAX_PASSES][RADIX];
   __shared__ uint8_t htab[256];
-  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < HIST_PARTS * MAX_PASSES * RADIX; i += blockDim.x) (&shp[0][0][0])[i] = 0;
   if (MODE == 1 && CURVE == 1) hilbert_table_init(htab);
   __syncthreads();
   bool bad_any = false;
@@ -76,16 +82,17 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
 #pragma unroll
         for (int d = 0; d < D; ++d) c[d] = pts[i * D + d];
         bool bad;
-        k = point_key<D, CURVE>(htab, c, bits, bad);
+        k = point_key<D, CURVE>(htab, c, bits, bad) >> key_shift;
         bad_any |= bad;
       }
       const uint32_t act = __activemask();
+      uint32_t(*sh)[RADIX] = shp[threadIdx.x % HIST_PARTS];
       for (int p = 0; p < passes; ++p) {
         uint32_t dg = (uint32_t)(k >> (p * RB)) & (RADIX - 1);
         int all_same;
         __match_all_sync(act, dg, &all_same);
         if (all_same) {
-          if ((lanemask_lt() & act) == 0) atomicAdd(&sh[p][dg], (uint32_t)__popc(act));
+          if ((lanemask_lt() & act) == 0) atomicAdd(&shp[0][p][dg], (uint32_t)__popc(act));
         } else {
           atomicAdd(&sh[p][dg], 1u);
         }
@@ -95,7 +102,9 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   if (bad_any) atomicOr(status, ST_RANGE);
   __syncthreads();
   for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
-    uint32_t v = (&sh[0][0])[i];
+    uint32_t v = 0;
+#pragma unroll
+    for (int q = 0; q < HIST_PARTS; ++q) v += (&shp[q][0][0])[i];
     if (v) atomicAdd(&hist[i], v);
   }
 }
@@ -152,7 +161,7 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
 #pragma unroll
         for (int d = 0; d < D; ++d) c[d] = a.pts[gi * D + d];
         bool bad;
-        key[j] = point_key<D, CURVE>(s_htab, c, a.bits, bad);
+        key[j] = point_key<D, CURVE>(s_htab, c, a.bits, bad) >> a.key_shift;
       }
     }
   }
@@ -363,7 +372,7 @@ static void launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_t n, i
                         int *status, cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
   PSI_LAUNCH_NAMED("k_sort_hist", (k_sort_hist<MODE, D, CURVE>), std::max(grid, 1), 256, 0, s, kin, enc.pts,
-                   enc.bits, n, passes, hist, status);
+                   enc.bits, enc.key_shift, n, passes, hist, status);
 }
 
 template <int MODE, int D, int CURVE>
@@ -418,6 +427,7 @@ psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint
     a.vout = vb[p & 1];
     a.pts = enc.pts;
     a.bits = enc.bits;
+    a.key_shift = enc.key_shift;
     a.n = n;
     a.shift = p * RB;
     a.gbase = gbase.p + p * RADIX;
@@ -648,6 +658,7 @@ extern "C" psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals,
     a.vout = vb[p & 1];
     a.pts = nullptr;
     a.bits = 0;
+    a.key_shift = 0;
     a.n = n;
     a.shift = p * RB;
     a.gbase = gbase + p * RADIX;

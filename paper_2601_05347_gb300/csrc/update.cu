@@ -164,9 +164,18 @@ Leaves leaves_of(NodeArrays &a, uint64_t *sk, uint32_t *si) {
   return l;
 }
 
+// owner[o] = old leaf whose output includes new leaf position o
+__global__ void k_owner_scatter(const int32_t *outl, const int64_t *pos, int64_t L, int32_t *owner) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = pos[j];
+    for (int t = 0; t < outl[j]; ++t) owner[p + t] = (int32_t)j;
+  }
+}
+
 struct InsertArgs {
   Leaves old, nw;
   Pool pool;
+  const int32_t *owner;
   const int32_t *sbeg, *send, *outl;
   const int64_t *pos, *boff;
   int64_t L, Lnew;
@@ -191,15 +200,7 @@ __global__ void k_insert_apply(InsertArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < a.Lnew; o += warps) {
-    int64_t lo = 0, hi = a.L;  // owner j: last old leaf with pos[j] <= o
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (a.pos[mid] <= o)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    const int64_t j = lo - 1;
+    const int64_t j = a.owner[o];
     const int t = (int)(o - a.pos[j]);
     const int len = a.send[j] - a.sbeg[j];
     const int cnt = a.old.cnt[j];
@@ -498,7 +499,11 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
     DevMem::free(nsi, s);
     return st;
   }
+  Buf<int32_t> owner;
+  if ((st = owner.alloc(Lnew, s))) return st;
+  PSI_LAUNCH(k_owner_scatter, grid_for(L), 256, 0, s, outl.p, pos.p, L, owner.p);
   InsertArgs a;
+  a.owner = owner.p;
   a.old = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
   a.nw = leaves_of(na, nsk, nsi);
   a.pool = ix->pool;
