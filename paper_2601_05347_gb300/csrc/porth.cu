@@ -22,7 +22,7 @@
 //   children of a node (the next depth's nodes whose first leaf lies inside
 //   its cell) are contiguous.  Boxes are unions of the children, bottom up.
 //
-// Updates (Algorithm 2) rely on history independence (Sec 6.2 "Impact of
+// Updates (Algorithm 2) rely on history independence (Sec 5.1.3 "Impact of
 // Updates to Queries"): the tree after a batch is the tree of the new point
 // set.  An insert merges the sorted batch into the sorted points; a delete
 // removes matching (point, id) pairs; both then re-derive leaves and nodes.

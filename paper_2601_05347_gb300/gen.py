@@ -1,4 +1,4 @@
-"""Seeded synthetic workloads shaped like the paper's (Sec 6.1: Uniform and Varden).
+"""Seeded synthetic workloads shaped like the paper's (Sec 5.1: Uniform and Varden).
 
 This module holds only random draws and workload shapes -- none of the index
 arithmetic -- so the tests, the oracle and the CUDA path can share it.  Every

@@ -65,7 +65,7 @@ def test_hilbert_bijection_adjacency_endpoints_nesting(bits):
     side = 1 << bits
     assert cells[0] == (0, 0)
     assert cells[-1] == (side - 1, 0)
-    # consecutive indices are grid neighbours (Sec 6.2: adjacent codes are always geometrically close)
+    # consecutive indices are grid neighbours (Sec 5.1.3: adjacent codes are always geometrically close)
     for a, b in zip(cells, cells[1:]):
         assert abs(a[0] - b[0]) + abs(a[1] - b[1]) == 1
     # every aligned run of 4^j indices fills an aligned 2^j x 2^j square
