@@ -136,6 +136,45 @@ int64_t psi_num_nodes(const psi_index *ix);
 /* Message of the last error on the calling thread ("" if none). */
 const char *psi_last_error(void);
 
+/* ---- Many independent indexes at once ---------------------------------- */
+
+typedef struct psi_batch psi_batch;
+
+/* Lays out storage for nidx independent SPaC indexes over one concatenated
+ * point array: index i owns points [h_offsets[i], h_offsets[i+1]) (host array
+ * of nidx+1 entries, h_offsets[0] = 0).  All indexes share cfg (SPAC_Z or
+ * SPAC_H).  `threads` is the thread-block size of the build (256, 512, 1024; 0
+ * = 512).  Allocates everything the build needs, so psi_batch_build and
+ * psi_batch_knn allocate nothing and can be captured in a CUDA graph.
+ * Synchronises `stream`. */
+psi_status psi_batch_create(const psi_config *cfg, const int64_t *h_offsets, int32_t nidx, int32_t threads,
+                            void *stream, psi_batch **out);
+
+/* Builds every index of the batch (Algorithm 3 per index: curve keys, (key, id)
+ * sort, leaf wrapping, summaries) in ONE persistent kernel launch: each thread
+ * block takes whole indexes, largest first, from an atomic queue.  Each index
+ * gets exactly the layout psi_build would give it.  d_pts [total][dim] and
+ * d_ids [total] are read during the call only. */
+psi_status psi_batch_build(psi_batch *b, const int32_t *d_pts, const uint32_t *d_ids, void *stream);
+
+/* Reserves query scratch for up to max_queries queries per psi_batch_knn call. */
+psi_status psi_batch_knn_reserve(psi_batch *b, int64_t max_queries, void *stream);
+
+/* k-NN (Sec 2.2) for queries grouped by index: d_qoffsets (DEVICE, nidx+1
+ * entries) gives the queries [qoff[i], qoff[i+1]) that ask index i.  Results as
+ * in psi_knn, one launch for all indexes.  nq <= the reserved capacity. */
+psi_status psi_batch_knn(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq, int32_t k,
+                         uint32_t *d_ids, int64_t *d_d2, void *stream);
+
+/* Waits for `stream` and returns any device-detected error of the batch. */
+psi_status psi_batch_sync(psi_batch *b, void *stream);
+psi_status psi_batch_destroy(psi_batch *b);
+
+/* Inspection: leaves of index i (counts[L], lo[L][dim], hi[L][dim]); *h_leaves = L. */
+int64_t psi_batch_num_leaves(const psi_batch *b, int32_t i);
+psi_status psi_batch_export_index(const psi_batch *b, int32_t i, int32_t *d_counts, int32_t *d_lo, int32_t *d_hi,
+                                  int64_t *h_leaves, void *stream);
+
 /* ---- Inspection (tests, tools) --------------------------------------- */
 
 /* Leaves in key order: counts[L], lo[L][dim], hi[L][dim], first key and first

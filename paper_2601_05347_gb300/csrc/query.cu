@@ -62,6 +62,7 @@ struct KnnArgs {
   int64_t nq;
   int k;
   const uint32_t *order;
+  const int32_t *qroot;  // per-query root (many indexes in one node array), or null
   uint32_t *out_id;
   int64_t *out_d2;
   int *status;
@@ -258,6 +259,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     for (int d = 0; d < D; ++d) qc[d] = a.q[q * D + d];
     KList<KPL> kl;
     kl.init();
+    const int32_t root = a.qroot ? a.qroot[q] : t.root;
     uint32_t kdk = order_key(kl.kd);
     auto expand = [&](uint32_t node, int lvl) {
       const int nk = t.kids[node];
@@ -280,12 +282,12 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
       if (STATS) ++n_int;
       __syncwarp();
     };
-    if (t.root >= 0) {
-      if (t.kids[t.root] == 0) {
-        knn_scan_leaf<D, KPL>(t, (uint32_t)t.root, qc, kl, a.k);
+    if (root >= 0) {
+      if (t.kids[root] == 0) {
+        knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k);
       } else {
         int lvl = 0;
-        expand((uint32_t)t.root, 0);
+        expand((uint32_t)root, 0);
         while (lvl >= 0) {
           const uint32_t key = s_key[w][lvl][lane];
           const uint32_t m = s_mask[w][lvl] & __ballot_sync(0xFFFFFFFFu, key <= kdk);
@@ -496,14 +498,11 @@ psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, Buf<ui
   return PSI_OK;
 }
 
-psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uint32_t *out_id, int64_t *out_d2,
-                   unsigned long long *d_stats, cudaStream_t s) {
+psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
+                         const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status,
+                         unsigned long long *d_stats, cudaStream_t s) {
   if (nq == 0) return PSI_OK;
-  Buf<uint32_t> ob;
-  uint32_t *order = nullptr;
-  psi_status st = query_order(ix, q, nq, ob, &order, s);
-  if (st) return st;
-  KnnArgs a{ix->view(), q, nq, k, order, out_id, out_d2, ix->d_status};
+  KnnArgs a{tv, q, nq, k, order, qroot, out_id, out_d2, status};
   KnnStats stats{d_stats};
   const int g = query_grid(nq);
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
@@ -514,7 +513,7 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
     else                                                                                     \
       PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK, false>), g, QW * 32, 0, s, a, stats);        \
   } while (0)
-  if (ix->D == 2) {
+  if (D == 2) {
     if (kpl == 1) KNN_CASE(2, 1);
     else if (kpl == 2) KNN_CASE(2, 2);
     else KNN_CASE(2, 4);
@@ -526,6 +525,21 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
 #undef KNN_CASE
   PSI_CK(cudaGetLastError());
   return PSI_OK;
+}
+
+psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
+                         const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status, cudaStream_t s) {
+  return run_knn_roots(tv, q, nq, k, order, qroot, D, out_id, out_d2, status, nullptr, s);
+}
+
+psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uint32_t *out_id, int64_t *out_d2,
+                   unsigned long long *d_stats, cudaStream_t s) {
+  if (nq == 0) return PSI_OK;
+  Buf<uint32_t> ob;
+  uint32_t *order = nullptr;
+  psi_status st = query_order(ix, q, nq, ob, &order, s);
+  if (st) return st;
+  return run_knn_roots(ix->view(), q, nq, k, order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s);
 }
 
 psi_status run_range_count(const psi_index *ix, const int32_t *boxes, int64_t nq, int64_t *counts, cudaStream_t s) {

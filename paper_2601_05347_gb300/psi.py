@@ -70,6 +70,14 @@ def lib():
             "psi_sort_pairs": (st, [P, P, i64, i32, P]),
             "psi_knn_instrumented": (st, [P, P, i64, i32, P, P, P, P]),
             "psi_sort_pairs_noalloc": (st, [P, P, i64, i32, P]),
+            "psi_batch_create": (st, [P, P, i32, i32, P, P]),
+            "psi_batch_build": (st, [P, P, P, P]),
+            "psi_batch_knn_reserve": (st, [P, i64, P]),
+            "psi_batch_knn": (st, [P, P, P, i64, i32, P, P, P]),
+            "psi_batch_sync": (st, [P, P]),
+            "psi_batch_destroy": (st, [P]),
+            "psi_batch_num_leaves": (i64, [P, i32]),
+            "psi_batch_export_index": (st, [P, i32, P, P, P, P, P]),
             "psi_launch_count": (i64, []),
             "psi_profile_enable": (None, [ctypes.c_int]),
             "psi_profile_reset": (None, []),
@@ -252,6 +260,71 @@ class Index:
             _check(lib().psi_export_nodes(self._h, _ptr(depth), _ptr(prefix), _ptr(cnt), _ptr(lo), _ptr(hi),
                                           _ptr(leaf), _stream(stream)))
         return {"depth": depth, "prefix": prefix, "count": cnt, "lo": lo, "hi": hi, "is_leaf": leaf}
+
+
+class Batch:
+    """Many independent SPaC indexes over one concatenated point array, built in
+    one persistent launch (psi_batch_*)."""
+
+    def __init__(self, offsets, *, dim: int = 2, kind: int | str = SPAC_H, leaf_size: int = 32,
+                 coord_bits: int | None = None, fanout: int = 32, threads: int = 0, stream=None):
+        import numpy as np
+        if isinstance(kind, str):
+            kind = KINDS[kind]
+        coord_bits = coord_bits or (30 if dim == 2 else 21)
+        self.dim, self.nidx = dim, len(offsets) - 1
+        self.cfg = Config(dim, kind, leaf_size, coord_bits, fanout, 0)
+        self._off = np.ascontiguousarray(offsets, dtype=np.int64)
+        h = ctypes.c_void_p()
+        _check(lib().psi_batch_create(ctypes.byref(self.cfg), self._off.ctypes.data_as(ctypes.c_void_p), self.nidx,
+                                      threads, _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self._qcap = 0
+
+    def build(self, pts: torch.Tensor, ids: torch.Tensor, stream=None):
+        _check(lib().psi_batch_build(self._h, _ptr(pts.contiguous()), _ptr(_u32(ids).contiguous()), _stream(stream)))
+
+    def reserve(self, max_queries: int, stream=None):
+        _check(lib().psi_batch_knn_reserve(self._h, int(max_queries), _stream(stream)))
+        self._qcap = max(self._qcap, int(max_queries))
+
+    def knn(self, q: torch.Tensor, qoffsets: torch.Tensor, k: int, out_ids=None, out_d2=None, stream=None):
+        nq = int(q.shape[0])
+        if nq > self._qcap:
+            self.reserve(nq, stream)
+        if out_ids is None:
+            out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        if out_d2 is None:
+            out_d2 = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        _check(lib().psi_batch_knn(self._h, _ptr(q.contiguous()), _ptr(qoffsets.contiguous()), nq, k, _ptr(out_ids),
+                                   _ptr(out_d2), _stream(stream)))
+        return out_ids, out_d2
+
+    def sync(self, stream=None):
+        _check(lib().psi_batch_sync(self._h, _stream(stream)))
+
+    def leaves(self, i: int, stream=None):
+        L = int(lib().psi_batch_num_leaves(self._h, i))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cnt = torch.empty(L, dtype=torch.int32, device=dev)
+        lo = torch.empty((L, self.dim), dtype=torch.int32, device=dev)
+        hi = torch.empty((L, self.dim), dtype=torch.int32, device=dev)
+        n = ctypes.c_int64(0)
+        if L:
+            _check(lib().psi_batch_export_index(self._h, i, _ptr(cnt), _ptr(lo), _ptr(hi), ctypes.byref(n),
+                                                _stream(stream)))
+        return {"count": cnt, "lo": lo, "hi": hi}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psi_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def encode(pts: torch.Tensor, kind: int | str = SPAC_Z, coord_bits: int | None = None, stream=None) -> torch.Tensor:
