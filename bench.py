@@ -338,12 +338,121 @@ def run_ours(args):
         "clocks": clk,
         "input_generation_s": round(gen_s, 1),
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args.batched_indexes, max(1, args.steps), args.warmup, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, host, budget_s=args.cpu_budget)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched many-index form vs one plain launch sequence per index
+# ---------------------------------------------------------------------------
+def batched_workload(nidx: int, rank: int = 0, max_size: int = 1_000_000):
+    """nidx indexes, sizes log-uniform in [1e3, max_size], half uniform and half
+    clustered; per-index 10-NN query counts log-uniform in [1e2, 1e5] at data points."""
+    s = gen.config_seed(3, 0, rank)
+    u = gen.splitmix64(s, np.arange(2 * nidx, dtype=np.uint64)) >> np.uint64(11)
+    u = u.astype(np.float64) / float(1 << 53)
+    sizes = np.floor(np.exp(np.log(1e3) + u[:nidx] * (np.log(max_size) - np.log(1e3)))).astype(np.int64)
+    nq = np.floor(np.exp(np.log(1e2) + u[nidx:] * (np.log(1e5) - np.log(1e2)))).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    qoff = np.concatenate([[0], np.cumsum(nq)]).astype(np.int64)
+    pts = np.empty((off[-1], 2), np.int32)
+    q = np.empty((qoff[-1], 2), np.int32)
+    for i in range(nidx):
+        n = int(sizes[i])
+        si = gen.config_seed(3, 1, rank) + 7 * i
+        if i % 2 == 0:
+            pts[off[i]:off[i + 1]] = gen.uniform(n, 2, BITS, si)
+        else:
+            pts[off[i]:off[i + 1]] = gen.varden(n, 2, BITS, si, clusters=max(1, min(100, n // 1000)))
+        q[qoff[i]:qoff[i + 1]] = pts[off[i] + gen.sample_with_replacement(n, int(nq[i]), si + 3)]
+    ids = np.arange(off[-1], dtype=np.uint32)
+    return sizes, off, pts, ids, q, qoff
+
+
+def run_batched(nidx: int, steps: int, warmup: int, rank: int = 0, max_size: int = 1_000_000, tune_sample: int = 256):
+    import torch
+    from paper_2601_05347_gb300 import psi, tune
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sizes, off, pts, ids, q, qoff = batched_workload(nidx, rank, max_size)
+    k = 10
+    dp = torch.from_numpy(pts).to(dev)
+    di = torch.from_numpy(ids.view(np.int32)).to(dev)
+    dq = torch.from_numpy(q).to(dev)
+    dqo = torch.from_numpy(qoff).to(dev)
+    nq = int(qoff[-1])
+    # autotune on a sample of the indexes
+    ns = min(nidx, tune_sample)
+    t_off, t_qoff = off[: ns + 1], qoff[: ns + 1]
+    phi, threads, tinfo = tune.autotune(t_off, dp[: t_off[-1]], di[: t_off[-1]], dq[: t_qoff[-1]],
+                                        dqo[: ns + 1], int(t_qoff[-1]), k, dim=2, kind="spac_h",
+                                        dist="half-uniform-half-varden", sizes=sizes[:ns])
+    b = psi.Batch(off, kind="spac_h", leaf_size=phi, threads=threads)
+    b.reserve(nq)
+    oi = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    od = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(max(1, warmup)):
+            b.build(dp, di)
+            b.knn(dq, dqo, k, oi, od)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.build(dp, di)
+        b.knn(dq, dqo, k, oi, od)
+    s = torch.cuda.current_stream()
+    for _ in range(max(1, warmup)):
+        g.replay()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record(s)
+    for _ in range(steps):
+        g.replay()
+    e[1].record(s)
+    # build alone (not in the graph) for the phase split
+    e[2].record(s)
+    b.build(dp, di)
+    e[3].record(s)
+    torch.cuda.synchronize()
+    b.sync()
+    batched_ms = e[0].elapsed_time(e[1]) / steps
+    build_ms = e[2].elapsed_time(e[3])
+    # plain form: one build + one k-NN call sequence per index
+    pi = torch.empty_like(oi)
+    pd = torch.empty_like(od)
+    keep = []
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(s)
+    for i in range(nidx):
+        a, z = int(off[i]), int(off[i + 1])
+        ix = psi.Index(dp[a:z], di[a:z], kind="spac_h", leaf_size=phi)
+        qa, qz = int(qoff[i]), int(qoff[i + 1])
+        ix.knn(dq[qa:qz], k, pi[qa:qz], pd[qa:qz])
+        keep.append(ix)
+    p1.record(s)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    for ix in keep:
+        ix.close()
+    identical = bool(torch.equal(pi, oi) and torch.equal(pd, od))
+    npts = int(off[-1])
+    return {"indexes": nidx, "points": npts, "queries": nq, "k": k,
+            "sizes": "log-uniform [1e3, %.0e]" % max_size, "query_counts": "log-uniform [1e2, 1e5]",
+            "tuned": {"leaf_size": phi, "threads": threads, "tune_sample_indexes": ns},
+            "batched_ms": round(batched_ms, 3), "batched_build_ms": round(build_ms, 3),
+            "batched_value": round((npts / 1e6) / (batched_ms * 1e-3), 1),
+            "plain_ms": round(plain_ms, 3), "plain_value": round((npts / 1e6) / (plain_ms * 1e-3), 1),
+            "unit": "Mpts/s (build + 10-NN of the whole batch)", "speedup_vs_plain": round(plain_ms / batched_ms, 2),
+            "results_identical": identical, "graph": "build + k-NN captured in one CUDA graph, replayed"}
 
 
 # ---------------------------------------------------------------------------
@@ -440,9 +549,25 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="scaled workload with n points (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-indexes", type=int, default=512,
+                    help="indexes in the batched-form comparison of the default line")
+    ap.add_argument("--batched", action="store_true", help="only the 4096-index batched configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batched:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import __graft_entry__
+        __graft_entry__.build()
+        r = run_batched(4096, args.steps, args.warmup)
+        print(json.dumps({"metric": "batched build + 10-NN of 4096 indexes", "value": r["batched_value"],
+                          "unit": r["unit"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": r["batched_ms"], "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                          "config": {"workload": "4096 2D indexes, sizes log-uniform [1e3, 1e6], SPaC-H"},
+                          "batched": r}), flush=True)
     else:
         run_ours(args)
 
