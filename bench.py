@@ -340,6 +340,8 @@ def run_ours(args):
     }
     if not args.no_batched:
         line["batched"] = run_batched(args.batched_indexes, max(1, args.steps), args.warmup, rank)
+    if not args.no_served:
+        line["served"] = run_served(args.served_points, args.served_requests, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, host, budget_s=args.cpu_budget)
     if rank == 0:
@@ -456,6 +458,147 @@ def run_batched(nidx: int, steps: int, warmup: int, rank: int = 0, max_size: int
 
 
 # ---------------------------------------------------------------------------
+# served form: continuous batching vs one request at a time
+# ---------------------------------------------------------------------------
+def served_requests(base, R, seed, upd=(1e3, 1e5), qry=(1e2, 1e5), rep_max=1e4, half_side=None):
+    """R requests: 30 % updates (insert / delete alternating, sizes log-uniform in upd,
+    in- and out-of-distribution inserts), 70 % queries (k-NN k in {1,10,100}, range count,
+    range list; counts log-uniform in qry, range lists capped at rep_max)."""
+    from paper_2601_05347_gb300 import serve
+    n = len(base)
+    u = gen.splitmix64(seed, np.arange(4 * R, dtype=np.uint64)) >> np.uint64(11)
+    u = u.astype(np.float64) / float(1 << 53)
+    perm_seed = gen.stream_seed(seed, 99)
+    order = gen.sample_without_replacement(n, min(n, 2_000_000), perm_seed)
+    dpos, next_id, reqs = 0, n, []
+    h = half_side or 1 << 14
+
+    def logu(x, lo, hi):
+        return int(np.exp(np.log(lo) + x * (np.log(hi) - np.log(lo))))
+
+    for t in range(R):
+        kind_u, size_u, k_u = u[4 * t], u[4 * t + 1], u[4 * t + 2]
+        if kind_u < 0.3:
+            m = logu(size_u, *upd)
+            if t % 2 == 0:
+                xr = (1 << (BITS - 1), 1 << BITS) if t % 4 == 0 else (0, 1 << (BITS - 1))
+                p = gen.varden(m, 2, BITS, seed + t, x_range=xr)
+                reqs.append(serve.Request("insert", p, np.arange(next_id, next_id + m, dtype=np.uint32)))
+                next_id += m
+            else:
+                m = min(m, len(order) - dpos)
+                take = order[dpos:dpos + m]
+                dpos += m
+                reqs.append(serve.Request("delete", base[take], take.astype(np.uint32)))
+        else:
+            nq = logu(size_u, *qry)
+            c = base[gen.sample_with_replacement(n, nq, seed + 7 * t)]
+            if kind_u < 0.65:
+                reqs.append(serve.Request("knn", c, k=[1, 10, 100][int(k_u * 3)]))
+            elif kind_u < 0.85:
+                reqs.append(serve.Request("count", gen.centred_boxes(c, h, BITS)))
+            else:
+                reqs.append(serve.Request("report", gen.centred_boxes(c[: int(rep_max)], h, BITS)))
+    return reqs
+
+
+def run_served(n_base: int, R: int, rank: int = 0, upd=(1e3, 1e5), qry=(1e2, 1e5), util=0.7):
+    import threading
+
+    import torch
+    from paper_2601_05347_gb300 import psi, serve
+    dev = torch.device("cuda", torch.cuda.current_device())
+    base = gen.varden(n_base, 2, BITS, gen.config_seed(4, 0, rank), x_range=(0, 1 << (BITS - 1)))
+    ids = np.arange(n_base, dtype=np.uint32)
+    h = gen.half_side_for_count(base, 1000, gen.config_seed(4, 1, rank))
+    reqs = served_requests(base, R, gen.config_seed(4, 2, rank), upd, qry, half_side=h)
+    dp = torch.from_numpy(base).to(dev)
+    di = torch.from_numpy(ids.view(np.int32)).to(dev)
+
+    def fresh():
+        ix = psi.Index(dp, di, kind="spac_h", leaf_size=32)
+        torch.cuda.synchronize()
+        return ix
+
+    def clone(r):
+        return serve.Request(r.kind, r.a, r.b, r.k)
+
+    # calibrate: plain service time of the whole list, back to back
+    ix = fresh()
+    t0 = time.perf_counter()
+    for r in reqs:
+        serve.serve_plain(ix, clone(r))
+    torch.cuda.synchronize()
+    busy = time.perf_counter() - t0
+    ix.close()
+    lam = util * len(reqs) / busy
+    gaps = -np.log(1.0 - (gen.splitmix64(gen.config_seed(4, 3, rank), np.arange(R, dtype=np.uint64))
+                          >> np.uint64(11)).astype(np.float64) / float(1 << 53)) / lam
+    arrive = np.cumsum(gaps)
+
+    # plain: one request at a time, in arrival order
+    ix = fresh()
+    plain = [clone(r) for r in reqs]
+    t0 = time.perf_counter()
+    for r, a in zip(plain, arrive):
+        now = time.perf_counter() - t0
+        if now < a:
+            time.sleep(a - now)
+        r.arrival = t0 + a
+        serve.serve_plain(ix, r)
+        r.done = time.perf_counter()
+    plain_s = time.perf_counter() - t0
+    ix.close()
+
+    # served: continuous batching
+    ix = fresh()
+    srv = serve.Server(ix)
+    served = [clone(r) for r in reqs]
+
+    def producer():
+        t0p = time.perf_counter()
+        for r, a in zip(served, arrive):
+            now = time.perf_counter() - t0p
+            if now < a:
+                time.sleep(a - now)
+            srv.submit(r)
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    for r in served:
+        r.future.result(timeout=600)
+    served_s = time.perf_counter() - t0
+    srv.close()
+    ix.close()
+    # the same requests in the same order: every answer must be identical
+    identical = True
+    ix2 = fresh()
+    for r, b in zip(plain, served):
+        got = b.future.result()
+        want = serve.serve_plain(ix2, clone(r))
+        if r.kind == "knn":
+            identical &= bool((got[0] == want[0]).all() and (got[1] == want[1]).all())
+        elif r.kind == "count":
+            identical &= bool((got == want).all())
+        elif r.kind == "delete":
+            identical &= got == want
+        elif r.kind == "report":
+            identical &= bool((got[0] == want[0]).all()) and sorted(got[1].tolist()) == sorted(want[1].tolist())
+    ix2.close()
+    per = {}
+    for kind in serve.KINDS:
+        per[kind] = {"plain": serve.percentiles(plain, kind), "served": serve.percentiles(served, kind)}
+    return {"resident_points": n_base, "requests": R, "arrival_rate_per_s": round(lam, 1),
+            "plain_utilisation_target": util,
+            "throughput_req_per_s": {"plain": round(R / plain_s, 1), "served": round(R / served_s, 1)},
+            "latency": per, "all": {"plain": serve.percentiles(plain), "served": serve.percentiles(served)},
+            "rounds": len(srv.rounds), "mean_requests_per_round": round(R / max(1, len(srv.rounds)), 2),
+            "results_identical": identical}
+
+
+# ---------------------------------------------------------------------------
 # oracle timings (the CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 def oracle_sample_step(w, host, frac: float):
@@ -553,9 +696,23 @@ def main():
     ap.add_argument("--batched-indexes", type=int, default=512,
                     help="indexes in the batched-form comparison of the default line")
     ap.add_argument("--batched", action="store_true", help="only the 4096-index batched configuration")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-points", type=int, default=20_000_000)
+    ap.add_argument("--served-requests", type=int, default=300)
+    ap.add_argument("--serve", action="store_true", help="only the served configuration at 5e8 resident points")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import __graft_entry__
+        __graft_entry__.build()
+        r = run_served(500_000_000, 1000, 0, upd=(1e3, 1e7), qry=(1e2, 1e6))
+        print(json.dumps({"metric": "served p50/p99 latency, 5e8 resident 2D points", "value": r["all"]["served"]["p99_ms"],
+                          "unit": "ms (p99, all requests)", "n_gpus": 1, "higher_is_better": False,
+                          "config": {"workload": "served: SPaC-H, 5e8 Varden points, Poisson mixed stream"},
+                          "served": r}), flush=True)
     elif args.batched:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
