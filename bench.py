@@ -502,7 +502,73 @@ def served_requests(base, R, seed, upd=(1e3, 1e5), qry=(1e2, 1e5), rep_max=1e4, 
     return reqs
 
 
-def run_served(n_base: int, R: int, rank: int = 0, upd=(1e3, 1e5), qry=(1e2, 1e5), util=0.7):
+def served_at_load(reqs, fresh, clone, lam, rank):
+    """One Poisson arrival sequence at rate lam through the plain form and the server."""
+    import threading
+
+    import torch
+    from paper_2601_05347_gb300 import serve
+    R = len(reqs)
+    gaps = -np.log(1.0 - (gen.splitmix64(gen.config_seed(4, 3, rank), np.arange(R, dtype=np.uint64))
+                          >> np.uint64(11)).astype(np.float64) / float(1 << 53)) / lam
+    arrive = np.cumsum(gaps)
+    ix = fresh()
+    plain = [clone(r) for r in reqs]
+    t0 = time.perf_counter()
+    for r, a in zip(plain, arrive):
+        now = time.perf_counter() - t0
+        if now < a:
+            time.sleep(a - now)
+        r.arrival = t0 + a
+        serve.serve_plain(ix, r)
+        r.done = time.perf_counter()
+    plain_s = time.perf_counter() - t0
+    ix.close()
+    ix = fresh()
+    srv = serve.Server(ix)
+    served = [clone(r) for r in reqs]
+
+    def producer():
+        t0p = time.perf_counter()
+        for r, a in zip(served, arrive):
+            now = time.perf_counter() - t0p
+            if now < a:
+                time.sleep(a - now)
+            srv.submit(r)
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    for r in served:
+        r.future.result(timeout=600)
+    served_s = time.perf_counter() - t0
+    srv.close()
+    ix.close()
+    identical = True
+    ix2 = fresh()
+    for r, b in zip(plain, served):
+        got = b.future.result()
+        want = serve.serve_plain(ix2, clone(r))
+        if r.kind == "knn":
+            identical &= bool((got[0] == want[0]).all() and (got[1] == want[1]).all())
+        elif r.kind == "count":
+            identical &= bool((got == want).all())
+        elif r.kind == "delete":
+            identical &= got == want
+        elif r.kind == "report":
+            identical &= bool((got[0] == want[0]).all()) and sorted(got[1].tolist()) == sorted(want[1].tolist())
+    ix2.close()
+    per = {kind: {"plain": serve.percentiles(plain, kind), "served": serve.percentiles(served, kind)}
+           for kind in serve.KINDS}
+    return {"arrival_rate_per_s": round(lam, 1),
+            "throughput_req_per_s": {"plain": round(R / plain_s, 1), "served": round(R / served_s, 1)},
+            "all": {"plain": serve.percentiles(plain), "served": serve.percentiles(served)}, "latency": per,
+            "rounds": len(srv.rounds), "mean_requests_per_round": round(R / max(1, len(srv.rounds)), 2),
+            "identical": identical}
+
+
+def run_served(n_base: int, R: int, rank: int = 0, upd=(1e3, 1e5), qry=(1e2, 1e5), loads=(0.7, 1.0, 1.3)):
     import threading
 
     import torch
@@ -531,70 +597,15 @@ def run_served(n_base: int, R: int, rank: int = 0, upd=(1e3, 1e5), qry=(1e2, 1e5
     torch.cuda.synchronize()
     busy = time.perf_counter() - t0
     ix.close()
-    lam = util * len(reqs) / busy
-    gaps = -np.log(1.0 - (gen.splitmix64(gen.config_seed(4, 3, rank), np.arange(R, dtype=np.uint64))
-                          >> np.uint64(11)).astype(np.float64) / float(1 << 53)) / lam
-    arrive = np.cumsum(gaps)
-
-    # plain: one request at a time, in arrival order
-    ix = fresh()
-    plain = [clone(r) for r in reqs]
-    t0 = time.perf_counter()
-    for r, a in zip(plain, arrive):
-        now = time.perf_counter() - t0
-        if now < a:
-            time.sleep(a - now)
-        r.arrival = t0 + a
-        serve.serve_plain(ix, r)
-        r.done = time.perf_counter()
-    plain_s = time.perf_counter() - t0
-    ix.close()
-
-    # served: continuous batching
-    ix = fresh()
-    srv = serve.Server(ix)
-    served = [clone(r) for r in reqs]
-
-    def producer():
-        t0p = time.perf_counter()
-        for r, a in zip(served, arrive):
-            now = time.perf_counter() - t0p
-            if now < a:
-                time.sleep(a - now)
-            srv.submit(r)
-
-    t0 = time.perf_counter()
-    th = threading.Thread(target=producer)
-    th.start()
-    th.join()
-    for r in served:
-        r.future.result(timeout=600)
-    served_s = time.perf_counter() - t0
-    srv.close()
-    ix.close()
-    # the same requests in the same order: every answer must be identical
+    capacity = len(reqs) / busy  # plain form, requests per second, back to back
+    out_loads = {}
     identical = True
-    ix2 = fresh()
-    for r, b in zip(plain, served):
-        got = b.future.result()
-        want = serve.serve_plain(ix2, clone(r))
-        if r.kind == "knn":
-            identical &= bool((got[0] == want[0]).all() and (got[1] == want[1]).all())
-        elif r.kind == "count":
-            identical &= bool((got == want).all())
-        elif r.kind == "delete":
-            identical &= got == want
-        elif r.kind == "report":
-            identical &= bool((got[0] == want[0]).all()) and sorted(got[1].tolist()) == sorted(want[1].tolist())
-    ix2.close()
-    per = {}
-    for kind in serve.KINDS:
-        per[kind] = {"plain": serve.percentiles(plain, kind), "served": serve.percentiles(served, kind)}
-    return {"resident_points": n_base, "requests": R, "arrival_rate_per_s": round(lam, 1),
-            "plain_utilisation_target": util,
-            "throughput_req_per_s": {"plain": round(R / plain_s, 1), "served": round(R / served_s, 1)},
-            "latency": per, "all": {"plain": serve.percentiles(plain), "served": serve.percentiles(served)},
-            "rounds": len(srv.rounds), "mean_requests_per_round": round(R / max(1, len(srv.rounds)), 2),
+    for util in loads:
+        r1 = served_at_load(reqs, fresh, clone, util * capacity, rank)
+        identical &= r1.pop("identical")
+        out_loads[f"{util:.1f}x"] = r1
+    return {"resident_points": n_base, "requests": R, "plain_capacity_req_per_s": round(capacity, 1),
+            "loads": out_loads,
             "results_identical": identical}
 
 

@@ -48,30 +48,43 @@ class Request:
 
 
 def _dev(a: np.ndarray, dev, stream) -> torch.Tensor:
+    """Host array -> device tensor, copied on `stream` (pageable source)."""
     a = np.ascontiguousarray(a)
     if a.dtype == np.uint32:
         a = a.view(np.int32)
     with torch.cuda.stream(stream):
-        return torch.from_numpy(a).pin_memory().to(dev, non_blocking=True)
+        return torch.from_numpy(a).to(dev)
 
 
 class Server:
     """Continuous-batching request loop around a psi.Index."""
 
-    def __init__(self, index: "psi.Index", mem_budget: int | None = None, query_streams: int = 3):
+    def __init__(self, index: "psi.Index", mem_budget: int | None = None, query_streams: int = 1,
+                 stage_bytes: int = 256 << 20):
         self.ix = index
         self.dev = torch.device("cuda", torch.cuda.current_device())
         free, _ = torch.cuda.mem_get_info(self.dev)
         self.budget = int(mem_budget if mem_budget is not None else 0.5 * free)
         self.main = torch.cuda.Stream(self.dev)
         self.qs = [torch.cuda.Stream(self.dev) for _ in range(query_streams)]
+        self.copy = torch.cuda.Stream(self.dev)  # result copies: updates never wait on them
+        # pinned staging: two input halves used alternately by the worker, one
+        # result buffer used by the finisher (larger payloads fall back to pageable copies)
+        self.stage_in = [torch.empty(stage_bytes // 2, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        self.stage_in_ev = [None, None]
+        self.stage_turn = 0
+        self.stage_out = torch.empty(stage_bytes, dtype=torch.uint8, pin_memory=True)
         self.pending = collections.deque()
         self.lock = threading.Condition()
         self.seq = 0
         self.stop_flag = False
         self.rounds = []  # (admitted, epochs) per round, for inspection
+        self.completions = collections.deque()
+        self.cv_done = threading.Condition()
         self.worker = threading.Thread(target=self._loop, daemon=True)
+        self.finisher = threading.Thread(target=self._finish_loop, daemon=True)
         self.worker.start()
+        self.finisher.start()
 
     # -- client side -------------------------------------------------------
     def submit(self, req: Request) -> Future:
@@ -91,6 +104,10 @@ class Server:
             self.stop_flag = True
             self.lock.notify()
         self.worker.join()
+        with self.cv_done:
+            self.completions.append(None)
+            self.cv_done.notify()
+        self.finisher.join()
 
     # -- worker --------------------------------------------------------------
     def _admit(self):
@@ -130,12 +147,34 @@ class Server:
                     if not r.future.done():
                         r.future.set_exception(e)
 
+    def _to_dev(self, a: np.ndarray, s) -> torch.Tensor:
+        """Host array -> device through a pinned staging half (async on s)."""
+        a = np.ascontiguousarray(a)
+        if a.dtype == np.uint32:
+            a = a.view(np.int32)
+        half = self.stage_in[self.stage_turn]
+        if a.nbytes > half.numel():
+            return _dev(a, self.dev, s)
+        ev = self.stage_in_ev[self.stage_turn]
+        if ev is not None:
+            ev.synchronize()  # the previous copy out of this half is done
+        view = half[: a.nbytes]
+        view.numpy()[:] = a.reshape(-1).view(np.uint8)
+        with torch.cuda.stream(s):
+            t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, device=self.dev)
+            t.view(-1).view(torch.uint8).copy_(view, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        self.stage_in_ev[self.stage_turn] = ev
+        self.stage_turn ^= 1
+        return t
+
     def _run_update(self, r: Request):
         s = self.main
         for q in self.qs:
             s.wait_stream(q)
-        pts = _dev(r.a, self.dev, s)
-        ids = _dev(r.b, self.dev, s)
+        pts = self._to_dev(r.a, s)
+        ids = self._to_dev(r.b, s)
         with torch.cuda.stream(s):
             if r.kind == "insert":
                 self.ix.insert(pts, ids, stream=s)
@@ -159,21 +198,50 @@ class Server:
             s.wait_stream(self.main)  # the tree state of this epoch
             cat = np.concatenate([r.a for r in rs])
             offs = np.cumsum([0] + [len(r.a) for r in rs])
-            x = _dev(cat, self.dev, s)
+            x = self._to_dev(cat, s)
             with torch.cuda.stream(s):
                 if kind == "knn":
-                    ids, d2 = self.ix.knn(x, k, stream=s)
-                    out = (ids.to("cpu", non_blocking=True), d2.to("cpu", non_blocking=True))
+                    out = self.ix.knn(x, k, stream=s)
                 elif kind == "count":
-                    out = (self.ix.range_count(x, stream=s).to("cpu", non_blocking=True),)
+                    out = (self.ix.range_count(x, stream=s),)
                 else:
-                    off, rid = self.ix.range_report(x, stream=s)
-                    out = (off.to("cpu", non_blocking=True), rid.to("cpu", non_blocking=True))
+                    out = self.ix.range_report(x, stream=s)
                 ev = torch.cuda.Event()
                 ev.record(s)
-            launched.append((kind, rs, offs, out, ev))
-        for kind, rs, offs, out, ev in launched:
-            ev.synchronize()
+            launched.append((kind, rs, offs, out, ev, x))
+        # results are copied back and handed out by the finisher thread, so
+        # the worker can launch the next epoch meanwhile
+        with self.cv_done:
+            self.completions.append(launched)
+            self.cv_done.notify()
+
+    def _finish_loop(self):
+        while True:
+            with self.cv_done:
+                while not self.completions:
+                    self.cv_done.wait()
+                launched = self.completions.popleft()
+            if launched is None:
+                return
+            self._finish(launched)
+
+    def _finish(self, launched):
+        for kind, rs, offs, dout, ev, _keep in launched:
+            with torch.cuda.stream(self.copy):  # device-to-host reads after the group's kernels
+                self.copy.wait_event(ev)
+                total = sum(t.numel() * t.element_size() for t in dout)
+                if total <= self.stage_out.numel():
+                    outs, pos = [], 0
+                    for t in dout:
+                        nb = t.numel() * t.element_size()
+                        dst = self.stage_out[pos: pos + nb]
+                        dst.copy_(t.contiguous().view(-1).view(torch.uint8), non_blocking=True)
+                        outs.append((dst, t.dtype, t.shape))
+                        pos += nb
+                    self.copy.synchronize()
+                    out = tuple(torch.from_numpy(d.numpy().copy()).view(dt).reshape(sh) for d, dt, sh in outs)
+                else:
+                    out = tuple(t.cpu() for t in dout)
             now = time.perf_counter()
             for j, r in enumerate(rs):
                 a, b = offs[j], offs[j + 1]
