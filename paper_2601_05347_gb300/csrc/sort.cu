@@ -9,8 +9,9 @@
 //   * k_sort_hist     reads every key once (computing it from the point when
 //                     encoding) and accumulates all digit histograms;
 //   * k_hist_scan     turns them into per-digit global bases;
-//   * k_onesweep      per digit: warp-level ranking with match.any into per-warp
-//                     shared counters (stable), tile totals published to a
+//   * k_onesweep      per digit: warp-level ranking (peer lanes from one ballot
+//                     per digit bit) into per-warp shared counters (stable),
+//                     tile totals published to a
 //                     look-back table, bounded spin on predecessors, shared-
 //                     memory staging so that each digit's run is written out
 //                     contiguously.
@@ -37,6 +38,7 @@ constexpr int SW = ST / 32;
 constexpr int MAX_PASSES = 8;
 
 constexpr uint32_t LB_AGG = 1u << 30, LB_PRE = 2u << 30, LB_VAL = (1u << 30) - 1;
+constexpr int LB_W = 8;  // predecessor tiles read per look-back step
 
 static_assert(RADIX == ST, "one digit per thread in the tile epilogue");
 
@@ -147,6 +149,10 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
   const int tile_n = (int)min((int64_t)TILE, a.n - base);
   const int wbase = w * (SI * 32);
 
+  if (MODE == 0) {  // the values are read after the keys are written: start them towards L2 now
+    for (int i = tid * 32; i < tile_n; i += ST * 32)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.vin + base + i));
+  }
   uint64_t key[SI];
 #pragma unroll
   for (int j = 0; j < SI; ++j) {
@@ -174,12 +180,22 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
     const int li = wbase + j * 32 + lane;
     const bool valid = li < tile_n;
     const uint32_t dg = valid ? ((uint32_t)(key[j] >> a.shift) & (RADIX - 1)) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+    // lanes holding the same digit, from one ballot per digit bit
+    uint32_t peers = __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, (dg >> b) & 1u);
+      peers &= ((dg >> b) & 1u) ? m : ~m;
+    }
+    // the lowest lane of each group reads and advances the warp's counter;
+    // the shuffle hands the old count to the group (and orders the warp)
     const uint32_t before = __popc(peers & lanemask_lt());
-    const uint32_t wb = valid ? s_wh[w][dg] : 0u;
-    __syncwarp();
-    if (valid && before == 0) s_wh[w][dg] = wb + __popc(peers);
-    __syncwarp();
+    uint32_t wb = 0;
+    if (valid && before == 0) {
+      wb = s_wh[w][dg];
+      s_wh[w][dg] = wb + __popc(peers);
+    }
+    wb = __shfl_sync(0xFFFFFFFFu, wb, valid ? __ffs(peers) - 1 : lane);
     rank[j] = wb + before;
   }
   __syncthreads();
@@ -212,23 +228,40 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
     const uint32_t excl = before + x - cnt;
     s_off[d] = excl;
 
+    // Look-back: read the words of up to LB_W predecessor tiles at once
+    // (independent loads), then fold them newest first until a tile that has
+    // published its inclusive prefix; a tile not published yet is re-read
+    // (bounded spin).
     uint32_t prev = 0;
     if (tile > 0) {
       int64_t t = (int64_t)tile - 1;
       uint32_t spins = 0;
-      while (t >= 0) {
-        const uint32_t v = ld_relaxed_u32(a.lookback + (size_t)t * RADIX + d);
-        if ((v & (LB_AGG | LB_PRE)) == 0) {
+      bool done = false;
+      while (!done && t >= 0) {
+        uint32_t v[LB_W];
+#pragma unroll
+        for (int u = 0; u < LB_W; ++u)
+          v[u] = (t - u >= 0) ? ld_relaxed_u32(a.lookback + (size_t)(t - u) * RADIX + d) : LB_PRE;
+        int u = 0;
+        for (; u < LB_W && t - u >= 0; ++u) {
+          if ((v[u] & (LB_AGG | LB_PRE)) == 0) break;  // not yet published: re-read from here
+          prev += v[u] & LB_VAL;
+          if (v[u] & LB_PRE) {
+            done = true;
+            break;
+          }
+        }
+        if (done) break;
+        if (u < LB_W && t - u >= 0) {
+          t -= u;
           if (++spins > kSpinLimit) {
             atomicOr(a.status, ST_TIMEOUT);
             break;
           }
           if (spins > 64) __nanosleep(64);
-          continue;
+        } else {
+          t -= LB_W;
         }
-        prev += v & LB_VAL;
-        if (v & LB_PRE) break;
-        --t;
       }
       st_relaxed_u32(my, LB_PRE | ((prev + cnt) & LB_VAL));
     }
