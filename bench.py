@@ -130,10 +130,10 @@ def kernel_bytes(name: str, w, launches: int) -> float | None:
     """
     n, mi, md = w["n"], w["m_ins"], w["m_del"]
     if name == "k_onesweep":
-        # sorts per step: build (n), insert batch (mi), delete batch (md), query order (n_knn); 8 passes each
-        items = [n, mi, md, w["n_knn"]]
-        per_sort = [20 + 7 * 24 for _ in items]
-        return float(sum(i * b for i, b in zip(items, per_sort)))
+        # sorts per step at 8-bit digits: build, insert batch, delete batch (60-bit keys, 8 passes)
+        # and the query order (top 48 key bits, 6 passes); the first pass of each reads points
+        sorts = [(n, 8), (mi, 8), (md, 8), (w["n_knn"], 6)]
+        return float(sum(items * (20 + (passes - 1) * 24) for items, passes in sorts))
     if name == "k_sort_hist":
         return float(8 * (n + mi + md + w["n_knn"]))
     if name == "k_leaf_gather":

@@ -181,8 +181,8 @@ static psi_status validate_cfg(const psi_config *c) {
     set_error("fanout must be 0 (default 32) or in [2, 32]");
     return PSI_ERR_INVALID;
   }
-  if (c->radix_bits != 0 && c->radix_bits != 8) {
-    set_error("radix_bits must be 0 or 8");
+  if (c->radix_bits != 0 && c->radix_bits != 8 && c->radix_bits != 10 && c->radix_bits != 11) {
+    set_error("radix_bits must be 0 (8), 8, 10 or 11");
     return PSI_ERR_INVALID;
   }
   return PSI_OK;

@@ -287,7 +287,7 @@ psi_status spac_build_fresh(psi_index *ix, const int32_t *pts, const uint32_t *i
   if ((st = k0.alloc(n, s)) || (st = k1.alloc(n, s)) || (st = v0.alloc(n, s)) || (st = v1.alloc(n, s))) return st;
   SortResult r;
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, n, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
-                       ix->d_status, s, &r)))
+                       ix->d_status, s, &r, ix->cfg.radix_bits)))
     return st;
   return spac_from_sorted(ix, r.keys, r.vals, pts, ids, n, s);
 }

@@ -145,7 +145,7 @@ struct SortResult {
 // The result lives in one of the two caller-provided buffer pairs.
 psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint32_t *vals_in, int64_t n,
                       int key_bits, const uint32_t *tie_ids, uint64_t *kbuf0, uint32_t *vbuf0, uint64_t *kbuf1,
-                      uint32_t *vbuf1, int *d_status, cudaStream_t s, SortResult *out);
+                      uint32_t *vbuf1, int *d_status, cudaStream_t s, SortResult *out, int radix_bits = 0);
 
 // Device-wide exclusive scan of int64 values (out may alias in); writes the
 // grand total to d_total if non-null.

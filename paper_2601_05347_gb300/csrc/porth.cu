@@ -436,7 +436,7 @@ psi_status porth_build(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   if ((st = k0.alloc(n, s)) || (st = k1.alloc(n, s)) || (st = v0.alloc(n, s)) || (st = v1.alloc(n, s))) return st;
   SortResult r;
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, n, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
-                       ix->d_status, s, &r)))
+                       ix->d_status, s, &r, ix->cfg.radix_bits)))
     return st;
   if (ix->D == 2)
     PSI_LAUNCH_NAMED("k_porth_gather", k_porth_gather<2>, grid_for(n), 256, 0, s, r.keys, r.vals, pts, ids, n,
@@ -455,7 +455,7 @@ psi_status porth_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, 
   if ((st = k0.alloc(m, s)) || (st = k1.alloc(m, s)) || (st = v0.alloc(m, s)) || (st = v1.alloc(m, s))) return st;
   SortResult r;
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, m, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
-                       ix->d_status, s, &r)))
+                       ix->d_status, s, &r, ix->cfg.radix_bits)))
     return st;
   Buf<int64_t> brank, shift;
   Buf<int32_t> delta;
@@ -493,7 +493,7 @@ psi_status porth_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, 
   if ((st = k0.alloc(m, s)) || (st = k1.alloc(m, s)) || (st = v0.alloc(m, s)) || (st = v1.alloc(m, s))) return st;
   SortResult r;
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, m, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
-                       ix->d_status, s, &r)))
+                       ix->d_status, s, &r, ix->cfg.radix_bits)))
     return st;
   Buf<int32_t> keep;
   Buf<int64_t> pos, tot;

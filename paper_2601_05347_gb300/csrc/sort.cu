@@ -21,6 +21,7 @@
 // k_tie_long (a later canonical leaf layout depends on it).
 #include "common.cuh"
 #include <mutex>
+#include <type_traits>
 
 #include "bitonic.cuh"
 #include "keys.cuh"
@@ -29,18 +30,39 @@ namespace psi {
 
 namespace {
 
-constexpr int RB = 8;
-constexpr int RADIX = 1 << RB;
 constexpr int ST = 256;        // threads per sort tile
 constexpr int SI = 16;         // keys per thread
 constexpr int TILE = ST * SI;  // 4096 keys per tile
 constexpr int SW = ST / 32;
-constexpr int MAX_PASSES = 8;
+constexpr int MAX_PASSES = 8;  // 64-bit keys at 8-bit digits
 
 constexpr uint32_t LB_AGG = 1u << 30, LB_PRE = 2u << 30, LB_VAL = (1u << 30) - 1;
 constexpr int LB_W = 8;  // predecessor tiles read per look-back step
 
-static_assert(RADIX == ST, "one digit per thread in the tile epilogue");
+// Digit width RB in {8, 10, 11}: RADIX digits, DPT digits per thread in the
+// tile epilogue; per-warp counters fit 16 bits (a warp ranks 512 keys).
+template <int RB>
+struct Radix {
+  static constexpr int RADIX = 1 << RB;
+  static constexpr int DPT = RADIX / ST;
+  static constexpr int PASSES64 = (64 + RB - 1) / RB;
+  static constexpr int HIST_PARTS = RB == 8 ? 4 : 1;
+  using Count = typename std::conditional<RB == 8, uint32_t, uint16_t>::type;
+  using Digit = typename std::conditional<RB == 8, uint8_t, uint16_t>::type;
+};
+
+template <int RB>
+struct OnesweepSmem {
+  using R = Radix<RB>;
+  typename R::Count wh[SW][R::RADIX];  // per-warp digit counters, then warp offsets
+  uint32_t off[R::RADIX];              // tile-exclusive digit offsets
+  uint32_t glob[R::RADIX];             // global position minus tile-local position
+  alignas(16) uint64_t stage[TILE];    // keys (then values) in digit order
+  typename R::Digit dig[TILE];         // digit of each staged position
+  uint32_t wsum[SW];
+  uint8_t htab[256];
+  uint32_t tile;
+};
 
 struct PassArgs {
   const uint64_t *kin;
@@ -53,25 +75,27 @@ struct PassArgs {
   int64_t n;
   int shift;
   const uint32_t *gbase;  // [RADIX] global exclusive digit offsets of this pass
-  uint32_t *lookback;     // [tiles][RADIX]
+  uint32_t *lookback;     // [tiles][RADIX] of this pass, zero on entry
+  uint32_t *lookback_next;  // table of the next pass: this pass zeroes it (or null)
   uint32_t *tile_ctr;
   int *status;
 };
 
-// Digit histograms go to HIST_PARTS copies in shared memory (lane % HIST_PARTS
-// picks the copy), so lanes of a warp that hit the same digit -- the common case
-// for the top digits of clustered input -- rarely collide on one address.
-constexpr int HIST_PARTS = 4;
-
-template <int MODE, int D, int CURVE>
+// Digit histograms of all passes in one read.  With 8-bit digits the counts go
+// to 4 shared copies (lane % 4 picks one) so that lanes of a warp hitting the
+// same digit -- common for the top digits of clustered input -- rarely collide.
+template <int MODE, int D, int CURVE, int RB>
 __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const int32_t *pts, int bits, int key_shift,
                                                    int64_t n, int passes, uint32_t *hist, int *status) {
-  __shared__ uint32_t shp[HIST_PARTS][MAX_PASSES][RADIX];
-  __shared__ uint8_t htab[256];
-  for (int i = threadIdx.x; i < HIST_PARTS * MAX_PASSES * RADIX; i += blockDim.x) (&shp[0][0][0])[i] = 0;
+  using R = Radix<RB>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][passes][RADIX]
+  uint8_t *htab = smem_raw + sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX;
+  for (int i = threadIdx.x; i < R::HIST_PARTS * passes * R::RADIX; i += blockDim.x) shp[i] = 0;
   if (MODE == 1 && CURVE == 1) hilbert_table_init(htab);
   __syncthreads();
   bool bad_any = false;
+  uint32_t *mine = shp + (threadIdx.x % R::HIST_PARTS) * passes * R::RADIX;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     int64_t i = i0 + threadIdx.x;
@@ -88,34 +112,41 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
         bad_any |= bad;
       }
       const uint32_t act = __activemask();
-      uint32_t(*sh)[RADIX] = shp[threadIdx.x % HIST_PARTS];
       for (int p = 0; p < passes; ++p) {
-        uint32_t dg = (uint32_t)(k >> (p * RB)) & (RADIX - 1);
+        uint32_t dg = (uint32_t)(k >> (p * RB)) & (R::RADIX - 1);
         int all_same;
         __match_all_sync(act, dg, &all_same);
         if (all_same) {
-          if ((lanemask_lt() & act) == 0) atomicAdd(&shp[0][p][dg], (uint32_t)__popc(act));
+          if ((lanemask_lt() & act) == 0) atomicAdd(&shp[p * R::RADIX + dg], (uint32_t)__popc(act));
         } else {
-          atomicAdd(&sh[p][dg], 1u);
+          atomicAdd(&mine[p * R::RADIX + dg], 1u);
         }
       }
     }
   }
   if (bad_any) atomicOr(status, ST_RANGE);
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
+  for (int i = threadIdx.x; i < passes * R::RADIX; i += blockDim.x) {
     uint32_t v = 0;
 #pragma unroll
-    for (int q = 0; q < HIST_PARTS; ++q) v += (&shp[q][0][0])[i];
+    for (int q = 0; q < R::HIST_PARTS; ++q) v += shp[q * passes * R::RADIX + i];
     if (v) atomicAdd(&hist[i], v);
   }
 }
 
-// One block per pass: exclusive scan of the pass's digit counts.
+// One block per pass: exclusive scan of the pass's digit counts (RADIX / blockDim per thread).
+template <int RB>
 __global__ void k_hist_scan(const uint32_t *hist, uint32_t *gbase) {
-  __shared__ uint32_t wsum[RADIX / 32];
-  const int p = blockIdx.x, d = threadIdx.x, lane = d & 31, w = d >> 5;
-  uint32_t c = hist[p * RADIX + d], x = c;
+  constexpr int RADIX = 1 << RB;
+  __shared__ uint32_t wsum[32];
+  const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int per = RADIX / blockDim.x;
+  uint32_t c[8], tot = 0;
+  for (int q = 0; q < per; ++q) {
+    c[q] = hist[p * RADIX + t * per + q];
+    tot += c[q];
+  }
+  uint32_t x = tot;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
@@ -125,26 +156,29 @@ __global__ void k_hist_scan(const uint32_t *hist, uint32_t *gbase) {
   __syncthreads();
   uint32_t before = 0;
   for (int i = 0; i < w; ++i) before += wsum[i];
-  gbase[p * RADIX + d] = before + x - c;
+  uint32_t run = before + x - tot;
+  for (int q = 0; q < per; ++q) {
+    gbase[p * RADIX + t * per + q] = run;
+    run += c[q];
+  }
 }
 
-template <int MODE, int D, int CURVE>
-__global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
-  __shared__ uint32_t s_wh[SW][RADIX];
-  __shared__ uint32_t s_off[RADIX];
-  __shared__ uint32_t s_glob[RADIX];
-  __shared__ __align__(16) uint64_t s_stage[TILE];
-  __shared__ uint8_t s_dig[TILE];  // digit of each staged position
-  __shared__ uint32_t s_wsum[SW];
-  __shared__ uint8_t s_htab[256];
-  __shared__ uint32_t s_tile;
+template <int MODE, int D, int CURVE, int RB>
+__global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
+  using R = Radix<RB>;
+  constexpr int RADIX = R::RADIX, DPT = R::DPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  OnesweepSmem<RB> &sm = *reinterpret_cast<OnesweepSmem<RB> *>(smem_raw);
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
-  for (int i = tid; i < SW * RADIX; i += ST) (&s_wh[0][0])[i] = 0;
-  if (MODE == 1 && CURVE == 1) hilbert_table_init(s_htab);
+  if (tid == 0) sm.tile = atomicAdd(a.tile_ctr, 1u);
+  {
+    uint32_t *z = reinterpret_cast<uint32_t *>(&sm.wh[0][0]);
+    for (int i = tid; i < (int)(sizeof(sm.wh) / 4); i += ST) z[i] = 0;
+  }
+  if (MODE == 1 && CURVE == 1) hilbert_table_init(sm.htab);
   __syncthreads();
-  const uint32_t tile = s_tile;
+  const uint32_t tile = sm.tile;
   const int64_t base = (int64_t)tile * TILE;
   const int tile_n = (int)min((int64_t)TILE, a.n - base);
   const int wbase = w * (SI * 32);
@@ -152,6 +186,9 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
   if (MODE == 0) {  // the values are read after the keys are written: start them towards L2 now
     for (int i = tid * 32; i < tile_n; i += ST * 32)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a.vin + base + i));
+  }
+  if (a.lookback_next) {  // the next pass's look-back words of this tile start at zero
+    for (int i = tid; i < RADIX; i += ST) a.lookback_next[(size_t)tile * RADIX + i] = 0;
   }
   uint64_t key[SI];
 #pragma unroll
@@ -167,7 +204,7 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
 #pragma unroll
         for (int d = 0; d < D; ++d) c[d] = a.pts[gi * D + d];
         bool bad;
-        key[j] = point_key<D, CURVE>(s_htab, c, a.bits, bad) >> a.key_shift;
+        key[j] = point_key<D, CURVE>(sm.htab, c, a.bits, bad) >> a.key_shift;
       }
     }
   }
@@ -192,80 +229,85 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
     const uint32_t before = __popc(peers & lanemask_lt());
     uint32_t wb = 0;
     if (valid && before == 0) {
-      wb = s_wh[w][dg];
-      s_wh[w][dg] = wb + __popc(peers);
+      wb = sm.wh[w][dg];
+      sm.wh[w][dg] = (typename R::Count)(wb + __popc(peers));
     }
     wb = __shfl_sync(0xFFFFFFFFu, wb, valid ? __ffs(peers) - 1 : lane);
     rank[j] = wb + before;
   }
   __syncthreads();
 
-  // Epilogue per digit (thread = digit): per-warp offsets, tile total,
-  // look-back publication, tile-local and global offsets.
+  // Epilogue: thread t owns digits [t*DPT, (t+1)*DPT): per-warp offsets, tile
+  // totals, look-back publication, tile-local and global offsets.
   {
-    const uint32_t d = tid;
-    uint32_t run = 0;
+    uint32_t cnt[DPT], tsum = 0;
 #pragma unroll
-    for (int ww = 0; ww < SW; ++ww) {
-      const uint32_t c = s_wh[ww][d];
-      s_wh[ww][d] = run;
-      run += c;
+    for (int q = 0; q < DPT; ++q) {
+      const int d = tid * DPT + q;
+      uint32_t run = 0;
+#pragma unroll
+      for (int ww = 0; ww < SW; ++ww) {
+        const uint32_t c = sm.wh[ww][d];
+        sm.wh[ww][d] = (typename R::Count)run;
+        run += c;
+      }
+      cnt[q] = run;
+      tsum += run;
+      st_relaxed_u32(a.lookback + (size_t)tile * RADIX + d, (tile == 0 ? LB_PRE : LB_AGG) | run);
     }
-    const uint32_t cnt = run;
-    uint32_t *my = a.lookback + (size_t)tile * RADIX + d;
-    st_relaxed_u32(my, (tile == 0 ? LB_PRE : LB_AGG) | cnt);
-
-    uint32_t x = cnt;
+    uint32_t x = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) s_wsum[w] = x;
+    if (lane == 31) sm.wsum[w] = x;
     __syncthreads();
-    uint32_t before = 0;
-    for (int i = 0; i < w; ++i) before += s_wsum[i];
-    const uint32_t excl = before + x - cnt;
-    s_off[d] = excl;
-
-    // Look-back: read the words of up to LB_W predecessor tiles at once
-    // (independent loads), then fold them newest first until a tile that has
-    // published its inclusive prefix; a tile not published yet is re-read
-    // (bounded spin).
-    uint32_t prev = 0;
-    if (tile > 0) {
-      int64_t t = (int64_t)tile - 1;
-      uint32_t spins = 0;
-      bool done = false;
-      while (!done && t >= 0) {
-        uint32_t v[LB_W];
+    uint32_t excl = x - tsum;
+    for (int i = 0; i < w; ++i) excl += sm.wsum[i];
 #pragma unroll
-        for (int u = 0; u < LB_W; ++u)
-          v[u] = (t - u >= 0) ? ld_relaxed_u32(a.lookback + (size_t)(t - u) * RADIX + d) : LB_PRE;
-        int u = 0;
-        for (; u < LB_W && t - u >= 0; ++u) {
-          if ((v[u] & (LB_AGG | LB_PRE)) == 0) break;  // not yet published: re-read from here
-          prev += v[u] & LB_VAL;
-          if (v[u] & LB_PRE) {
-            done = true;
-            break;
+    for (int q = 0; q < DPT; ++q) {
+      const int d = tid * DPT + q;
+      sm.off[d] = excl;
+      // Look-back: read the words of up to LB_W predecessor tiles at once,
+      // fold them newest first until a tile with its inclusive prefix; a tile
+      // not published yet is re-read (bounded spin).
+      uint32_t prev = 0;
+      if (tile > 0) {
+        int64_t t = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        bool done = false;
+        while (!done && t >= 0) {
+          uint32_t v[LB_W];
+#pragma unroll
+          for (int u = 0; u < LB_W; ++u)
+            v[u] = (t - u >= 0) ? ld_relaxed_u32(a.lookback + (size_t)(t - u) * RADIX + d) : LB_PRE;
+          int u = 0;
+          for (; u < LB_W && t - u >= 0; ++u) {
+            if ((v[u] & (LB_AGG | LB_PRE)) == 0) break;
+            prev += v[u] & LB_VAL;
+            if (v[u] & LB_PRE) {
+              done = true;
+              break;
+            }
+          }
+          if (done) break;
+          if (u < LB_W && t - u >= 0) {
+            t -= u;
+            if (++spins > kSpinLimit) {
+              atomicOr(a.status, ST_TIMEOUT);
+              break;
+            }
+            if (spins > 64) __nanosleep(64);
+          } else {
+            t -= LB_W;
           }
         }
-        if (done) break;
-        if (u < LB_W && t - u >= 0) {
-          t -= u;
-          if (++spins > kSpinLimit) {
-            atomicOr(a.status, ST_TIMEOUT);
-            break;
-          }
-          if (spins > 64) __nanosleep(64);
-        } else {
-          t -= LB_W;
-        }
+        st_relaxed_u32(a.lookback + (size_t)tile * RADIX + d, LB_PRE | ((prev + cnt[q]) & LB_VAL));
       }
-      st_relaxed_u32(my, LB_PRE | ((prev + cnt) & LB_VAL));
+      sm.glob[d] = a.gbase[d] + prev - excl;
+      excl += cnt[q];
     }
-    s_glob[d] = a.gbase[d] + prev - excl;
   }
   __syncthreads();
 
@@ -275,8 +317,8 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
     const int li = wbase + j * 32 + lane;
     if (li < tile_n) {
       const uint32_t dg = (uint32_t)(key[j] >> a.shift) & (RADIX - 1);
-      const uint32_t lp = s_off[dg] + s_wh[w][dg] + rank[j];
-      s_stage[lp] = key[j];
+      const uint32_t lp = sm.off[dg] + sm.wh[w][dg] + rank[j];
+      sm.stage[lp] = key[j];
       rank[j] = lp;
     }
   }
@@ -285,14 +327,14 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
   for (int i = 0; i < SI; ++i) {
     const int p = tid + i * ST;
     if (p < tile_n) {
-      const uint64_t k = s_stage[p];
+      const uint64_t k = sm.stage[p];
       const uint32_t dg = (uint32_t)(k >> a.shift) & (RADIX - 1);
-      s_dig[p] = (uint8_t)dg;
-      a.kout[s_glob[dg] + p] = k;
+      sm.dig[p] = (typename R::Digit)dg;
+      a.kout[sm.glob[dg] + p] = k;
     }
   }
   __syncthreads();
-  uint32_t *s_v = reinterpret_cast<uint32_t *>(s_stage);
+  uint32_t *s_v = reinterpret_cast<uint32_t *>(sm.stage);
 #pragma unroll
   for (int j = 0; j < SI; ++j) {
     const int li = wbase + j * 32 + lane;
@@ -302,7 +344,7 @@ __global__ __launch_bounds__(ST, 3) void k_onesweep(PassArgs a) {
 #pragma unroll
   for (int i = 0; i < SI; ++i) {
     const int p = tid + i * ST;
-    if (p < tile_n) a.vout[s_glob[s_dig[p]] + p] = s_v[p];
+    if (p < tile_n) a.vout[sm.glob[sm.dig[p]] + p] = s_v[p];
   }
 }
 
@@ -400,55 +442,64 @@ __global__ __launch_bounds__(1024) void k_tie_long(const uint64_t *keys, uint32_
 
 // ---------------------------------------------------------------------------
 
-template <int MODE, int D, int CURVE>
-static void launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_t n, int passes, uint32_t *hist,
-                        int *status, cudaStream_t s) {
+template <int MODE, int D, int CURVE, int RB>
+static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_t n, int passes, uint32_t *hist,
+                              int *status, cudaStream_t s) {
+  using R = Radix<RB>;
+  auto kern = k_sort_hist<MODE, D, CURVE, RB>;
+  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX + 256;
+  if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
-  PSI_LAUNCH_NAMED("k_sort_hist", (k_sort_hist<MODE, D, CURVE>), std::max(grid, 1), 256, 0, s, kin, enc.pts,
-                   enc.bits, enc.key_shift, n, passes, hist, status);
+  PSI_LAUNCH_NAMED("k_sort_hist", kern, std::max(grid, 1), 256, smem, s, kin, enc.pts, enc.bits, enc.key_shift, n,
+                   passes, hist, status);
+  return PSI_OK;
 }
 
-template <int MODE, int D, int CURVE>
-static void launch_pass(const PassArgs &a, int64_t tiles, cudaStream_t s) {
-  PSI_LAUNCH_NAMED("k_onesweep", (k_onesweep<MODE, D, CURVE>), (unsigned)tiles, ST, 0, s, a);
+template <int MODE, int D, int CURVE, int RB>
+static psi_status launch_pass(const PassArgs &a, int64_t tiles, cudaStream_t s) {
+  auto kern = k_onesweep<MODE, D, CURVE, RB>;
+  const size_t smem = sizeof(OnesweepSmem<RB>);
+  if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PSI_LAUNCH_NAMED("k_onesweep", kern, (unsigned)tiles, ST, smem, s, a);
+  return PSI_OK;
 }
 
-psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint32_t *vals_in, int64_t n,
-                      int key_bits, const uint32_t *tie_ids, uint64_t *kbuf0, uint32_t *vbuf0, uint64_t *kbuf1,
-                      uint32_t *vbuf1, int *d_status, cudaStream_t s, SortResult *out) {
-  out->keys = kbuf0;
-  out->vals = vbuf0;
-  if (n <= 0) return PSI_OK;
-  if (n >= (int64_t)LB_VAL) {
-    set_error("sort: more than 2^30-1 pairs in one sort");
-    return PSI_ERR_INVALID;
-  }
+// Digit width: 8 unless 10 or 11 is asked for.  Wider digits save passes but
+// measured slower per pass on GB300 with 4096-key tiles (1e8 pairs: 0.92 ms
+// at 8 bits, 1.67 ms at 10, 2.98 ms at 11): a tile's digit runs get too
+// short for whole-sector writes and each thread walks several look-back chains.
+static int pick_radix(int /*key_bits*/, int requested) {
+  return (requested == 10 || requested == 11) ? requested : 8;
+}
+
+template <int RB>
+static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, const uint32_t *vals_in, int64_t n,
+                                int key_bits, uint64_t *kbuf0, uint32_t *vbuf0, uint64_t *kbuf1, uint32_t *vbuf1,
+                                int *d_status, cudaStream_t s, SortResult *out) {
+  using R = Radix<RB>;
   const bool encode = enc.pts != nullptr;
-  if (encode && (enc.dim != 2 && enc.dim != 3)) return PSI_ERR_INVALID;
-  if (encode && enc.curve == CURVE_HILBERT && enc.dim != 2) return PSI_ERR_INVALID;
-  key_bits = std::max(1, std::min(64, key_bits));
   const int passes = (key_bits + RB - 1) / RB;
   const int64_t tiles = ceil_div(n, TILE);
-
   Buf<uint32_t> hist, gbase, lookback, ctr;
   psi_status st;
-  if ((st = hist.alloc((size_t)passes * RADIX, s))) return st;
-  if ((st = gbase.alloc((size_t)passes * RADIX, s))) return st;
-  if ((st = lookback.alloc((size_t)passes * tiles * RADIX, s))) return st;
-  if ((st = ctr.alloc(passes, s))) return st;
-  PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * passes * RADIX, s));
-  PSI_CK(cudaMemsetAsync(lookback.p, 0, sizeof(uint32_t) * passes * tiles * RADIX, s));
+  // two look-back tables used alternately: pass p clears the table of pass p+1
+  if ((st = hist.alloc((size_t)passes * R::RADIX, s)) || (st = gbase.alloc((size_t)passes * R::RADIX, s)) ||
+      (st = lookback.alloc((size_t)2 * tiles * R::RADIX, s)) || (st = ctr.alloc(passes, s)))
+    return st;
+  PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * passes * R::RADIX, s));
+  PSI_CK(cudaMemsetAsync(lookback.p, 0, sizeof(uint32_t) * tiles * R::RADIX, s));
   PSI_CK(cudaMemsetAsync(ctr.p, 0, sizeof(uint32_t) * passes, s));
 
   if (!encode)
-    launch_hist<0, 2, 0>(keys_in, enc, n, passes, hist.p, d_status, s);
+    st = launch_hist<0, 2, 0, RB>(keys_in, enc, n, passes, hist.p, d_status, s);
   else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
-    launch_hist<1, 2, 0>(nullptr, enc, n, passes, hist.p, d_status, s);
+    st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, passes, hist.p, d_status, s);
   else if (enc.dim == 2)
-    launch_hist<1, 2, 1>(nullptr, enc, n, passes, hist.p, d_status, s);
+    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, passes, hist.p, d_status, s);
   else
-    launch_hist<1, 3, 0>(nullptr, enc, n, passes, hist.p, d_status, s);
-  PSI_LAUNCH(k_hist_scan, passes, RADIX, 0, s, hist.p, gbase.p);
+    st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, passes, hist.p, d_status, s);
+  if (st) return st;
+  PSI_LAUNCH_NAMED("k_hist_scan", k_hist_scan<RB>, passes, std::min(R::RADIX, 1024), 0, s, hist.p, gbase.p);
 
   uint64_t *kb[2] = {kbuf0, kbuf1};
   uint32_t *vb[2] = {vbuf0, vbuf1};
@@ -463,21 +514,52 @@ psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint
     a.key_shift = enc.key_shift;
     a.n = n;
     a.shift = p * RB;
-    a.gbase = gbase.p + p * RADIX;
-    a.lookback = lookback.p + (size_t)p * tiles * RADIX;
+    a.gbase = gbase.p + p * R::RADIX;
+    a.lookback = lookback.p + (size_t)(p & 1) * tiles * R::RADIX;
+    a.lookback_next = p + 1 < passes ? lookback.p + (size_t)((p + 1) & 1) * tiles * R::RADIX : nullptr;
     a.tile_ctr = ctr.p + p;
     a.status = d_status;
     if (p > 0 || !encode)
-      launch_pass<0, 2, 0>(a, tiles, s);
+      st = launch_pass<0, 2, 0, RB>(a, tiles, s);
     else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
-      launch_pass<1, 2, 0>(a, tiles, s);
+      st = launch_pass<1, 2, 0, RB>(a, tiles, s);
     else if (enc.dim == 2)
-      launch_pass<1, 2, 1>(a, tiles, s);
+      st = launch_pass<1, 2, 1, RB>(a, tiles, s);
     else
-      launch_pass<1, 3, 0>(a, tiles, s);
+      st = launch_pass<1, 3, 0, RB>(a, tiles, s);
+    if (st) return st;
   }
   out->keys = kb[(passes - 1) & 1];
   out->vals = vb[(passes - 1) & 1];
+  return PSI_OK;
+}
+
+psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint32_t *vals_in, int64_t n,
+                      int key_bits, const uint32_t *tie_ids, uint64_t *kbuf0, uint32_t *vbuf0, uint64_t *kbuf1,
+                      uint32_t *vbuf1, int *d_status, cudaStream_t s, SortResult *out, int radix_bits) {
+  out->keys = kbuf0;
+  out->vals = vbuf0;
+  if (n <= 0) return PSI_OK;
+  if (n >= (int64_t)LB_VAL) {
+    set_error("sort: more than 2^30-1 pairs in one sort");
+    return PSI_ERR_INVALID;
+  }
+  const bool encode = enc.pts != nullptr;
+  if (encode && (enc.dim != 2 && enc.dim != 3)) return PSI_ERR_INVALID;
+  if (encode && enc.curve == CURVE_HILBERT && enc.dim != 2) return PSI_ERR_INVALID;
+  key_bits = std::max(1, std::min(64, key_bits));
+  psi_status st;
+  switch (pick_radix(key_bits, radix_bits)) {
+    case 10:
+      st = sort_pairs_rb<10>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out);
+      break;
+    case 11:
+      st = sort_pairs_rb<11>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out);
+      break;
+    default:
+      st = sort_pairs_rb<8>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out);
+  }
+  if (st) return st;
 
   if (tie_ids) {
     const int64_t cap_long = n / (kShortRun + 1) + 1;
@@ -611,6 +693,7 @@ constexpr int64_t kNoAllocTiles = (kNoAllocMaxPairs + TILE - 1) / TILE;
 constexpr size_t kOffKeys = 0;
 constexpr size_t kOffVals = kOffKeys + sizeof(uint64_t) * kNoAllocMaxPairs;
 constexpr size_t kOffHist = kOffVals + sizeof(uint32_t) * kNoAllocMaxPairs;
+constexpr int RADIX = Radix<8>::RADIX;
 constexpr size_t kOffBase = kOffHist + sizeof(uint32_t) * MAX_PASSES * RADIX;
 constexpr size_t kOffLook = kOffBase + sizeof(uint32_t) * MAX_PASSES * RADIX;
 constexpr size_t kOffCtr = kOffLook + sizeof(uint32_t) * MAX_PASSES * kNoAllocTiles * RADIX;
@@ -670,7 +753,7 @@ extern "C" psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals,
   uint32_t *look = reinterpret_cast<uint32_t *>(base + kOffLook);
   uint32_t *ctr = reinterpret_cast<uint32_t *>(base + kOffCtr);
   int *status = reinterpret_cast<int *>(base + kOffStatus);
-  const int passes = (key_bits + RB - 1) / RB;
+  const int passes = (key_bits + 8 - 1) / 8;
   const int64_t tiles = ceil_div(n, TILE);
   // the array keeps the previous call's contents: clear what must start at zero
   PSI_CK(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * passes * RADIX, s));
@@ -678,8 +761,8 @@ extern "C" psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals,
   PSI_CK(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * passes, s));
   PSI_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
   EncodeSpec none;
-  launch_hist<0, 2, 0>(d_keys, none, n, passes, hist, status, s);
-  PSI_LAUNCH(k_hist_scan, passes, RADIX, 0, s, hist, gbase);
+  if ((st = launch_hist<0, 2, 0, 8>(d_keys, none, n, passes, hist, status, s))) return st;
+  PSI_LAUNCH_NAMED("k_hist_scan", k_hist_scan<8>, passes, RADIX, 0, s, hist, gbase);
   // ping-pong between the scratch pair (even passes) and the caller's arrays
   uint64_t *kb[2] = {skeys, d_keys};
   uint32_t *vb[2] = {svals, d_vals};
@@ -693,12 +776,13 @@ extern "C" psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals,
     a.bits = 0;
     a.key_shift = 0;
     a.n = n;
-    a.shift = p * RB;
+    a.shift = p * 8;
     a.gbase = gbase + p * RADIX;
     a.lookback = look + (size_t)p * tiles * RADIX;
+    a.lookback_next = nullptr;
     a.tile_ctr = ctr + p;
     a.status = status;
-    launch_pass<0, 2, 0>(a, tiles, s);
+    if ((st = launch_pass<0, 2, 0, 8>(a, tiles, s))) return st;
   }
   if ((passes & 1) == 1) {  // the last pass wrote the scratch pair
     PSI_CK(cudaMemcpyAsync(d_keys, skeys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));

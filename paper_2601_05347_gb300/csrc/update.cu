@@ -38,7 +38,7 @@ psi_status sort_batch(psi_index *ix, const int32_t *pts, const uint32_t *ids, in
     return st;
   SortResult r;
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, m, ix->key_bits, ids, b.k0.p, b.v0.p, b.k1.p, b.v1.p,
-                       ix->d_status, s, &r)))
+                       ix->d_status, s, &r, ix->cfg.radix_bits)))
     return st;
   b.keys = r.keys;
   b.vals = r.vals;

@@ -124,14 +124,14 @@ class Index:
     """A device-resident spatial index (SPaC-Z, SPaC-H or P-Orth)."""
 
     def __init__(self, pts: torch.Tensor, ids: torch.Tensor, *, kind: int | str = SPAC_Z, leaf_size: int = 32,
-                 coord_bits: int | None = None, fanout: int = 32, stream=None):
+                 coord_bits: int | None = None, fanout: int = 32, radix_bits: int = 0, stream=None):
         if isinstance(kind, str):
             kind = KINDS[kind]
         dim = int(pts.shape[1]) if pts.dim() == 2 else 2
         if coord_bits is None:
             coord_bits = 30 if dim == 2 else 21
         self.dim, self.kind, self.leaf_size, self.coord_bits, self.fanout = dim, kind, leaf_size, coord_bits, fanout
-        self.cfg = Config(dim, kind, leaf_size, coord_bits, fanout, 0)
+        self.cfg = Config(dim, kind, leaf_size, coord_bits, fanout, radix_bits)
         h = ctypes.c_void_p()
         pts = pts.contiguous()
         ids = _u32(ids).contiguous()

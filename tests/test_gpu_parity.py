@@ -124,6 +124,28 @@ def test_spac_build_layout(kind, n, phi, fanout):
     check_spac_layout(ix, o)
 
 
+@pytest.mark.parametrize("radix", [8, 10, 11])
+@pytest.mark.parametrize("kind,dim,bits", [("spac_h", 2, 30), ("spac_z", 3, 21), ("porth", 2, 30)])
+def test_every_digit_width_gives_the_same_index(radix, kind, dim, bits):
+    p, ids = points(100003, dim, bits, 61 + radix, clustered=True)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits, radix_bits=radix)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
+    if kind == "porth":
+        check_porth_nodes(ix, o)
+    else:
+        check_spac_layout(ix, o)
+    newp = gen.varden(20000, dim, bits, 7 + radix)
+    newi = np.arange(10_000_000, 10_020_000, dtype=np.uint32)
+    ix.insert(T(newp), T(newi))
+    o.insert(newp, newi)
+    ix.delete(T(p[:5000]), T(ids[:5000]))
+    o.delete(p[:5000], ids[:5000])
+    q = query_points(2000, dim, bits, 3, p)
+    gi, gd = ix.knn(T(q), 10)
+    oi, od = o.knn(q, 10)
+    assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
+
+
 @pytest.mark.parametrize("dup", [False, True])
 def test_spac_build_layout_3d_and_duplicates(dup):
     p, ids = points(60000, 3, 21, 5, dup=dup)
