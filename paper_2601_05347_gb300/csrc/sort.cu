@@ -57,6 +57,8 @@ struct OnesweepSmem {
   typename R::Count wh[SW][R::RADIX];  // per-warp digit counters, then warp offsets
   uint32_t off[R::RADIX];              // tile-exclusive digit offsets
   uint32_t glob[R::RADIX];             // global position minus tile-local position
+  uint32_t gb[R::RADIX];               // global exclusive digit offsets of this pass
+  uint32_t nh[R::RADIX];               // next pass's digit counts of this tile
   alignas(16) uint64_t stage[TILE];    // keys (then values) in digit order
   typename R::Digit dig[TILE];         // digit of each staged position
   uint32_t wsum[SW];
@@ -74,7 +76,10 @@ struct PassArgs {
   int key_shift;
   int64_t n;
   int shift;
-  const uint32_t *gbase;  // [RADIX] global exclusive digit offsets of this pass
+  const uint32_t *gbase;  // [RADIX] global exclusive digit offsets of this pass, or null:
+  const uint32_t *hist_cur;  //   then this pass's digit counts, scanned by every tile
+  uint32_t *hist_next;       // next pass's digit counts (accumulated here), or null
+  int shift_next;
   uint32_t *lookback;     // [tiles][RADIX] of this pass, zero on entry
   uint32_t *lookback_next;  // table of the next pass: this pass zeroes it (or null)
   uint32_t *tile_ctr;
@@ -177,6 +182,33 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
     for (int i = tid; i < (int)(sizeof(sm.wh) / 4); i += ST) z[i] = 0;
   }
   if (MODE == 1 && CURVE == 1) hilbert_table_init(sm.htab);
+  if (a.hist_next)
+    for (int i = tid; i < RADIX; i += ST) sm.nh[i] = 0;
+  if (a.gbase) {
+    for (int i = tid; i < RADIX; i += ST) sm.gb[i] = a.gbase[i];
+  } else {  // exclusive scan of this pass's digit counts
+    uint32_t c[DPT], tot = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      c[q] = a.hist_cur[tid * DPT + q];
+      tot += c[q];
+    }
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sm.wsum[w] = x;
+    __syncthreads();
+    uint32_t run = x - tot;
+    for (int i = 0; i < w; ++i) run += sm.wsum[i];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      sm.gb[tid * DPT + q] = run;
+      run += c[q];
+    }
+  }
   __syncthreads();
   const uint32_t tile = sm.tile;
   const int64_t base = (int64_t)tile * TILE;
@@ -209,6 +241,11 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
     }
   }
 
+  if (a.hist_next) {  // the next pass's digit of every key of the tile
+#pragma unroll
+    for (int j = 0; j < SI; ++j)
+      if (wbase + j * 32 + lane < tile_n) atomicAdd(&sm.nh[(uint32_t)(key[j] >> a.shift_next) & (RADIX - 1)], 1u);
+  }
   // Stable rank of each key among equal digits of its warp (items in
   // (item, lane) order = input order).
   uint32_t rank[SI];
@@ -305,7 +342,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
         }
         st_relaxed_u32(a.lookback + (size_t)tile * RADIX + d, LB_PRE | ((prev + cnt[q]) & LB_VAL));
       }
-      sm.glob[d] = a.gbase[d] + prev - excl;
+      sm.glob[d] = sm.gb[d] + prev - excl;
       excl += cnt[q];
     }
   }
@@ -346,6 +383,9 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
     const int p = tid + i * ST;
     if (p < tile_n) a.vout[sm.glob[sm.dig[p]] + p] = s_v[p];
   }
+  if (a.hist_next)
+    for (int i = tid; i < RADIX; i += ST)
+      if (sm.nh[i]) atomicAdd(&a.hist_next[i], sm.nh[i]);
 }
 
 // ---- Ties: runs of equal keys ordered by id ------------------------------
@@ -480,26 +520,26 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   const bool encode = enc.pts != nullptr;
   const int passes = (key_bits + RB - 1) / RB;
   const int64_t tiles = ceil_div(n, TILE);
-  Buf<uint32_t> hist, gbase, lookback, ctr;
+  Buf<uint32_t> hist, lookback, ctr;
   psi_status st;
   // two look-back tables used alternately: pass p clears the table of pass p+1
-  if ((st = hist.alloc((size_t)passes * R::RADIX, s)) || (st = gbase.alloc((size_t)passes * R::RADIX, s)) ||
+  if ((st = hist.alloc((size_t)passes * R::RADIX, s)) ||
       (st = lookback.alloc((size_t)2 * tiles * R::RADIX, s)) || (st = ctr.alloc(passes, s)))
     return st;
   PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * passes * R::RADIX, s));
   PSI_CK(cudaMemsetAsync(lookback.p, 0, sizeof(uint32_t) * tiles * R::RADIX, s));
   PSI_CK(cudaMemsetAsync(ctr.p, 0, sizeof(uint32_t) * passes, s));
 
+  // digit 0 is counted up front; every pass counts the next digit of its keys
   if (!encode)
-    st = launch_hist<0, 2, 0, RB>(keys_in, enc, n, passes, hist.p, d_status, s);
+    st = launch_hist<0, 2, 0, RB>(keys_in, enc, n, 1, hist.p, d_status, s);
   else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
-    st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, passes, hist.p, d_status, s);
+    st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
   else if (enc.dim == 2)
-    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, passes, hist.p, d_status, s);
+    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
   else
-    st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, passes, hist.p, d_status, s);
+    st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
   if (st) return st;
-  PSI_LAUNCH_NAMED("k_hist_scan", k_hist_scan<RB>, passes, std::min(R::RADIX, 1024), 0, s, hist.p, gbase.p);
 
   uint64_t *kb[2] = {kbuf0, kbuf1};
   uint32_t *vb[2] = {vbuf0, vbuf1};
@@ -514,7 +554,10 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     a.key_shift = enc.key_shift;
     a.n = n;
     a.shift = p * RB;
-    a.gbase = gbase.p + p * R::RADIX;
+    a.gbase = nullptr;
+    a.hist_cur = hist.p + p * R::RADIX;
+    a.hist_next = p + 1 < passes ? hist.p + (p + 1) * R::RADIX : nullptr;
+    a.shift_next = (p + 1) * RB;
     a.lookback = lookback.p + (size_t)(p & 1) * tiles * R::RADIX;
     a.lookback_next = p + 1 < passes ? lookback.p + (size_t)((p + 1) & 1) * tiles * R::RADIX : nullptr;
     a.tile_ctr = ctr.p + p;
@@ -778,6 +821,9 @@ extern "C" psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals,
     a.n = n;
     a.shift = p * 8;
     a.gbase = gbase + p * RADIX;
+    a.hist_cur = nullptr;
+    a.hist_next = nullptr;
+    a.shift_next = 0;
     a.lookback = look + (size_t)p * tiles * RADIX;
     a.lookback_next = nullptr;
     a.tile_ctr = ctr + p;
