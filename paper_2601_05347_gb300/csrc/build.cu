@@ -94,55 +94,90 @@ NodeW node_w(const NodeArrays &a) {
   return w;
 }
 
-// One warp per leaf: gather the leaf's points by their sorted positions into
-// its block (structure of arrays), reduce the box, write the leaf node and its
-// separator (the first (key, id) of the leaf).
+// One warp per group of GL consecutive leaves: gather each leaf's points by
+// their sorted positions into its block (structure of arrays), reduce the
+// boxes, write the leaf nodes and their separators (the first (key, id) of
+// each leaf).  All sorted positions of the group are loaded first, then all
+// gathers are issued, so a warp keeps GL x 3 independent loads in flight
+// instead of waiting on each leaf's dependent position -> point chain.
+constexpr int GL = 4;
+
 template <int D>
 __global__ void k_leaf_gather(const uint64_t *skeys, const uint32_t *svals, const int32_t *pts, const uint32_t *ids,
                               int64_t n, int phi, int C, PoolW pool, NodeW nodes, uint64_t *sep_key,
                               uint32_t *sep_id, int64_t L) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < L; leaf += warps) {
-    const int64_t b = leaf * phi;
-    const int cnt = (int)min((int64_t)phi, n - b);
-    int32_t lo[D], hi[D];
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * GL < L; g += warps) {
+    for (int s0 = 0; s0 < phi; s0 += 32) {  // phi <= 64: at most two rounds
+      uint32_t v[GL];
+      uint64_t k[GL];
+      int32_t c[GL][D];
+      uint32_t id[GL];
+      bool ok[GL];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      lo[d] = INT32_MAX;
-      hi[d] = INT32_MIN;
-    }
-    const int64_t slot0 = leaf * C;
-    for (int s = lane; s < cnt; s += 32) {
-      const uint32_t v = svals[b + s];
-      const int64_t slot = slot0 + s;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const int32_t c = pts[(int64_t)v * D + d];
-        pool.px[d][slot] = c;
-        lo[d] = min(lo[d], c);
-        hi[d] = max(hi[d], c);
+      for (int u = 0; u < GL; ++u) {
+        const int64_t leaf = g * GL + u;
+        const int64_t b = leaf * phi;
+        const int s = s0 + lane;
+        ok[u] = leaf < L && s < phi && b + s < n;
+        v[u] = ok[u] ? svals[b + s] : 0u;
+        k[u] = ok[u] ? skeys[b + s] : 0ull;
       }
-      pool.pid[slot] = ids[v];
-      pool.pkey[slot] = skeys[b + s];
-    }
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      lo[d] = __reduce_min_sync(0xFFFFFFFFu, lo[d]);
-      hi[d] = __reduce_max_sync(0xFFFFFFFFu, hi[d]);
-    }
-    if (lane == 0) {
+      for (int u = 0; u < GL; ++u) {
+        if (ok[u]) {
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        nodes.lo[d][leaf] = lo[d];
-        nodes.hi[d][leaf] = hi[d];
+          for (int d = 0; d < D; ++d) c[u][d] = pts[(int64_t)v[u] * D + d];
+          id[u] = ids[v[u]];
+        }
       }
-      nodes.cnt[leaf] = cnt;
-      nodes.ref[leaf] = (uint32_t)slot0;
-      nodes.kids[leaf] = 0;
-      nodes.depth[leaf] = 0;
-      sep_key[leaf] = skeys[b];
-      sep_id[leaf] = ids[svals[b]];
+#pragma unroll
+      for (int u = 0; u < GL; ++u) {
+        if (!ok[u]) continue;
+        const int64_t leaf = g * GL + u;
+        const int64_t slot = leaf * C + s0 + lane;
+#pragma unroll
+        for (int d = 0; d < D; ++d) pool.px[d][slot] = c[u][d];
+        pool.pid[slot] = id[u];
+        pool.pkey[slot] = k[u];
+      }
+#pragma unroll
+      for (int u = 0; u < GL; ++u) {
+        const int64_t leaf = g * GL + u;
+        if (leaf >= L) break;
+        const int64_t b = leaf * phi;
+        const int cnt = (int)min((int64_t)phi, n - b);
+        int32_t lo[D], hi[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          lo[d] = ok[u] ? c[u][d] : INT32_MAX;
+          hi[d] = ok[u] ? c[u][d] : INT32_MIN;
+          lo[d] = __reduce_min_sync(0xFFFFFFFFu, lo[d]);
+          hi[d] = __reduce_max_sync(0xFFFFFFFFu, hi[d]);
+        }
+        if (lane == 0) {
+          if (s0 == 0) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              nodes.lo[d][leaf] = lo[d];
+              nodes.hi[d][leaf] = hi[d];
+            }
+            nodes.cnt[leaf] = cnt;
+            nodes.ref[leaf] = (uint32_t)(leaf * C);
+            nodes.kids[leaf] = 0;
+            nodes.depth[leaf] = 0;
+            sep_key[leaf] = k[u];
+            sep_id[leaf] = id[u];
+          } else if (s0 < cnt) {  // second round of a leaf wider than a warp
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              nodes.lo[d][leaf] = min(nodes.lo[d][leaf], lo[d]);
+              nodes.hi[d][leaf] = max(nodes.hi[d][leaf], hi[d]);
+            }
+          }
+        }
+      }
     }
   }
 }
@@ -253,12 +288,13 @@ psi_status spac_from_sorted(psi_index *ix, const uint64_t *skeys, const uint32_t
   pw.pkey = ix->pool.pkey;
   NodeW nw = node_w(ix->nodes);
   if (ix->L > 0) {
+    const int g = warp_grid(ceil_div(ix->L, GL));
     if (ix->D == 2)
-      PSI_LAUNCH_NAMED("k_leaf_gather", k_leaf_gather<2>, warp_grid(ix->L), 256, 0, s, skeys, svals, pts, ids, n,
-                       ix->phi, ix->C, pw, nw, ix->sep_key, ix->sep_id, ix->L);
+      PSI_LAUNCH_NAMED("k_leaf_gather", k_leaf_gather<2>, g, 256, 0, s, skeys, svals, pts, ids, n, ix->phi, ix->C, pw,
+                       nw, ix->sep_key, ix->sep_id, ix->L);
     else
-      PSI_LAUNCH_NAMED("k_leaf_gather", k_leaf_gather<3>, warp_grid(ix->L), 256, 0, s, skeys, svals, pts, ids, n,
-                       ix->phi, ix->C, pw, nw, ix->sep_key, ix->sep_id, ix->L);
+      PSI_LAUNCH_NAMED("k_leaf_gather", k_leaf_gather<3>, g, 256, 0, s, skeys, svals, pts, ids, n, ix->phi, ix->C, pw,
+                       nw, ix->sep_key, ix->sep_id, ix->L);
   }
   return build_spac_summary(ix, s);
 }
