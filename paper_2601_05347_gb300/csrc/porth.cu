@@ -46,16 +46,43 @@ __device__ __forceinline__ uint64_t cell_of(uint64_t k, int depth, int D, int bi
   return sh >= 64 ? 0 : (k >> sh);
 }
 
-// Gather the sorted points into the contiguous pool.
+// Gather the sorted points into the contiguous pool: GP items per thread,
+// all positions loaded first, then all gathers, so that each thread keeps
+// several independent random loads in flight.
+constexpr int GP = 4;
+
 template <int D>
 __global__ void k_porth_gather(const uint64_t *skeys, const uint32_t *svals, const int32_t *pts, const uint32_t *ids,
                                int64_t n, Pool pool) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t v = svals[i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * GP;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * GP + threadIdx.x; i0 < n; i0 += stride) {
+    uint32_t v[GP];
 #pragma unroll
-    for (int d = 0; d < D; ++d) pool.px[d][i] = pts[(int64_t)v * D + d];
-    pool.pid[i] = ids[v];
-    pool.pkey[i] = skeys[i];
+    for (int u = 0; u < GP; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+      v[u] = i < n ? svals[i] : 0u;
+    }
+    int32_t c[GP][D];
+    uint32_t id[GP];
+#pragma unroll
+    for (int u = 0; u < GP; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+      if (i < n) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) c[u][d] = pts[(int64_t)v[u] * D + d];
+        id[u] = ids[v[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < GP; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+      if (i < n) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) pool.px[d][i] = c[u][d];
+        pool.pid[i] = id[u];
+        pool.pkey[i] = skeys[i];
+      }
+    }
   }
 }
 
@@ -125,16 +152,24 @@ __global__ void k_heads(const int32_t *ld, const uint64_t *lkey, int64_t L, int 
   }
 }
 
+// Node records (depth << 32 | first leaf) in preorder, and the number of
+// nodes per depth (counted in shared memory, one global add per block and depth).
 __global__ void k_emit_nodes(const int32_t *ld, const int32_t *c, const int64_t *base, int64_t L, uint64_t *nkey,
                              uint32_t *nval, int32_t *depth_hist) {
+  __shared__ int32_t sh[64];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t o = base[i];
     for (int l = c[i] + 1; l <= ld[i]; ++l, ++o) {
       nkey[o] = ((uint64_t)l << 32) | (uint64_t)i;
       nval[o] = (uint32_t)o;
-      atomicAdd(&depth_hist[l], 1);
+      atomicAdd(&sh[l], 1);
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 64; i += blockDim.x)
+    if (sh[i]) atomicAdd(&depth_hist[i], sh[i]);
 }
 
 struct LinkArgs {
