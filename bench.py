@@ -635,6 +635,130 @@ def run_served(n_base: int, R: int, rank: int = 0, upd=(1e3, 1e5), qry=(1e2, 1e5
 
 
 # ---------------------------------------------------------------------------
+# the other configurations of the metric (measurement only; parity is in tests/)
+# ---------------------------------------------------------------------------
+def _timed(fn, reps=1):
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        out = fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def run_config1():
+    """2D uniform n=1e6, SPaC-Z, leaf 32: build, insert 1e5, delete 1e5 live, 1e4 10-NN, 1e4 range counts (~100 pts)."""
+    import torch
+    from paper_2601_05347_gb300 import psi
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else a).cuda()
+    n, m = 1_000_000, 100_000
+    pts = gen.uniform(n, 2, BITS, gen.config_seed(0, 0))
+    ins = gen.uniform(m, 2, BITS, gen.config_seed(0, 1))
+    live_p = np.concatenate([pts, ins])
+    live_i = np.arange(n + m, dtype=np.uint32)
+    dsel = gen.sample_without_replacement(n + m, m, gen.config_seed(0, 2))
+    q = gen.uniform(10_000, 2, BITS, gen.config_seed(0, 3))
+    side = int((1 << BITS) * np.sqrt(100 / n))
+    boxes = gen.square_boxes(10_000, 2, BITS, side, gen.config_seed(0, 4))
+    d = dict(p=T(pts), i=T(live_i[:n]), ip=T(ins), ii=T(live_i[n:]), dp=T(live_p[dsel]), di=T(live_i[dsel]), q=T(q),
+             b=T(boxes))
+    res = {}
+    t, _ = _timed(lambda: psi.Index(d["p"], d["i"], kind="spac_z", leaf_size=32).close())
+    res["build_ms"] = round(t, 3)
+    ix = psi.Index(d["p"], d["i"], kind="spac_z", leaf_size=32)
+    s = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    e[0].record(s)
+    ix.insert(d["ip"], d["ii"])
+    e[1].record(s)
+    ix.delete(d["dp"], d["di"])
+    e[2].record(s)
+    ix.knn(d["q"], 10)
+    e[3].record(s)
+    c = ix.range_count(d["b"])
+    e[4].record(s)
+    torch.cuda.synchronize()
+    res.update(insert_ms=round(e[0].elapsed_time(e[1]), 3), delete_ms=round(e[1].elapsed_time(e[2]), 3),
+               knn_ms=round(e[2].elapsed_time(e[3]), 3), range_count_ms=round(e[3].elapsed_time(e[4]), 3),
+               mean_range_count=round(float(c.float().mean()), 1), size=len(ix))
+    res["build_Mpts_s"] = round(n / res["build_ms"] / 1e3, 1)
+    ix.close()
+    return res
+
+
+def run_config3(n=100_000_000, nq=10_000_000):
+    """3D n=1e8, coordinates in [0, 2^21): uniform and clustered, P-Orth and SPaC-Z side by side."""
+    import torch
+    from paper_2601_05347_gb300 import psi
+    b3 = 21
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else a).cuda()
+    out = {}
+    for dist in ("uniform", "varden"):
+        if dist == "uniform":
+            pts = gen.uniform(n, 3, b3, gen.config_seed(2, 0))
+            ind = gen.uniform(n // 10, 3, b3, gen.config_seed(2, 1))
+            ood = gen.varden(n // 10, 3, b3, gen.config_seed(2, 2))
+        else:
+            pts = gen.varden(n, 3, b3, gen.config_seed(2, 3), x_range=(0, 1 << (b3 - 1)))
+            ind = gen.varden(n // 10, 3, b3, gen.config_seed(2, 4), x_range=(0, 1 << (b3 - 1)))
+            ood = gen.varden(n // 10, 3, b3, gen.config_seed(2, 5), x_range=(1 << (b3 - 1), 1 << b3))
+        ids = np.arange(n, dtype=np.uint32)
+        dsel = gen.sample_without_replacement(n, n // 10, gen.config_seed(2, 6))
+        q = pts[gen.sample_with_replacement(n, nq, gen.config_seed(2, 7))]
+        h2 = gen.half_side_for_count(pts, 1e2, gen.config_seed(2, 8))
+        h4 = gen.half_side_for_count(pts, 1e4, gen.config_seed(2, 9))
+        cen = pts[gen.sample_with_replacement(n, 50_000, gen.config_seed(2, 10))]
+        dp, di, dq = T(pts), T(ids), T(q)
+        dind, dood = T(ind), T(ood)
+        iid = T(np.arange(n, n + n // 10, dtype=np.uint32))
+        oid = T(np.arange(n + n // 10, n + 2 * (n // 10), dtype=np.uint32))
+        ddp, ddi = T(pts[dsel]), T(ids[dsel])
+        b2, b4 = T(gen.centred_boxes(cen, h2, b3)), T(gen.centred_boxes(cen, h4, b3))
+        for kind in ("porth", "spac_z"):
+            r = {}
+            t, _ = _timed(lambda: psi.Index(dp, di, kind=kind, leaf_size=32, coord_bits=b3).close())
+            r["build_ms"] = round(t, 2)
+            r["build_Mpts_s"] = round(n / t / 1e3, 1)
+            for k in (1, 10, 100):
+                ix = psi.Index(dp, di, kind=kind, leaf_size=32, coord_bits=b3)
+                t, _ = _timed(lambda: ix.knn(dq, k))
+                r[f"knn{k}_Mq_s"] = round(nq / t / 1e3, 2)
+                ix.close()
+            ix = psi.Index(dp, di, kind=kind, leaf_size=32, coord_bits=b3)
+            t, c2 = _timed(lambda: ix.range_count(b2))
+            r["range_count_1e2_Mq_s"] = round(5e4 / t / 1e3, 2)
+            r["mean_count_1e2"] = round(float(c2.float().mean()), 1)
+            t, c4 = _timed(lambda: ix.range_count(b4))
+            r["range_count_1e4_Mq_s"] = round(5e4 / t / 1e3, 2)
+            r["mean_count_1e4"] = round(float(c4.float().mean()), 1)
+            s = torch.cuda.current_stream()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(s)
+            ix.insert(dind, iid)
+            e[1].record(s)
+            ix.insert(dood, oid)
+            e[2].record(s)
+            ix.delete(ddp, ddi)
+            e[3].record(s)
+            torch.cuda.synchronize()
+            r["insert_ind_10pct_ms"] = round(e[0].elapsed_time(e[1]), 2)
+            r["insert_ood_10pct_ms"] = round(e[1].elapsed_time(e[2]), 2)
+            r["delete_10pct_ms"] = round(e[2].elapsed_time(e[3]), 2)
+            t, _ = _timed(lambda: ix.knn(dq, 10))
+            r["knn10_after_updates_Mq_s"] = round(nq / t / 1e3, 2)
+            r["size_after"] = len(ix)
+            ix.close()
+            out[f"{dist}/{kind}"] = r
+            print(json.dumps({f"{dist}/{kind}": r}), file=sys.stderr, flush=True)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # oracle timings (the CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 def oracle_sample_step(w, host, frac: float):
@@ -736,9 +860,17 @@ def main():
     ap.add_argument("--served-points", type=int, default=20_000_000)
     ap.add_argument("--served-requests", type=int, default=300)
     ap.add_argument("--serve", action="store_true", help="only the served configuration at 5e8 resident points")
+    ap.add_argument("--configs", action="store_true", help="the 2D uniform 1e6 and 3D 1e8 configurations")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.configs:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"metric": "other configurations", "config1_2d_uniform_1e6_spac_z": run_config1(),
+                          "config3_3d_1e8": run_config3()}), flush=True)
     elif args.serve:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
