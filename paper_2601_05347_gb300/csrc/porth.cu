@@ -152,8 +152,10 @@ __global__ void k_heads(const int32_t *ld, const uint64_t *lkey, int64_t L, int 
   }
 }
 
-// Node records (depth << 32 | first leaf) in preorder, and the number of
-// nodes per depth (counted in shared memory, one global add per block and depth).
+// Node records in preorder -- key = depth, value = first leaf -- and the
+// number of nodes per depth (counted in shared memory, one global add per
+// block and depth).  Preorder lists the nodes of each depth by first leaf, so
+// one stable pass on the depth digit orders them depth-major, leaf-minor.
 __global__ void k_emit_nodes(const int32_t *ld, const int32_t *c, const int64_t *base, int64_t L, uint64_t *nkey,
                              uint32_t *nval, int32_t *depth_hist) {
   __shared__ int32_t sh[64];
@@ -162,8 +164,8 @@ __global__ void k_emit_nodes(const int32_t *ld, const int32_t *c, const int64_t 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t o = base[i];
     for (int l = c[i] + 1; l <= ld[i]; ++l, ++o) {
-      nkey[o] = ((uint64_t)l << 32) | (uint64_t)i;
-      nval[o] = (uint32_t)o;
+      nkey[o] = (uint64_t)l;
+      nval[o] = (uint32_t)i;
       atomicAdd(&sh[l], 1);
     }
   }
@@ -173,7 +175,8 @@ __global__ void k_emit_nodes(const int32_t *ld, const int32_t *c, const int64_t 
 }
 
 struct LinkArgs {
-  const uint64_t *nkey;  // sorted (depth << 32 | first leaf)
+  const uint64_t *ndepth;  // node depth, depth-major order
+  const uint32_t *nleaf;   // node's first leaf, ascending within a depth
   const int64_t *doff;   // [bits + 2] depth offsets
   const int64_t *lb;     // leaf begin slot
   const int32_t *ld;
@@ -186,8 +189,8 @@ struct LinkArgs {
 
 __global__ void k_link(LinkArgs a) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.N; x += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(a.nkey[x] >> 32);
-    const int64_t i = (int64_t)(a.nkey[x] & 0xFFFFFFFFu);
+    const int l = (int)a.ndepth[x];
+    const int64_t i = (int64_t)a.nleaf[x];
     const int sh = a.D * (a.bits - l);
     const uint64_t prefix = sh >= 64 ? 0 : (a.lkey[i] >> sh);
     a.nodes.depth[x] = l;
@@ -218,7 +221,7 @@ __global__ void k_link(LinkArgs a) {
       int64_t p = s0, q = s1;
       while (p < q) {
         const int64_t mid = (p + q) >> 1;
-        if ((int64_t)(a.nkey[mid] & 0xFFFFFFFFu) < i)
+        if ((int64_t)a.nleaf[mid] < i)
           p = mid + 1;
         else
           q = mid;
@@ -227,7 +230,7 @@ __global__ void k_link(LinkArgs a) {
       q = s1;
       while (p < q) {
         const int64_t mid = (p + q) >> 1;
-        if ((int64_t)(a.nkey[mid] & 0xFFFFFFFFu) < e)
+        if ((int64_t)a.nleaf[mid] < e)
           p = mid + 1;
         else
           q = mid;
@@ -425,9 +428,9 @@ psi_status porth_derive(psi_index *ix, cudaStream_t s) {
   Buf<int> sst;
   if ((st = sst.alloc(1, s))) return st;
   PSI_CK(cudaMemsetAsync(sst.p, 0, sizeof(int), s));
-  // (depth << 32 | first leaf) has at most 37 significant bits: 5 digit passes;
-  // the input arrays double as the second ping-pong buffer
-  if ((st = sort_pairs(none, nk0.p, nv0.p, N, 40, nullptr, nk1.p, nv1.p, nk0.p, nv0.p, sst.p, s, &r)))
+  // one stable digit pass on the depth (< 64); the input arrays double as the
+  // second ping-pong buffer
+  if ((st = sort_pairs(none, nk0.p, nv0.p, N, 8, nullptr, nk1.p, nv1.p, nk0.p, nv0.p, sst.p, s, &r)))
     return st;
   PSI_CK(cudaStreamSynchronize(s));
   std::vector<int64_t> doff(bits + 3, 0);
@@ -439,7 +442,7 @@ psi_status porth_derive(psi_index *ix, cudaStream_t s) {
 
   if ((st = alloc_nodes(ix->nodes, D, N, true, s))) return st;
   if ((st = DevMem::alloc((void **)&ix->leaf_node, sizeof(int32_t) * L, s))) return st;
-  LinkArgs la{r.keys, d_doff.p, lb.p, ld.p, lkey.p, L, N, n, D, bits, ix->nodes, ix->leaf_node};
+  LinkArgs la{r.keys, r.vals, d_doff.p, lb.p, ld.p, lkey.p, L, N, n, D, bits, ix->nodes, ix->leaf_node};
   PSI_LAUNCH(k_link, grid_for(N), 256, 0, s, la);
   int maxd = 0;
   for (int l = 0; l <= bits; ++l)
