@@ -65,6 +65,23 @@ def make_inputs(w, rank: int):
                 half_side=h)
 
 
+def max_over_ranks(values, world: int, device=None) -> list:
+    """Element-wise maximum of each rank's values over all ranks: a replica
+    job takes as long as its slowest rank.  Collective; every rank calls it."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(world: int, units_per_rank: int, ms: float, per: float = 1e6) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3) / per
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -235,11 +252,9 @@ def run_ours(args):
     psi.profile_enable(False)
     phase_ms = {p: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, p in enumerate(phases)}
 
-    if world > 1:
-        t = torch.tensor([total_ms] + [phase_ms[p] for p in phases], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t[0])
-        phase_ms = {p: float(t[i + 1]) for i, p in enumerate(phases)}
+    t = max_over_ranks([total_ms] + [phase_ms[p] for p in phases], world, dev)
+    total_ms = t[0]
+    phase_ms = {p: t[i + 1] for i, p in enumerate(phases)}
 
     # traversal counters of one instrumented k-NN pass over the same queries
     ixs = psi.Index(d["pts"], d["ids"], kind="spac_h", leaf_size=32)
@@ -267,7 +282,7 @@ def run_ours(args):
             e2e_ms.append((time.perf_counter() - a) * 1e3)
         ix.close()
         del leaves
-    e2e_build = statistics.mean(e2e_ms)
+    e2e_build = max_over_ranks([statistics.mean(e2e_ms)], world, dev)[0]
 
     # roofline of the dominant kernel (largest share of the timed steps)
     total_prof = sum(v[1] for v in prof.values()) or 1.0
@@ -320,7 +335,7 @@ def run_ours(args):
 
     ms_step = total_ms / args.steps
     build_ms = phase_ms["build"]
-    value = world * n / (build_ms * 1e-3) / 1e6
+    value = job_throughput(world, n, build_ms)
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -352,7 +367,7 @@ def run_ours(args):
             "range_count": {"ms": round(phase_ms["range_count"], 3),
                             "value": round(w["n_box"] / phase_ms["range_count"] * 1e3, 1), "unit": "queries/s"},
         },
-        "e2e": {"value": round(world * n / (e2e_build * 1e-3) / 1e6, 2), "unit": "Mpts/s (build)",
+        "e2e": {"value": round(job_throughput(world, n, e2e_build), 2), "unit": "Mpts/s (build)",
                 "h2d_bytes_per_step": int(host["pts"].nbytes + host["ids"].nbytes), "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches),
         "roofline": roof,
