@@ -50,6 +50,8 @@ def lib():
         L.or_morton.argtypes = [P, ctypes.c_int, ctypes.c_int]
         L.or_hilbert2.restype = ctypes.c_uint64
         L.or_hilbert2.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int]
+        L.or_hilbert3.restype = ctypes.c_uint64
+        L.or_hilbert3.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]
         L.or_keys.restype = ctypes.c_int
         L.or_keys.argtypes = [P, P, i64, P]
         L.or_build.restype = P
@@ -95,6 +97,10 @@ def morton(p, dim: int, bits: int) -> int:
 
 def hilbert2(x: int, y: int, bits: int) -> int:
     return int(lib().or_hilbert2(int(x), int(y), bits))
+
+
+def hilbert3(x: int, y: int, z: int, bits: int) -> int:
+    return int(lib().or_hilbert3(int(x), int(y), int(z), bits))
 
 
 def keys(pts, dim: int, kind: int, bits: int) -> np.ndarray:

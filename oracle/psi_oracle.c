@@ -11,7 +11,8 @@
  *   - Morton bit order: key bit D*i + d is bit i of coordinate d (x lowest).
  *   - Hilbert orientation: Hilbert's 1891 curve starting at (0,0), visiting the
  *     quadrants lower-left, upper-left, upper-right, lower-right, ending at
- *     (2^b - 1, 0).
+ *     (2^b - 1, 0).  In 3D: Skilling's curve (see or_hilbert3), from (0,0,0)
+ *     to (2^b - 1, 0, 0).
  *   - A node is a leaf iff it holds at most phi points (P-Orth: or it is a
  *     single cell at depth b).
  *   - Ties in key are ordered by id; k-NN ties in distance are ordered by id.
@@ -76,6 +77,43 @@ uint64_t or_hilbert2(int32_t x, int32_t y, int bits) {
   return d;
 }
 
+/* 3D Hilbert curve.  The paper defines Hilbert keys in 2D only; in 3D the
+ * curve is read as Skilling's (J. Skilling, "Programming the Hilbert curve",
+ * AIP Conf. Proc. 707, 2004) with axes X0 = x, X1 = y, X2 = z.  His method, on
+ * whole coordinate words:
+ *   1. from the top bit level down to level 1, for each axis i in turn: if
+ *      bit l of X_i is set, complement the bits of X_0 below l; otherwise
+ *      exchange the bits below l between X_0 and X_i;
+ *   2. Gray-code across the axes (X_i ^= X_{i-1} for i = 1, 2), then
+ *      complement, at every level, the bits below each set bit of X_2;
+ *   3. the key reads the transposed words level by level, top level first,
+ *      X_0's bit the most significant of each three-bit digit. */
+uint64_t or_hilbert3(int32_t x, int32_t y, int32_t z, int bits) {
+  uint32_t X[3] = {(uint32_t)x, (uint32_t)y, (uint32_t)z};
+  for (int level = bits - 1; level >= 1; --level) {
+    uint32_t bit = (uint32_t)1 << level, below = bit - 1;
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & bit) {
+        X[0] ^= below;
+      } else {
+        uint32_t diff = (X[0] ^ X[i]) & below;
+        X[0] ^= diff;
+        X[i] ^= diff;
+      }
+    }
+  }
+  X[1] ^= X[0];
+  X[2] ^= X[1];
+  uint32_t flip = 0;
+  for (int level = bits - 1; level >= 1; --level)
+    if (X[2] & ((uint32_t)1 << level)) flip ^= ((uint32_t)1 << level) - 1;
+  for (int i = 0; i < 3; ++i) X[i] ^= flip;
+  uint64_t key = 0;
+  for (int level = bits - 1; level >= 0; --level)
+    for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> level) & 1u);
+  return key;
+}
+
 static int in_domain(const int32_t *p, int dim, int bits) {
   for (int d = 0; d < dim; ++d)
     if (p[d] < 0 || (int64_t)p[d] >= ((int64_t)1 << bits)) return 0;
@@ -83,6 +121,7 @@ static int in_domain(const int32_t *p, int dim, int bits) {
 }
 
 static uint64_t key_of(const or_cfg *cfg, const int32_t *p) {
+  if (cfg->kind == OR_SPAC_H && cfg->dim == 3) return or_hilbert3(p[0], p[1], p[2], cfg->bits);
   if (cfg->kind == OR_SPAC_H) return or_hilbert2(p[0], p[1], cfg->bits);
   return or_morton(p, cfg->dim, cfg->bits);
 }

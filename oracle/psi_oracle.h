@@ -31,6 +31,8 @@ typedef struct {
 /* Space-filling-curve keys (Sec 2.2 "Spatial Filling Curves"). */
 uint64_t or_morton(const int32_t *p, int dim, int bits);
 uint64_t or_hilbert2(int32_t x, int32_t y, int bits);
+/* Skilling's 3D Hilbert index of (x, y, z) at `bits` bits per axis. */
+uint64_t or_hilbert3(int32_t x, int32_t y, int32_t z, int bits);
 /* Keys of n points under cfg (Morton for SPAC_Z and PORTH, Hilbert for SPAC_H).
  * Returns 0, or -1 if a coordinate lies outside [0, 2^bits). */
 int or_keys(const or_cfg *cfg, const int32_t *pts, int64_t n, uint64_t *keys);

@@ -100,6 +100,63 @@ def test_hilbert_self_similar_at_30_bits():
     assert O.hilbert2(0, 0, 30) == 0
 
 
+def hilbert3_inverse(bits):
+    side = 1 << bits
+    cells = [None] * (side ** 3)
+    for x in range(side):
+        for y in range(side):
+            for z in range(side):
+                d = O.hilbert3(x, y, z, bits)
+                assert 0 <= d < len(cells)
+                assert cells[d] is None, "not a bijection"
+                cells[d] = (x, y, z)
+    return cells
+
+
+def test_hilbert3_order_one_is_gray_code():
+    # the first-order 3D curve visits the cube's corners in reflected binary
+    # Gray-code order, x the most significant bit: g(k) = k ^ (k >> 1)
+    want = [((k ^ (k >> 1)) >> 2 & 1, (k ^ (k >> 1)) >> 1 & 1, (k ^ (k >> 1)) & 1) for k in range(8)]
+    assert hilbert3_inverse(1) == want
+
+
+@pytest.mark.parametrize("bits", [2, 3, 4])
+def test_hilbert3_bijection_adjacency_endpoints_nesting(bits):
+    cells = hilbert3_inverse(bits)
+    side = 1 << bits
+    assert cells[0] == (0, 0, 0)
+    assert cells[-1] == (side - 1, 0, 0)
+    for a, b in zip(cells, cells[1:]):
+        assert sum(abs(a[i] - b[i]) for i in range(3)) == 1
+    # every aligned run of 8^j indices fills an aligned 2^j cube
+    for j in range(1, bits):
+        blk = 1 << (3 * j)
+        for t in range(0, len(cells), blk):
+            for axis in range(3):
+                assert len({c[axis] >> j for c in cells[t:t + blk]}) == 1
+
+
+def test_hilbert3_self_similar_at_21_bits():
+    rng = np.random.default_rng(2)
+    for x, y, z in rng.integers(0, 16, size=(300, 3)):
+        top = O.hilbert3(int(x) << 17, int(y) << 17, int(z) << 17, 21)
+        assert top >> 51 == O.hilbert3(int(x), int(y), int(z), 4)
+    assert O.hilbert3(0, 0, 0, 21) == 0
+    assert O.hilbert3((1 << 21) - 1, 0, 0, 21) == (1 << 63) - 1
+    # neighbours along the curve stay neighbours at full resolution: walk the
+    # keys of a small aligned cube deep inside the domain
+    base = np.array([123456, 987654, 1 << 20]) & ~np.int64(7)
+    cells = {}
+    for dx in range(8):
+        for dy in range(8):
+            for dz in range(8):
+                cells[O.hilbert3(int(base[0] + dx), int(base[1] + dy), int(base[2] + dz), 21)] = (dx, dy, dz)
+    ks = sorted(cells)
+    assert ks[-1] - ks[0] == 511  # an aligned 8^3 cube is one contiguous run
+    for a, b in zip(ks, ks[1:]):
+        assert sum(abs(cells[a][i] - cells[b][i]) for i in range(3)) == 1
+
+
 def test_keys_reject_out_of_range():
     with pytest.raises(ValueError):
         O.keys(np.array([[1 << 30, 0]]), 2, O.SPAC_Z, 30)
@@ -117,3 +174,7 @@ def test_keys_batch_matches_scalar():
     for i, (x, y) in enumerate(p):
         assert kz[i] == O.morton([x, y], 2, 30)
         assert kh[i] == O.hilbert2(x, y, 30)
+    p3 = rng.integers(0, 1 << 21, size=(50, 3))
+    k3 = O.keys(p3, 3, O.SPAC_H, 21)
+    for i, (x, y, z) in enumerate(p3):
+        assert k3[i] == O.hilbert3(x, y, z, 21)
