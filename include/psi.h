@@ -51,7 +51,7 @@ typedef enum {
 
 typedef enum {
   PSI_SPAC_Z = 0, /* SPaC-tree on the Morton (Z) curve, Sec 4 */
-  PSI_SPAC_H = 1, /* SPaC-tree on the Hilbert curve (2D), Sec 4 */
+  PSI_SPAC_H = 1, /* SPaC-tree on the Hilbert curve (2D: Hilbert 1891; 3D: Skilling 2004), Sec 4 */
   PSI_PORTH = 2   /* P-Orth tree, Sec 3 */
 } psi_kind;
 

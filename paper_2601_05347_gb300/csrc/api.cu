@@ -164,10 +164,6 @@ static psi_status validate_cfg(const psi_config *c) {
     set_error("unknown index kind");
     return PSI_ERR_INVALID;
   }
-  if (c->kind == PSI_SPAC_H && c->dim != 2) {
-    set_error("the Hilbert curve is implemented in 2D only");
-    return PSI_ERR_INVALID;
-  }
   if (c->leaf_size < 1 || c->leaf_size > kMaxLeaf) {
     set_error("leaf_size must be in [1, 64]");
     return PSI_ERR_INVALID;

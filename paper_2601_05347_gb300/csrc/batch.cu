@@ -87,7 +87,7 @@ struct BuildSmem {
   uint64_t stage[CH];          // chunk keys (then values) in digit order
   uint8_t dig[CH];             // digit of each staged position
   uint32_t wsum[32];
-  uint8_t htab[256];
+  alignas(16) uint8_t htab[kCurveTabBytes];
   int job;
   int nlong;
   int64_t long_start[64];
@@ -117,7 +117,7 @@ __global__ __launch_bounds__(BT) void k_batch_build(BuildArgs a) {
   BuildSmem<BT> &sm = *reinterpret_cast<BuildSmem<BT> *>(smem_raw);
   constexpr int W = BuildSmem<BT>::W, CH = BuildSmem<BT>::CH;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (CURVE == 1) hilbert_table_init(sm.htab);
+  curve_table_init<D, CURVE>(sm.htab);
   for (;;) {
     if (tid == 0) sm.job = (int)atomicAdd(a.queue, 1u);
     __syncthreads();
@@ -411,8 +411,8 @@ __global__ void k_query_roots(const int64_t *qoff, int nseg, const int32_t *root
 template <int D, int CURVE>
 __global__ void k_query_keys(const int32_t *q, const int32_t *qseg, int64_t nq, int bits, int shift, uint64_t *keys,
                              uint32_t *vals) {
-  __shared__ uint8_t htab[256];
-  if (CURVE == 1) hilbert_table_init(htab);
+  __shared__ alignas(16) uint8_t htab[kCurveTabBytes];
+  curve_table_init<D, CURVE>(htab);
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t c[D];
@@ -464,7 +464,7 @@ psi_status psi_batch_create(const psi_config *cfg, const int64_t *h_offsets, int
     return PSI_ERR_INVALID;
   }
   *out = nullptr;
-  if (cfg->kind == PSI_PORTH || cfg->dim < 2 || cfg->dim > 3 || (cfg->kind == PSI_SPAC_H && cfg->dim != 2) ||
+  if (cfg->kind == PSI_PORTH || cfg->dim < 2 || cfg->dim > 3 ||
       cfg->leaf_size < 1 || cfg->leaf_size > 64 || cfg->coord_bits < 1 ||
       cfg->coord_bits > (cfg->dim == 2 ? 31 : 21) || (cfg->fanout != 0 && (cfg->fanout < 2 || cfg->fanout > 32))) {
     set_error("batched indexes support SPaC-Z / SPaC-H with the usual leaf, bit and fanout limits");
@@ -598,6 +598,7 @@ psi_status psi_batch_build(psi_batch *b, const int32_t *d_pts, const uint32_t *d
     if (b->threads == 1024) return launch_build<DD, CC, 1024>(b, a, s);           \
     return launch_build<DD, CC, 512>(b, a, s);                                    \
   } while (0)
+  if (b->D == 3 && b->curve == CURVE_HILBERT) BUILD_CASE(3, 1);
   if (b->D == 3) BUILD_CASE(3, 0);
   if (b->curve == CURVE_HILBERT) BUILD_CASE(2, 1);
   BUILD_CASE(2, 0);
@@ -650,7 +651,10 @@ psi_status psi_batch_knn(psi_batch *b, const int32_t *d_q, const int64_t *d_qoff
   PSI_LAUNCH(k_query_roots, g, 256, 0, s, d_qoffsets, b->nidx, b->d_root, nq, b->d_qroot, b->d_qseg);
   const int order_bits = std::min(40, b->key_bits);
   const int shift = b->key_bits - order_bits;
-  if (b->D == 3)
+  if (b->D == 3 && b->curve == CURVE_HILBERT)
+    PSI_LAUNCH_NAMED("k_query_keys", (k_query_keys<3, 1>), g, 256, 0, s, d_q, b->d_qseg, nq, b->cfg.coord_bits, shift,
+                     b->qk0, b->qv0);
+  else if (b->D == 3)
     PSI_LAUNCH_NAMED("k_query_keys", (k_query_keys<3, 0>), g, 256, 0, s, d_q, b->d_qseg, nq, b->cfg.coord_bits, shift,
                      b->qk0, b->qv0);
   else if (b->curve == CURVE_HILBERT)

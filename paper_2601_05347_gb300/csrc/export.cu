@@ -75,8 +75,8 @@ __global__ void k_export_nodes(TreeView t, const int32_t *ndepth, const uint64_t
 
 template <int D, int CURVE>
 __global__ void k_encode(const int32_t *pts, int64_t n, int bits, uint64_t *keys, int *status) {
-  __shared__ uint8_t htab[256];
-  if (CURVE == 1) hilbert_table_init(htab);
+  __shared__ alignas(16) uint8_t htab[kCurveTabBytes];
+  curve_table_init<D, CURVE>(htab);
   __syncthreads();
   bool bad_any = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -139,7 +139,7 @@ using namespace psi;
 extern "C" psi_status psi_encode(const psi_config *cfg, const int32_t *d_pts, int64_t n, uint64_t *d_keys,
                                  void *stream) {
   if (!cfg || n < 0 || (n > 0 && (!d_pts || !d_keys)) || (cfg->dim != 2 && cfg->dim != 3) ||
-      (cfg->kind == PSI_SPAC_H && cfg->dim != 2) || cfg->coord_bits < 1 ||
+      cfg->coord_bits < 1 ||
       cfg->coord_bits > (cfg->dim == 2 ? 31 : 21)) {
     set_error("invalid encode arguments");
     return PSI_ERR_INVALID;
@@ -151,7 +151,9 @@ extern "C" psi_status psi_encode(const psi_config *cfg, const int32_t *d_pts, in
   if (st) return st;
   PSI_CK(cudaMemsetAsync(status.p, 0, sizeof(int), s));
   const int g = grid_for(n);
-  if (cfg->dim == 3)
+  if (cfg->dim == 3 && cfg->kind == PSI_SPAC_H)
+    PSI_LAUNCH_NAMED("k_encode", (k_encode<3, 1>), g, 256, 0, s, d_pts, n, cfg->coord_bits, d_keys, status.p);
+  else if (cfg->dim == 3)
     PSI_LAUNCH_NAMED("k_encode", (k_encode<3, 0>), g, 256, 0, s, d_pts, n, cfg->coord_bits, d_keys, status.p);
   else if (cfg->kind == PSI_SPAC_H)
     PSI_LAUNCH_NAMED("k_encode", (k_encode<2, 1>), g, 256, 0, s, d_pts, n, cfg->coord_bits, d_keys, status.p);

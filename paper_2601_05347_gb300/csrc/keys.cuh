@@ -16,6 +16,25 @@
 // two state bits.  Three levels are consumed per step through a 256-entry
 // table (state, 3 x-bits, 3 y-bits) -> (6 key bits, next state) that every
 // thread block derives from the automaton into shared memory.
+//
+// Hilbert keys (3D; the paper defines Hilbert keys in 2D only, so the 3D curve
+// is a reading): Skilling's curve (J. Skilling, "Programming the Hilbert
+// curve", AIP Conf. Proc. 707, 2004) with axes X0 = x, X1 = y, X2 = z, which
+// runs from (0,0,0) to (2^b - 1, 0, 0).  His method works on whole coordinate
+// words -- undo the sub-cube symmetries from the top bit down, then Gray-code
+// -- but every step at bit level l only alters the bits below l, so it runs
+// here as an automaton read top level first.  The state is the symmetry that
+// the levels above have imposed on the bits below (a permutation of the three
+// axes with a reflection per axis) plus the running parity of the Gray code of
+// the last axis; 96 encodings, 48 reachable.  Per level: the point's octant
+// bits are mapped through the symmetry to (b0, b1, b2); the Gray code
+// g = (b0, b0^b1, b0^b1^b2), complemented when the parity is odd, is the
+// octant digit (g0 most significant); the parity absorbs g2; then for
+// i = 0, 1, 2 in turn, a set b_i reflects axis 0 and a clear b_i exchanges
+// axes 0 and i.  One level is consumed per step through a 768-entry table
+// (state, octant) -> (next state, digit) that every thread block derives from
+// the automaton into shared memory; the octant bits are read off the point's
+// Morton key, three bits per level.
 #pragma once
 #include <stdint.h>
 
@@ -84,6 +103,83 @@ __device__ __forceinline__ uint64_t hilbert2_key(const uint8_t *tab, uint32_t x,
   return d;
 }
 
+// Bytes of shared memory for the curve tables of either dimension.
+constexpr int kCurveTabBytes = 1536;
+
+// The 3D automaton state: perm index (0..5) x 16 + reflections x 2 + parity;
+// permutations in lexicographic order (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0).
+__device__ __forceinline__ void perm3_of(int idx, int *p) {
+  const int p0 = idx >> 1;
+  const int a = p0 == 0 ? 1 : 0;        // smaller remaining axis
+  const int b = p0 == 2 ? 1 : 2;        // larger remaining axis
+  p[0] = p0;
+  p[1] = (idx & 1) ? b : a;
+  p[2] = (idx & 1) ? a : b;
+}
+
+// Fills the 768-entry table as uint16 (next state x 64 | digit); call with all
+// threads, then sync.
+__device__ __forceinline__ void hilbert3_table_init(uint8_t *tab8) {
+  uint16_t *tab = reinterpret_cast<uint16_t *>(tab8);
+  for (int e = threadIdx.x; e < 768; e += blockDim.x) {
+    const int id = e >> 3, r = e & 7;
+    int p[3];
+    perm3_of(id >> 4, p);
+    int f = (id >> 1) & 7, par = id & 1;
+    int b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b[i] = ((r >> p[i]) & 1) ^ ((f >> i) & 1);
+    const int g0 = b[0], g1 = b[0] ^ b[1], g2 = g1 ^ b[2];
+    const int digit = ((g0 ^ par) << 2) | ((g1 ^ par) << 1) | (g2 ^ par);
+    par ^= g2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (b[i]) {
+        f ^= 1;
+      } else if (i) {
+        const int t = p[0];
+        p[0] = p[i];
+        p[i] = t;
+        const int f0 = f & 1, fi = (f >> i) & 1;
+        f = (f & ~(1 | (1 << i))) | fi | (f0 << i);
+      }
+    }
+    int pi = 0;
+    for (int c = 0; c < 6; ++c) {
+      int q[3];
+      perm3_of(c, q);
+      if (q[0] == p[0] && q[1] == p[1]) pi = c;
+    }
+    const int next = (pi << 4) | (f << 1) | par;
+    tab[e] = (uint16_t)((next << 6) | digit);
+  }
+}
+
+__device__ __forceinline__ uint64_t hilbert3_key(const uint8_t *tab8, uint32_t x, uint32_t y, uint32_t z,
+                                                 int bits) {
+  const uint16_t *tab = reinterpret_cast<const uint16_t *>(tab8);
+  const uint64_t m = morton3_key(x, y, z);
+  uint32_t st = 0;  // state x 8
+  uint64_t d = 0;
+  for (int l = bits - 1; l >= 0; --l) {
+    const uint32_t e = tab[st | (uint32_t)((m >> (3 * l)) & 7u)];
+    d = (d << 3) | (e & 7u);
+    st = e >> 3;
+  }
+  return d;
+}
+
+// Curve table of the (D, CURVE) key; call with all threads, then sync.
+template <int D, int CURVE>
+__device__ __forceinline__ void curve_table_init(uint8_t *tab) {
+  if (CURVE == 1) {
+    if (D == 2)
+      hilbert_table_init(tab);
+    else
+      hilbert3_table_init(tab);
+  }
+}
+
 // Key of point p (dim coordinates) under the encode spec; sets *bad if a
 // coordinate lies outside [0, 2^bits).
 template <int D, int CURVE>
@@ -93,6 +189,7 @@ __device__ __forceinline__ uint64_t point_key(const uint8_t *htab, const int32_t
 #pragma unroll
   for (int d = 0; d < D; ++d) b |= (uint32_t)c[d] >= lim;
   bad = b;
+  if (CURVE == 1 && D == 3) return hilbert3_key(htab, (uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[D - 1], bits);
   if (CURVE == 1) return hilbert2_key(htab, (uint32_t)c[0], (uint32_t)c[1], bits);
   if (D == 2) return morton2_key((uint32_t)c[0], (uint32_t)c[1]);
   return morton3_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2]);

@@ -45,7 +45,6 @@ template <int RB>
 struct Radix {
   static constexpr int RADIX = 1 << RB;
   static constexpr int DPT = RADIX / ST;
-  static constexpr int PASSES64 = (64 + RB - 1) / RB;
   static constexpr int HIST_PARTS = RB == 8 ? 4 : 1;
   using Count = typename std::conditional<RB == 8, uint32_t, uint16_t>::type;
   using Digit = typename std::conditional<RB == 8, uint8_t, uint16_t>::type;
@@ -62,7 +61,7 @@ struct OnesweepSmem {
   alignas(16) uint64_t stage[TILE];    // keys (then values) in digit order
   typename R::Digit dig[TILE];         // digit of each staged position
   uint32_t wsum[SW];
-  uint8_t htab[256];
+  alignas(16) uint8_t htab[kCurveTabBytes];
   uint32_t tile;
 };
 
@@ -97,7 +96,7 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][passes][RADIX]
   uint8_t *htab = smem_raw + sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX;
   for (int i = threadIdx.x; i < R::HIST_PARTS * passes * R::RADIX; i += blockDim.x) shp[i] = 0;
-  if (MODE == 1 && CURVE == 1) hilbert_table_init(htab);
+  if (MODE == 1) curve_table_init<D, CURVE>(htab);
   __syncthreads();
   bool bad_any = false;
   uint32_t *mine = shp + (threadIdx.x % R::HIST_PARTS) * passes * R::RADIX;
@@ -181,7 +180,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
     uint32_t *z = reinterpret_cast<uint32_t *>(&sm.wh[0][0]);
     for (int i = tid; i < (int)(sizeof(sm.wh) / 4); i += ST) z[i] = 0;
   }
-  if (MODE == 1 && CURVE == 1) hilbert_table_init(sm.htab);
+  if (MODE == 1) curve_table_init<D, CURVE>(sm.htab);
   if (a.hist_next)
     for (int i = tid; i < RADIX; i += ST) sm.nh[i] = 0;
   if (a.gbase) {
@@ -487,7 +486,7 @@ static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_
                               int *status, cudaStream_t s) {
   using R = Radix<RB>;
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
-  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX + 256;
+  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX + kCurveTabBytes;
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
   PSI_LAUNCH_NAMED("k_sort_hist", kern, std::max(grid, 1), 256, smem, s, kin, enc.pts, enc.bits, enc.key_shift, n,
@@ -537,8 +536,10 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
   else if (enc.dim == 2)
     st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
-  else
+  else if (enc.curve == CURVE_MORTON)
     st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
+  else
+    st = launch_hist<1, 3, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
   if (st) return st;
 
   uint64_t *kb[2] = {kbuf0, kbuf1};
@@ -568,8 +569,10 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
       st = launch_pass<1, 2, 0, RB>(a, tiles, s);
     else if (enc.dim == 2)
       st = launch_pass<1, 2, 1, RB>(a, tiles, s);
-    else
+    else if (enc.curve == CURVE_MORTON)
       st = launch_pass<1, 3, 0, RB>(a, tiles, s);
+    else
+      st = launch_pass<1, 3, 1, RB>(a, tiles, s);
     if (st) return st;
   }
   out->keys = kb[(passes - 1) & 1];
@@ -589,7 +592,6 @@ psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint
   }
   const bool encode = enc.pts != nullptr;
   if (encode && (enc.dim != 2 && enc.dim != 3)) return PSI_ERR_INVALID;
-  if (encode && enc.curve == CURVE_HILBERT && enc.dim != 2) return PSI_ERR_INVALID;
   key_bits = std::max(1, std::min(64, key_bits));
   psi_status st;
   switch (pick_radix(key_bits, radix_bits)) {

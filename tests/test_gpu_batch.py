@@ -76,10 +76,11 @@ def test_batch_layout_and_knn_match_oracle(kind, threads):
         assert (gd[qoff[i]:qoff[i + 1]] == od).all(), i
 
 
-def test_batch_3d_and_k100():
+@pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
+def test_batch_3d_and_k100(kind):
     sizes = [500, 20000, 3, 7000]
     pts, ids, off = make_batch(sizes, dim=3, bits=21, seed=4)
-    b = psi.Batch(off, dim=3, kind="spac_z", leaf_size=16, coord_bits=21)
+    b = psi.Batch(off, dim=3, kind=kind, leaf_size=16, coord_bits=21)
     b.build(T(pts), T(ids))
     q, qoff = queries(sizes, pts, off, 3, 21, 9)
     gi, gd = b.knn(T(q), T(qoff), 100)

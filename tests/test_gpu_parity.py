@@ -52,7 +52,8 @@ def points(n, dim, bits, seed, dup=False, clustered=False):
 # ---------------------------------------------------------------- keys, sort
 
 @pytest.mark.parametrize("dim,bits,kind", [(2, 30, "spac_z"), (2, 30, "spac_h"), (3, 21, "spac_z"), (2, 31, "spac_h"),
-                                           (2, 7, "spac_h"), (2, 1, "spac_h"), (3, 5, "porth"), (2, 31, "spac_z")])
+                                           (2, 7, "spac_h"), (2, 1, "spac_h"), (3, 5, "porth"), (2, 31, "spac_z"),
+                                           (3, 21, "spac_h"), (3, 1, "spac_h"), (3, 9, "spac_h")])
 def test_encode_matches_oracle(dim, bits, kind):
     p = gen.uniform(5000, dim, bits, 3)
     p[:4] = 0
@@ -125,7 +126,7 @@ def test_spac_build_layout(kind, n, phi, fanout):
 
 
 @pytest.mark.parametrize("radix", [8, 10, 11])
-@pytest.mark.parametrize("kind,dim,bits", [("spac_h", 2, 30), ("spac_z", 3, 21), ("porth", 2, 30)])
+@pytest.mark.parametrize("kind,dim,bits", [("spac_h", 2, 30), ("spac_z", 3, 21), ("porth", 2, 30), ("spac_h", 3, 21)])
 def test_every_digit_width_gives_the_same_index(radix, kind, dim, bits):
     p, ids = points(100003, dim, bits, 61 + radix, clustered=True)
     ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits, radix_bits=radix)
@@ -146,11 +147,12 @@ def test_every_digit_width_gives_the_same_index(radix, kind, dim, bits):
     assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
 
 
+@pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
 @pytest.mark.parametrize("dup", [False, True])
-def test_spac_build_layout_3d_and_duplicates(dup):
+def test_spac_build_layout_3d_and_duplicates(kind, dup):
     p, ids = points(60000, 3, 21, 5, dup=dup)
-    ix = psi.Index(T(p), T(ids), kind="spac_z", leaf_size=32, coord_bits=21)
-    o = O.Index(p, ids, dim=3, kind=O.SPAC_Z, phi=32, bits=21)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=21)
+    o = O.Index(p, ids, dim=3, kind=KIND[kind], phi=32, bits=21)
     check_spac_layout(ix, o)
 
 
@@ -181,7 +183,7 @@ def query_points(nq, dim, bits, seed, data):
 
 
 @pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("spac_z", 3, 21),
-                                           ("porth", 3, 21)])
+                                           ("porth", 3, 21), ("spac_h", 3, 21)])
 @pytest.mark.parametrize("k", [1, 10, 32, 33, 100, 128])
 def test_knn_matches_oracle(kind, dim, bits, k):
     n = 30000
@@ -216,7 +218,8 @@ def test_knn_ties_by_id():
     assert U32(gi)[0].tolist() == want and gd.cpu().tolist()[0] == [100] * 4
 
 
-@pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("porth", 3, 21)])
+@pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("porth", 3, 21),
+                                           ("spac_z", 3, 21), ("spac_h", 3, 21)])
 def test_range_count_and_report_match_oracle(kind, dim, bits):
     n = 40000
     p, ids = points(n, dim, bits, 31, clustered=True)
@@ -270,24 +273,25 @@ def spac_invariants(ix):
     assert all((pair < nxt[leaf]) & ((pair >= sep[leaf]) | (leaf == 0)))
 
 
-@pytest.mark.parametrize("kind", ["spac_z", "spac_h", "porth"])
-def test_updates_match_oracle(kind):
+@pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("spac_h", 3, 21),
+                                           ("porth", 3, 21)])
+def test_updates_match_oracle(kind, dim, bits):
     n = 50000
-    p, ids = points(n, 2, 30, 41, clustered=True)
-    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32)
-    o = O.Index(p, ids, kind=KIND[kind], phi=32)
+    p, ids = points(n, dim, bits, 41, clustered=True)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
     live_p, live_i = p, ids
     rng_seed = 5
     for step, (m_ins, m_del, ood) in enumerate([(5000, 3000, False), (20000, 1000, True), (100, 30000, False),
                                                 (60000, 0, True), (0, 50000, False)]):
-        newp = gen.varden(m_ins, 2, 30, 1000 + step, x_range=(1 << 29, 1 << 30) if ood else None)
+        newp = gen.varden(m_ins, dim, bits, 1000 + step, x_range=(1 << (bits - 1), 1 << bits) if ood else None)
         newi = (np.arange(m_ins, dtype=np.uint32) + 10_000_000 * (step + 1)).astype(np.uint32)
         ix.insert(T(newp), T(newi))
         o.insert(newp, newi)
         live_p = np.concatenate([live_p, newp])
         live_i = np.concatenate([live_i, newi])
         sel = gen.sample_without_replacement(len(live_i), min(m_del, len(live_i)), rng_seed + step)
-        dp = np.concatenate([live_p[sel], [[3, 4]]]).astype(np.int32)   # plus one absent point
+        dp = np.concatenate([live_p[sel], [[3, 4, 5][:dim]]]).astype(np.int32)   # plus one absent point
         di = np.concatenate([live_i[sel], [live_i[0]]]).astype(np.uint32)
         nd = torch.zeros(1, dtype=torch.int64, device=DEV)
         ix.delete(T(dp), T(di), nd)
@@ -310,11 +314,11 @@ def test_updates_match_oracle(kind):
         if kind != "porth" and len(live_i):
             spac_invariants(ix)
         # queries
-        q = query_points(3000, 2, 30, 7 + step, live_p)
+        q = query_points(3000, dim, bits, 7 + step, live_p)
         gi, gd = ix.knn(T(q), 10)
         oi2, od2 = o.knn(q, 10)
         assert (U32(gi) == oi2).all() and (gd.cpu().numpy() == od2).all()
-        boxes = gen.square_boxes(300, 2, 30, 1 << 23, 9 + step)
+        boxes = gen.square_boxes(300, dim, bits, 1 << (bits - 7), 9 + step)
         assert (ix.range_count(T(boxes)).cpu().numpy() == o.range_count(boxes)).all()
         if kind == "porth":
             check_porth_nodes(ix, o)
