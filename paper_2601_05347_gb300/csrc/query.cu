@@ -21,6 +21,24 @@
 #include "keys.cuh"
 
 namespace psi {
+
+// Seed-leaf inputs of the k-NN kernel (all null/zero: no seed).
+struct KnnSeed {
+  const uint64_t *qkey = nullptr;
+  const uint64_t *sep_key = nullptr;
+  int64_t L = 0;
+  int key_shift = 0;
+};
+
+// Curve order of a query batch and its sorted keys; owns the sort buffers.
+struct QueryOrder {
+  Buf<uint64_t> k0, k1;
+  Buf<uint32_t> v0, v1;
+  const uint32_t *order = nullptr;
+  const uint64_t *keys = nullptr;
+  int key_shift = 0;
+};
+
 namespace {
 
 constexpr int QW = 4;         // warps per block
@@ -63,6 +81,12 @@ struct KnnArgs {
   int k;
   const uint32_t *order;
   const int32_t *qroot;  // per-query root (many indexes in one node array), or null
+  // seed leaf (SPaC only): qkey[i] = top bits of the curve key of the i-th query
+  // in curve order, sep_key[j] = first key of leaf j (node j); null: no seed
+  const uint64_t *qkey;
+  const uint64_t *sep_key;
+  int64_t L;
+  int key_shift;  // qkey = curve key >> key_shift
   uint32_t *out_id;
   int64_t *out_d2;
   int *status;
@@ -234,14 +258,33 @@ struct KnnStats {
 
 constexpr int MAXLVL = 33;  // tree depth bound (P-Orth: 31 levels below the root)
 
+// Last leaf j whose first key (>> shift) is <= key, or 0: a 32-ary search by
+// the warp, one ballot over 32 evenly spaced separators per round.
+__device__ __forceinline__ int64_t seed_leaf(const uint64_t *sep_key, int64_t L, uint64_t key, int shift) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = L;  // the answer lies in [lo, hi)
+  while (hi - lo > 1) {
+    const int64_t step = (hi - lo + 31) >> 5;
+    const int64_t p = lo + (int64_t)lane * step;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, p < hi && (sep_key[p] >> shift) <= key);
+    if (m == 0) return lo;  // only when lo == 0: the key precedes every leaf
+    lo += (int64_t)(31 - __clz(m)) * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
 // One warp per query: depth-first search that always enters the nearest
 // not-yet-visited child (Appendix "Implementation Details": children in
 // increasing box distance).  Each level of the current path keeps, in shared
 // memory, its children's distance keys and a bitmask of children still to
 // visit; one ballot prunes every remaining child farther than the current
-// k-th distance, one reduce picks the nearest.  The first path taken is the
-// greedy descent to the nearest leaf, which makes the k-th distance finite
-// early.
+// k-th distance, one reduce picks the nearest.
+// Seed (SPaC): the leaf that holds the query's own curve position is scanned
+// first.  SPaC leaves are consecutive runs of the curve and their boxes
+// overlap, so the nearest box is often not the leaf around the query; the
+// curve neighbours make the k-th distance nearly final before the search
+// starts, and the search then skips the seed leaf.
 template <int D, int KPL, bool STATS>
 __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
   __shared__ uint32_t s_key[QW][MAXLVL][32];
@@ -260,6 +303,28 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     KList<KPL> kl;
     kl.init();
     const int32_t root = a.qroot ? a.qroot[q] : t.root;
+    // seed leaves [s_lo, s_hi]: the leaf at the query's curve position, widened
+    // along the curve until it holds at least k points
+    int64_t s_lo = 0, s_hi = -1;
+    if (a.qkey && root >= 0 && a.L > 0) {
+      const int64_t j = seed_leaf(a.sep_key, a.L, a.qkey[qi], a.key_shift);
+      int64_t got = 0;
+      s_lo = j;
+      s_hi = j - 1;
+      while (got < a.k && (s_lo > 0 || s_hi + 1 < a.L)) {
+        int64_t nx;
+        if (s_hi < s_lo || (s_hi + 1 < a.L && (s_lo == 0 || s_hi - j <= j - s_lo)))
+          nx = ++s_hi;
+        else
+          nx = --s_lo;
+        knn_scan_leaf<D, KPL>(t, (uint32_t)nx, qc, kl, a.k);
+        got += t.cnt[nx];
+        if (STATS) {
+          ++n_leaf;
+          n_pts += t.cnt[nx];
+        }
+      }
+    }
     uint32_t kdk = order_key(kl.kd);
     auto expand = [&](uint32_t node, int lvl) {
       const int nk = t.kids[node];
@@ -284,7 +349,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     };
     if (root >= 0) {
       if (t.kids[root] == 0) {
-        knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k);
+        if (s_hi < s_lo) knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k);
       } else {
         int lvl = 0;
         expand((uint32_t)root, 0);
@@ -304,6 +369,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
           if (lane == 0) s_mask[w][lvl] = m & ~(1u << src);
           __syncwarp();
           if (is_leaf) {
+            if ((int64_t)child >= s_lo && (int64_t)child <= s_hi) continue;  // scanned as a seed
             knn_scan_leaf<D, KPL>(t, child, qc, kl, a.k);
             kdk = order_key(kl.kd);
             if (STATS) {
@@ -473,36 +539,35 @@ int query_grid(int64_t nq) {
 }  // namespace
 
 // Sorts the query points along the index's curve so that neighbouring warps
-// traverse neighbouring parts of the tree; returns the permutation in *order.
-psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, Buf<uint32_t> &order_buf, uint32_t **order,
-                       cudaStream_t s) {
-  *order = nullptr;
+// traverse neighbouring parts of the tree; returns the permutation in *order
+// and the sorted keys (curve key >> *key_shift) in *qkeys.
+psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, QueryOrder &qo, cudaStream_t s) {
+  qo.order = nullptr;
+  qo.keys = nullptr;
   if (nq < 4096) return PSI_OK;
-  Buf<uint64_t> k0, k1;
-  Buf<uint32_t> v1;
   psi_status st;
-  if ((st = k0.alloc(nq, s)) || (st = k1.alloc(nq, s)) || (st = order_buf.alloc(nq, s)) || (st = v1.alloc(nq, s)))
+  if ((st = qo.k0.alloc(nq, s)) || (st = qo.k1.alloc(nq, s)) || (st = qo.v0.alloc(nq, s)) ||
+      (st = qo.v1.alloc(nq, s)))
     return st;
   // locality only needs the top bits of the curve key: 48 bits, 6 digit passes
   EncodeSpec e = encode_spec(ix, q);
   const int order_bits = std::min(48, ix->key_bits);
   e.key_shift = ix->key_bits - order_bits;
   SortResult r;
-  if ((st = sort_pairs(e, nullptr, nullptr, nq, order_bits, nullptr, k0.p, order_buf.p, k1.p, v1.p, ix->d_status,
-                       s, &r)))
+  if ((st = sort_pairs(e, nullptr, nullptr, nq, order_bits, nullptr, qo.k0.p, qo.v0.p, qo.k1.p, qo.v1.p,
+                       ix->d_status, s, &r)))
     return st;
-  if (r.vals == v1.p) {
-    std::swap(order_buf.p, v1.p);
-  }
-  *order = order_buf.p;
+  qo.order = r.vals;
+  qo.keys = r.keys;
+  qo.key_shift = e.key_shift;
   return PSI_OK;
 }
 
 psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
                          const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status,
-                         unsigned long long *d_stats, cudaStream_t s) {
+                         unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed) {
   if (nq == 0) return PSI_OK;
-  KnnArgs a{tv, q, nq, k, order, qroot, out_id, out_d2, status};
+  KnnArgs a{tv, q, nq, k, order, qroot, seed.qkey, seed.sep_key, seed.L, seed.key_shift, out_id, out_d2, status};
   KnnStats stats{d_stats};
   const int g = query_grid(nq);
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
@@ -529,17 +594,24 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
 
 psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
                          const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status, cudaStream_t s) {
-  return run_knn_roots(tv, q, nq, k, order, qroot, D, out_id, out_d2, status, nullptr, s);
+  return run_knn_roots(tv, q, nq, k, order, qroot, D, out_id, out_d2, status, nullptr, s, KnnSeed{});
 }
 
 psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uint32_t *out_id, int64_t *out_d2,
                    unsigned long long *d_stats, cudaStream_t s) {
   if (nq == 0) return PSI_OK;
-  Buf<uint32_t> ob;
-  uint32_t *order = nullptr;
-  psi_status st = query_order(ix, q, nq, ob, &order, s);
+  QueryOrder qo;
+  psi_status st = query_order(ix, q, nq, qo, s);
   if (st) return st;
-  return run_knn_roots(ix->view(), q, nq, k, order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s);
+  KnnSeed seed;
+  if (ix->cfg.kind != PSI_PORTH && qo.keys) {  // P-Orth leaves do not overlap: no seed needed
+    seed.qkey = qo.keys;
+    seed.sep_key = ix->sep_key;
+    seed.L = ix->L;
+    seed.key_shift = qo.key_shift;
+  }
+  return run_knn_roots(ix->view(), q, nq, k, qo.order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s,
+                       seed);
 }
 
 psi_status run_range_count(const psi_index *ix, const int32_t *boxes, int64_t nq, int64_t *counts, cudaStream_t s) {
