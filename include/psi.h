@@ -233,6 +233,10 @@ psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n,
 psi_status psi_knn_instrumented(const psi_index *ix, const int32_t *d_q, int64_t q, int32_t k, uint32_t *d_ids,
                                 int64_t *d_d2, uint64_t *d_stats, void *stream);
 
+/* psi_batch_knn with the same traversal counters (summed over all indexes). */
+psi_status psi_batch_knn_instrumented(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq,
+                                      int32_t k, uint32_t *d_ids, int64_t *d_d2, uint64_t *d_stats, void *stream);
+
 /* Number of kernels this library has launched in the process. */
 int64_t psi_launch_count(void);
 

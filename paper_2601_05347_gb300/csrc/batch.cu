@@ -51,8 +51,6 @@ struct psi_batch {
 
 namespace psi {
 
-psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
-                         const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status, cudaStream_t s);
 int64_t summary_capacity(int64_t L, int F);
 
 namespace {
@@ -634,8 +632,8 @@ psi_status psi_batch_knn_reserve(psi_batch *b, int64_t max_queries, void *stream
   return PSI_OK;
 }
 
-psi_status psi_batch_knn(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq, int32_t k,
-                         uint32_t *d_ids, int64_t *d_d2, void *stream) {
+static psi_status batch_knn(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq, int32_t k,
+                            uint32_t *d_ids, int64_t *d_d2, unsigned long long *d_stats, void *stream) {
   set_error("");
   if (!b || nq < 0 || k < 1 || k > 128 || (nq > 0 && (!d_q || !d_qoffsets || !d_ids || !d_d2))) {
     set_error("invalid batch k-NN arguments (1 <= k <= 128)");
@@ -681,7 +679,30 @@ psi_status psi_batch_knn(psi_batch *b, const int32_t *d_q, const int64_t *d_qoff
   tv.kids = b->nodes.kids;
   tv.pid = b->pool.pid;
   tv.root = -1;
-  return run_knn_roots(tv, d_q, nq, k, r.vals, b->d_qroot, b->D, d_ids, d_d2, b->d_status, s);
+  KnnSeed seed;  // leaves at each query's curve position in its own index
+  seed.qkey = r.keys;
+  seed.qkey_mask = (uint64_t(1) << order_bits) - 1;
+  seed.key_shift = shift;
+  seed.qseg = b->d_qseg;
+  seed.off = b->d_off;
+  seed.node_off = b->d_node_off;
+  seed.phi = b->phi;
+  seed.pkey = b->pool.pkey;
+  return run_knn_roots(tv, d_q, nq, k, r.vals, b->d_qroot, b->D, d_ids, d_d2, b->d_status, d_stats, s, seed);
+}
+
+psi_status psi_batch_knn(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq, int32_t k,
+                         uint32_t *d_ids, int64_t *d_d2, void *stream) {
+  return batch_knn(b, d_q, d_qoffsets, nq, k, d_ids, d_d2, nullptr, stream);
+}
+
+psi_status psi_batch_knn_instrumented(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq,
+                                      int32_t k, uint32_t *d_ids, int64_t *d_d2, uint64_t *d_stats, void *stream) {
+  if (!d_stats) {
+    set_error("psi_batch_knn_instrumented: d_stats is null");
+    return PSI_ERR_INVALID;
+  }
+  return batch_knn(b, d_q, d_qoffsets, nq, k, d_ids, d_d2, (unsigned long long *)d_stats, stream);
 }
 
 psi_status psi_batch_sync(psi_batch *b, void *stream) {

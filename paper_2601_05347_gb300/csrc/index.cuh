@@ -109,4 +109,29 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
 psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, int64_t *d_deleted,
                        cudaStream_t s);
 EncodeSpec encode_spec(const psi_index *ix, const int32_t *pts);
+
+// Seed-leaf inputs of the k-NN kernel (qkey null: no seed).  qkey[i] holds
+// the curve key of the i-th query in curve order (bits in qkey_mask, the key
+// shifted right by key_shift).  One index: leaf j is node j and its first key
+// is sep_key[j].  Many indexes: query q belongs to index qseg[q], whose leaves
+// are nodes node_off[i] + [0, ceil(n_i / phi)) with n_i = off[i+1] - off[i],
+// built once, so a leaf's first slot holds its smallest key pkey[ref[leaf]].
+struct KnnSeed {
+  const uint64_t *qkey = nullptr;
+  uint64_t qkey_mask = ~0ull;
+  int key_shift = 0;
+  const uint64_t *sep_key = nullptr;
+  int64_t L = 0;
+  const int32_t *qseg = nullptr;
+  const int64_t *off = nullptr;
+  const int64_t *node_off = nullptr;
+  int phi = 0;
+  const uint64_t *pkey = nullptr;
+};
+
+// k-NN of nq queries, each starting at qroot[q] (or tv.root when qroot is
+// null), in the given query order; d_stats (or null) receives traversal counts.
+psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
+                         const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status,
+                         unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed);
 }  // namespace psi

@@ -22,14 +22,6 @@
 
 namespace psi {
 
-// Seed-leaf inputs of the k-NN kernel (all null/zero: no seed).
-struct KnnSeed {
-  const uint64_t *qkey = nullptr;
-  const uint64_t *sep_key = nullptr;
-  int64_t L = 0;
-  int key_shift = 0;
-};
-
 // Curve order of a query batch and its sorted keys; owns the sort buffers.
 struct QueryOrder {
   Buf<uint64_t> k0, k1;
@@ -81,12 +73,7 @@ struct KnnArgs {
   int k;
   const uint32_t *order;
   const int32_t *qroot;  // per-query root (many indexes in one node array), or null
-  // seed leaf (SPaC only): qkey[i] = top bits of the curve key of the i-th query
-  // in curve order, sep_key[j] = first key of leaf j (node j); null: no seed
-  const uint64_t *qkey;
-  const uint64_t *sep_key;
-  int64_t L;
-  int key_shift;  // qkey = curve key >> key_shift
+  KnnSeed seed;  // SPaC: leaves scanned before the search
   uint32_t *out_id;
   int64_t *out_d2;
   int *status;
@@ -258,15 +245,16 @@ struct KnnStats {
 
 constexpr int MAXLVL = 33;  // tree depth bound (P-Orth: 31 levels below the root)
 
-// Last leaf j whose first key (>> shift) is <= key, or 0: a 32-ary search by
-// the warp, one ballot over 32 evenly spaced separators per round.
-__device__ __forceinline__ int64_t seed_leaf(const uint64_t *sep_key, int64_t L, uint64_t key, int shift) {
+// Last leaf j in [0, L) whose first key (>> shift) is <= key, or 0: a 32-ary
+// search by the warp, one ballot over 32 evenly spaced leaves per round.
+template <typename FirstKey>
+__device__ __forceinline__ int64_t seed_leaf(FirstKey first_key, int64_t L, uint64_t key, int shift) {
   const int lane = threadIdx.x & 31;
   int64_t lo = 0, hi = L;  // the answer lies in [lo, hi)
   while (hi - lo > 1) {
     const int64_t step = (hi - lo + 31) >> 5;
     const int64_t p = lo + (int64_t)lane * step;
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, p < hi && (sep_key[p] >> shift) <= key);
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, p < hi && (first_key(p) >> shift) <= key);
     if (m == 0) return lo;  // only when lo == 0: the key precedes every leaf
     lo += (int64_t)(31 - __clz(m)) * step;
     hi = min(hi, lo + step);
@@ -306,14 +294,25 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     // seed leaves [s_lo, s_hi]: the leaf at the query's curve position, widened
     // along the curve until it holds at least k points
     int64_t s_lo = 0, s_hi = -1;
-    if (a.qkey && root >= 0 && a.L > 0) {
-      const int64_t j = seed_leaf(a.sep_key, a.L, a.qkey[qi], a.key_shift);
+    const KnnSeed &sd = a.seed;
+    int64_t lb = 0, L = sd.L;  // the query's leaves are nodes [lb, lb + L)
+    if (sd.qkey && sd.qseg) {
+      const int sg = sd.qseg[q];
+      lb = sd.node_off[sg];
+      L = (sd.off[sg + 1] - sd.off[sg] + sd.phi - 1) / sd.phi;
+    }
+    if (sd.qkey && root >= 0 && L > 0) {
+      const uint64_t key = sd.qkey[qi] & sd.qkey_mask;
+      const int64_t j =
+          lb + (sd.sep_key ? seed_leaf([&](int64_t p) { return sd.sep_key[p]; }, L, key, sd.key_shift)
+                           : seed_leaf([&](int64_t p) { return sd.pkey[t.ref[lb + p]]; }, L, key, sd.key_shift));
+      const int64_t le = lb + L;
       int64_t got = 0;
       s_lo = j;
       s_hi = j - 1;
-      while (got < a.k && (s_lo > 0 || s_hi + 1 < a.L)) {
+      while (got < a.k && (s_lo > lb || s_hi + 1 < le)) {
         int64_t nx;
-        if (s_hi < s_lo || (s_hi + 1 < a.L && (s_lo == 0 || s_hi - j <= j - s_lo)))
+        if (s_hi < s_lo || (s_hi + 1 < le && (s_lo == lb || s_hi - j <= j - s_lo)))
           nx = ++s_hi;
         else
           nx = --s_lo;
@@ -567,7 +566,7 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
                          const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status,
                          unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed) {
   if (nq == 0) return PSI_OK;
-  KnnArgs a{tv, q, nq, k, order, qroot, seed.qkey, seed.sep_key, seed.L, seed.key_shift, out_id, out_d2, status};
+  KnnArgs a{tv, q, nq, k, order, qroot, seed, out_id, out_d2, status};
   KnnStats stats{d_stats};
   const int g = query_grid(nq);
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
@@ -592,10 +591,7 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
   return PSI_OK;
 }
 
-psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
-                         const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status, cudaStream_t s) {
-  return run_knn_roots(tv, q, nq, k, order, qroot, D, out_id, out_d2, status, nullptr, s, KnnSeed{});
-}
+
 
 psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uint32_t *out_id, int64_t *out_d2,
                    unsigned long long *d_stats, cudaStream_t s) {

@@ -74,6 +74,7 @@ def lib():
             "psi_batch_build": (st, [P, P, P, P]),
             "psi_batch_knn_reserve": (st, [P, i64, P]),
             "psi_batch_knn": (st, [P, P, P, i64, i32, P, P, P]),
+            "psi_batch_knn_instrumented": (st, [P, P, P, i64, i32, P, P, P, P]),
             "psi_batch_sync": (st, [P, P]),
             "psi_batch_destroy": (st, [P]),
             "psi_batch_num_leaves": (i64, [P, i32]),
@@ -299,6 +300,19 @@ class Batch:
         _check(lib().psi_batch_knn(self._h, _ptr(q.contiguous()), _ptr(qoffsets.contiguous()), nq, k, _ptr(out_ids),
                                    _ptr(out_d2), _stream(stream)))
         return out_ids, out_d2
+
+    def knn_stats(self, q: torch.Tensor, qoffsets: torch.Tensor, k: int, stream=None):
+        """Batched k-NN with traversal counters: (ids, d2, {nodes, leaves, points, queries})."""
+        nq = int(q.shape[0])
+        if nq > self._qcap:
+            self.reserve(nq, stream)
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        out_d2 = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        st = torch.zeros(4, dtype=torch.int64, device=q.device)
+        _check(lib().psi_batch_knn_instrumented(self._h, _ptr(q.contiguous()), _ptr(qoffsets.contiguous()), nq, k,
+                                                _ptr(out_ids), _ptr(out_d2), _ptr(st), _stream(stream)))
+        c = st.cpu().tolist()
+        return out_ids, out_d2, {"nodes": c[0], "leaves": c[1], "points": c[2], "queries": c[3]}
 
     def sync(self, stream=None):
         _check(lib().psi_batch_sync(self._h, _stream(stream)))

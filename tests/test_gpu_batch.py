@@ -119,3 +119,18 @@ def test_batch_replays_from_cuda_graph():
     o = O.Index(pts[off[9]:off[10]], ids[off[9]:off[10]], kind=O.SPAC_H, phi=32)
     oi, od = o.knn(q[qoff[9]:qoff[10]], 10)
     assert (out_i.cpu().numpy().view(np.uint32)[qoff[9]:qoff[10]] == oi).all()
+
+
+def test_batch_knn_instrumented_matches_and_counts():
+    pts, ids, off = make_batch(SIZES, seed=13)
+    b = psi.Batch(off, kind="spac_h", leaf_size=32)
+    b.build(T(pts), T(ids))
+    q, qoff = queries(SIZES, pts, off, 2, 30, 17)
+    gi, gd = b.knn(T(q), T(qoff), 10)
+    si, sd, st = b.knn_stats(T(q), T(qoff), 10)
+    assert torch.equal(gi, si) and torch.equal(gd, sd)
+    assert st["queries"] == len(q)
+    # every query of a non-empty index scans at least one leaf; points scanned
+    # are at most 2*phi per leaf
+    nonempty = sum(int(qoff[i + 1] - qoff[i]) for i, n in enumerate(SIZES) if n)
+    assert st["leaves"] >= nonempty and st["points"] <= 64 * st["leaves"]
