@@ -94,15 +94,20 @@ __global__ void k_insert_plan(const int32_t *cnt, const int32_t *sbeg, const int
 
 constexpr int MAXPL = 4;  // points per lane in one block (C <= 128)
 
-// Sorts, in place, the block of every leaf that will be re-wrapped.
+// Sorts, in place, the block of every leaf that will be re-wrapped.  A warp
+// takes 32 leaves: one lane per leaf finds the few that overflow, then the
+// warp sorts each of those.
 __global__ void k_sort_overflow_leaves(const int32_t *ncnt, const uint32_t *nref, const int32_t *sbeg,
                                        const int32_t *send, int64_t L, int C, int D, Pool pool) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < L; j += warps) {
-    const int len = send[j] - sbeg[j];
+  for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < L; j0 += warps * 32) {
+    const int64_t jl = j0 + lane;
+    uint32_t todo = __ballot_sync(0xFFFFFFFFu, jl < L && send[jl] > sbeg[jl] && ncnt[jl] + (send[jl] - sbeg[jl]) > C);
+   while (todo) {
+    const int64_t j = j0 + __ffs(todo) - 1;
+    todo &= todo - 1;
     const int cnt = ncnt[j];
-    if (len == 0 || cnt + len <= C) continue;
     const uint32_t s0 = nref[j];
     uint64_t k[MAXPL];
     uint32_t id[MAXPL];
@@ -139,6 +144,8 @@ __global__ void k_sort_overflow_leaves(const int32_t *ncnt, const uint32_t *nref
         for (int d = 0; d < D; ++d) pool.px[d][s0 + rank[r]] = c[r][d];
       }
     }
+    __syncwarp();
+   }
   }
 }
 
@@ -164,11 +171,34 @@ Leaves leaves_of(NodeArrays &a, uint64_t *sk, uint32_t *si) {
   return l;
 }
 
-// owner[o] = old leaf whose output includes new leaf position o
-__global__ void k_owner_scatter(const int32_t *outl, const int64_t *pos, int64_t L, int32_t *owner) {
+// owner[o] = old leaf whose output includes new leaf position o.  A thread
+// writes the first kOwnerInline entries of its leaf; a leaf that becomes more
+// leaves than that (a long sorted run arriving at one place, e.g. a batch in a
+// region the index did not cover) is listed, and k_owner_fill_big spreads the
+// rest of its entries over a whole block.
+constexpr int kOwnerInline = 32;
+
+__global__ void k_owner_scatter(const int32_t *outl, const int64_t *pos, int64_t L, int32_t *owner, int32_t *big,
+                                uint32_t *n_big, int64_t cap_big) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = pos[j];
-    for (int t = 0; t < outl[j]; ++t) owner[p + t] = (int32_t)j;
+    const int r = outl[j];
+    for (int t = 0; t < min(r, kOwnerInline); ++t) owner[p + t] = (int32_t)j;
+    if (r > kOwnerInline) {
+      const uint32_t slot = atomicAdd(n_big, 1u);
+      if (slot < cap_big) big[slot] = (int32_t)j;
+    }
+  }
+}
+
+__global__ void k_owner_fill_big(const int32_t *outl, const int64_t *pos, const int32_t *big, const uint32_t *n_big,
+                                 int64_t cap_big, int32_t *owner) {
+  const int64_t nb = min((int64_t)*n_big, cap_big);
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int32_t j = big[b];
+    const int64_t p = pos[j];
+    const int r = outl[j];
+    for (int t = kOwnerInline + threadIdx.x; t < r; t += blockDim.x) owner[p + t] = j;
   }
 }
 
@@ -194,12 +224,39 @@ __device__ __forceinline__ bool leaf_before_slice(const InsertArgs &a, uint32_t 
   return a.pool.pid[ls] <= a.ids[a.bvals[bi]];
 }
 
-// One warp per new leaf position.
+// A warp takes 32 new leaf positions: a lane copies the descriptor of an
+// untouched leaf (most of them), then the warp builds each touched one.
 template <int D>
 __global__ void k_insert_apply(InsertArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < a.Lnew; o += warps) {
+  for (int64_t o0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; o0 < a.Lnew; o0 += warps * 32) {
+    bool touched = false;
+    {
+      const int64_t ol = o0 + lane;
+      if (ol < a.Lnew) {
+        const int64_t j = a.owner[ol];
+        if (a.send[j] == a.sbeg[j]) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            a.nw.lo[d][ol] = a.old.lo[d][j];
+            a.nw.hi[d][ol] = a.old.hi[d][j];
+          }
+          a.nw.cnt[ol] = a.old.cnt[j];
+          a.nw.ref[ol] = a.old.ref[j];
+          a.nw.kids[ol] = 0;
+          a.nw.depth[ol] = 0;
+          a.nw.sk[ol] = a.old.sk[j];
+          a.nw.si[ol] = a.old.si[j];
+        } else {
+          touched = true;
+        }
+      }
+    }
+    uint32_t todo = __ballot_sync(0xFFFFFFFFu, touched);
+   while (todo) {
+    const int64_t o = o0 + __ffs(todo) - 1;
+    todo &= todo - 1;
     const int64_t j = a.owner[o];
     const int t = (int)(o - a.pos[j]);
     const int len = a.send[j] - a.sbeg[j];
@@ -316,19 +373,26 @@ __global__ void k_insert_apply(InsertArgs a) {
         a.nw.si[o] = a.pool.pid[d0];
       }
     }
+    __syncwarp();
+   }
   }
 }
 
-// One warp per touched leaf: remove the points named by its slice.
+// Remove the points named by each leaf's slice: a warp takes 32 leaves, one
+// lane per leaf finds those with a slice, then the warp compacts each of them.
 template <int D>
 __global__ void k_delete_leaves(Leaves lv, Pool pool, const int32_t *sbeg, const int32_t *send, int64_t L,
                                 const uint64_t *bkeys, const uint32_t *bvals, const int32_t *pts,
                                 const uint32_t *ids, unsigned long long *deleted) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < L; j += warps) {
+  for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < L; j0 += warps * 32) {
+    const int64_t jl = j0 + lane;
+    uint32_t todo = __ballot_sync(0xFFFFFFFFu, jl < L && send[jl] > sbeg[jl]);
+   while (todo) {
+    const int64_t j = j0 + __ffs(todo) - 1;
+    todo &= todo - 1;
     const int64_t b = sbeg[j], e = send[j];
-    if (e == b) continue;
     const int cnt = lv.cnt[j];
     const uint32_t s0 = lv.ref[j];
     uint64_t k[MAXPL];
@@ -401,6 +465,8 @@ __global__ void k_delete_leaves(Leaves lv, Pool pool, const int32_t *sbeg, const
       }
       if (cnt - out) atomicAdd(deleted, (unsigned long long)(cnt - out));
     }
+    __syncwarp();
+   }
   }
 }
 
@@ -485,8 +551,8 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
 
   const int64_t base_block = ix->pool_used;
   if ((st = grow_pool(ix, (base_block + NB) * ix->C, base_block * ix->C, s))) return st;
-  PSI_LAUNCH(k_sort_overflow_leaves, warp_grid(L), 256, 0, s, ix->nodes.cnt, ix->nodes.ref, sbeg.p, send.p, L, ix->C,
-             ix->D, ix->pool);
+  PSI_LAUNCH(k_sort_overflow_leaves, warp_grid(ceil_div(L, 32)), 256, 0, s, ix->nodes.cnt, ix->nodes.ref, sbeg.p,
+             send.p, L, ix->C, ix->D, ix->pool);
 
   NodeArrays na;
   uint64_t *nsk = nullptr;
@@ -499,9 +565,15 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
     DevMem::free(nsi, s);
     return st;
   }
-  Buf<int32_t> owner;
-  if ((st = owner.alloc(Lnew, s))) return st;
-  PSI_LAUNCH(k_owner_scatter, grid_for(L), 256, 0, s, outl.p, pos.p, L, owner.p);
+  // a leaf re-wrapped into more than kOwnerInline leaves holds more than
+  // (kOwnerInline - 2) * phi of the batch's points (its block holds at most 2 phi)
+  const int64_t cap_big = m / ((kOwnerInline - 2) * (int64_t)ix->phi) + 1;
+  Buf<int32_t> owner, big;
+  Buf<uint32_t> n_big;
+  if ((st = owner.alloc(Lnew, s)) || (st = big.alloc(cap_big, s)) || (st = n_big.alloc(1, s))) return st;
+  PSI_CK(cudaMemsetAsync(n_big.p, 0, sizeof(uint32_t), s));
+  PSI_LAUNCH(k_owner_scatter, grid_for(L), 256, 0, s, outl.p, pos.p, L, owner.p, big.p, n_big.p, cap_big);
+  PSI_LAUNCH(k_owner_fill_big, num_sms() * 4, 256, 0, s, outl.p, pos.p, big.p, n_big.p, cap_big, owner.p);
   InsertArgs a;
   a.owner = owner.p;
   a.old = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
@@ -522,9 +594,9 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   a.C = ix->C;
   a.phi = ix->phi;
   if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_insert_apply", k_insert_apply<2>, warp_grid(Lnew), 256, 0, s, a);
+    PSI_LAUNCH_NAMED("k_insert_apply", k_insert_apply<2>, warp_grid(ceil_div(Lnew, 32)), 256, 0, s, a);
   else
-    PSI_LAUNCH_NAMED("k_insert_apply", k_insert_apply<3>, warp_grid(Lnew), 256, 0, s, a);
+    PSI_LAUNCH_NAMED("k_insert_apply", k_insert_apply<3>, warp_grid(ceil_div(Lnew, 32)), 256, 0, s, a);
   free_nodes(ix->nodes, s);
   DevMem::free(ix->sep_key, s);
   DevMem::free(ix->sep_id, s);
@@ -558,10 +630,10 @@ psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   PSI_LAUNCH(k_slices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p);
   Leaves lv = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
   if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<2>, warp_grid(L), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<2>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
                      b.keys, b.vals, pts, ids, del.p);
   else
-    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<3>, warp_grid(L), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<3>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
                      b.keys, b.vals, pts, ids, del.p);
   PSI_LAUNCH(k_nonempty, grid_for(L), 256, 0, s, ix->nodes.cnt, L, keep.p);
   if ((st = scan_i32_to_i64(keep.p, pos.p, L, tot.p, s))) return st;
