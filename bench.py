@@ -734,7 +734,7 @@ def run_config3(n=100_000_000, nq=10_000_000):
         oid = T(np.arange(n + n // 10, n + 2 * (n // 10), dtype=np.uint32))
         ddp, ddi = T(pts[dsel]), T(ids[dsel])
         b2, b4 = T(gen.centred_boxes(cen, h2, b3)), T(gen.centred_boxes(cen, h4, b3))
-        for kind in ("porth", "spac_z"):
+        for kind in ("porth", "spac_z", "spac_h"):
             r = {}
             t, _ = _timed(lambda: psi.Index(dp, di, kind=kind, leaf_size=32, coord_bits=b3).close())
             r["build_ms"] = round(t, 2)
@@ -763,13 +763,139 @@ def run_config3(n=100_000_000, nq=10_000_000):
             torch.cuda.synchronize()
             r["insert_ind_10pct_ms"] = round(e[0].elapsed_time(e[1]), 2)
             r["insert_ood_10pct_ms"] = round(e[1].elapsed_time(e[2]), 2)
-            r["delete_10pct_ms"] = round(e[2].elapsed_time(e[3]), 2)
+            r["delete_ind_10pct_ms"] = round(e[2].elapsed_time(e[3]), 2)
             t, _ = _timed(lambda: ix.knn(dq, 10))
             r["knn10_after_updates_Mq_s"] = round(nq / t / 1e3, 2)
+            e[0].record(s)
+            ix.delete(dood, oid)  # out-of-distribution delete: the batch inserted above
+            e[1].record(s)
+            torch.cuda.synchronize()
+            r["delete_ood_10pct_ms"] = round(e[0].elapsed_time(e[1]), 2)
             r["size_after"] = len(ix)
             ix.close()
             out[f"{dist}/{kind}"] = r
             print(json.dumps({f"{dist}/{kind}": r}), file=sys.stderr, flush=True)
+    return out
+
+
+def _event_ms(fn):
+    """Device time of one call (stream-ordered events around it)."""
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_config2(n=100_000_000):
+    """2D clustered n=1e8, SPaC-H, leaf 32: insert and delete batches of 1%, 10% and 100% of n, in-distribution
+    (same generator, same region) and out-of-distribution (new walkers in the other half of the x range), each
+    on a freshly built tree.  Delete in-distribution = a uniform sample of the base points; delete
+    out-of-distribution = the out-of-distribution batch inserted just before."""
+    import torch
+    from paper_2601_05347_gb300 import psi
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else a).cuda()
+    half = 1 << (BITS - 1)
+    base = gen.varden(n, 2, BITS, gen.config_seed(1, 0), x_range=(0, half))
+    dp, di = T(base), T(np.arange(n, dtype=np.uint32))
+    fresh = lambda: psi.Index(dp, di, kind="spac_h", leaf_size=32)
+    out = {}
+    for j, frac in enumerate((0.01, 0.1, 1.0)):
+        m = int(n * frac)
+        ind = T(gen.varden(m, 2, BITS, gen.config_seed(1, 10 + j), x_range=(0, half)))
+        ood = T(gen.varden(m, 2, BITS, gen.config_seed(1, 20 + j), x_range=(half, 1 << BITS)))
+        nid = T(np.arange(n, n + m, dtype=np.uint32))
+        sel = gen.sample_without_replacement(n, m, gen.config_seed(1, 30 + j))
+        dsel_p, dsel_i = T(base[sel]), T(sel.astype(np.uint32))
+        r = {}
+        for rep in range(2):  # the first round warms the memory pool; the second is reported
+            ix = fresh()
+            r["insert_ind_ms"] = _event_ms(lambda: ix.insert(ind, nid))
+            ix.close()
+            ix = fresh()
+            r["insert_ood_ms"] = _event_ms(lambda: ix.insert(ood, nid))
+            r["delete_ood_ms"] = _event_ms(lambda: ix.delete(ood, nid))
+            assert len(ix) == n
+            ix.close()
+            ix = fresh()
+            r["delete_ind_ms"] = _event_ms(lambda: ix.delete(dsel_p, dsel_i))
+            assert len(ix) == n - m
+            ix.close()
+        r = {k: round(v, 3) for k, v in r.items()}
+        for k in list(r):
+            r[k.replace("_ms", "_Mpts_s")] = round(m / r[k] / 1e3, 1)
+        out[f"{int(frac * 100)}pct"] = r
+        print(json.dumps({f"config2 {int(frac * 100)}pct": r}), file=sys.stderr, flush=True)
+        del ind, ood, nid, dsel_p, dsel_i
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_incremental(n=100_000_000, ratios=(0.1, 0.01, 0.001, 0.0001), nq=10_000_000):
+    """Incremental construction and destruction (Sec 5.1): the index is built by n/b batch inserts of
+    consecutive slices of the point array (b = ratio * n) starting from an empty index, then emptied by
+    n/b batch deletes in the same order; 10-NN queries at data points are timed after half of the batches.
+    Uniform, Sweepline (uniform sorted by x, so batches are spatially local strips) and Varden, 2D."""
+    import torch
+    from paper_2601_05347_gb300 import psi
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else a).cuda()
+    out = {}
+    empty_p = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    empty_i = torch.zeros(0, dtype=torch.int32, device="cuda")
+    for dist in ("uniform", "sweepline", "varden"):
+        seed = gen.config_seed(5, {"uniform": 0, "sweepline": 1, "varden": 2}[dist])
+        pts = {"uniform": gen.uniform, "sweepline": gen.sweepline, "varden": gen.varden}[dist](n, 2, BITS, seed)
+        dp, di = T(pts), T(np.arange(n, dtype=np.uint32))
+        dq = T(pts[gen.sample_with_replacement(n, nq, seed + 1)])
+        for kind in ("spac_h", "spac_z", "porth"):
+            for ratio in ratios:
+                key = f"{dist}/{kind}/{ratio * 100:g}pct"
+                if kind == "porth" and ratio < 0.01:
+                    out[key] = {"skipped": "P-Orth batch updates re-derive the whole tree (O(n) per batch)"}
+                    continue
+                b = max(1, int(n * ratio))
+                nb = (n + b - 1) // b
+                r = {"batches": nb}
+                s = torch.cuda.current_stream()
+                # insertion
+                ix = psi.Index(empty_p, empty_i, kind=kind, leaf_size=32)
+                ms = 0.0
+                for j in range(nb):
+                    if j == nb // 2:
+                        r["knn10_after_half_inserts_Mq_s"] = round(nq / _event_ms(lambda: ix.knn(dq, 10)) / 1e3, 2)
+                        r["leaves_after_half_inserts"] = ix.num_leaves
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    ix.insert(dp[j * b:(j + 1) * b], di[j * b:(j + 1) * b])
+                    e1.record(s)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                assert len(ix) == n
+                r["insert_total_ms"] = round(ms, 2)
+                r["insert_Mpts_s"] = round(n / ms / 1e3, 1)
+                # deletion, same order
+                ms = 0.0
+                for j in range(nb):
+                    if j == nb // 2:
+                        r["knn10_after_half_deletes_Mq_s"] = round(nq / _event_ms(lambda: ix.knn(dq, 10)) / 1e3, 2)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    ix.delete(dp[j * b:(j + 1) * b], di[j * b:(j + 1) * b])
+                    e1.record(s)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                assert len(ix) == 0
+                r["delete_total_ms"] = round(ms, 2)
+                r["delete_Mpts_s"] = round(n / ms / 1e3, 1)
+                ix.close()
+                out[key] = r
+                print(json.dumps({key: r}), file=sys.stderr, flush=True)
+        del dp, di, dq
+        torch.cuda.empty_cache()
     return out
 
 
@@ -875,7 +1001,10 @@ def main():
     ap.add_argument("--served-points", type=int, default=20_000_000)
     ap.add_argument("--served-requests", type=int, default=300)
     ap.add_argument("--serve", action="store_true", help="only the served configuration at 5e8 resident points")
-    ap.add_argument("--configs", action="store_true", help="the 2D uniform 1e6 and 3D 1e8 configurations")
+    ap.add_argument("--configs", action="store_true",
+                    help="the 2D uniform 1e6, 2D clustered update-batch and 3D 1e8 configurations")
+    ap.add_argument("--incremental", action="store_true",
+                    help="incremental construction/destruction by 10%%..0.01%% batches (Uniform, Sweepline, Varden)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -885,7 +1014,15 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         print(json.dumps({"metric": "other configurations", "config1_2d_uniform_1e6_spac_z": run_config1(),
+                          "config2_2d_varden_1e8_spac_h_updates": run_config2(),
                           "config3_3d_1e8": run_config3()}), flush=True)
+    elif args.incremental:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"metric": "incremental construction / destruction, 1e8 2D points",
+                          "incremental": run_incremental(args.n or 100_000_000)}), flush=True)
     elif args.serve:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

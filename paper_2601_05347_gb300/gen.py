@@ -15,6 +15,9 @@ Workload recipe (restated in the design doc):
     restarts at a new uniform position (probability ``p_restart``) or moves by a
     step drawn uniformly from [-step, step] per coordinate.  The walk is folded
     (reflected) into the region.
+  * Sweepline: the Uniform points ordered by their first coordinate (ties in
+    generation order), so that consecutive batches of an incremental workload
+    are spatially local strips (Sec 5.1).
   * Out-of-distribution batches for a clustered base live in the other half of
     the x range.
 """
@@ -55,6 +58,12 @@ def uniform(n: int, dim: int, bits: int, seed: int) -> np.ndarray:
     """n points with iid uniform int32 coordinates in [0, 2^bits)."""
     d = splitmix64(stream_seed(seed, 0), np.arange(n * dim, dtype=np.uint64))
     return (d >> np.uint64(64 - bits)).astype(np.int32).reshape(n, dim)
+
+
+def sweepline(n: int, dim: int, bits: int, seed: int) -> np.ndarray:
+    """The points of ``uniform(n, dim, bits, seed)`` sorted by first coordinate (stable)."""
+    p = uniform(n, dim, bits, seed)
+    return p[np.argsort(p[:, 0], kind="stable")]
 
 
 def varden(n: int, dim: int, bits: int, seed: int, clusters: int = 100, step: int | None = None,

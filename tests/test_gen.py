@@ -53,3 +53,15 @@ def test_boxes():
     b = gen.square_boxes(100, 2, 30, 1000, 1)
     assert (b[:, 2:] - b[:, :2] == 999).all()
     assert b.min() >= 0 and b.max() < (1 << 30)
+
+
+def test_sweepline_is_uniform_sorted_by_first_coordinate():
+    p = gen.sweepline(5000, 2, 30, 4)
+    u = gen.uniform(5000, 2, 30, 4)
+    assert (np.diff(p[:, 0].astype(np.int64)) >= 0).all()
+    # same multiset of points as the uniform draw
+    assert sorted(map(tuple, p.tolist())) == sorted(map(tuple, u.tolist()))
+    # consecutive tenths are disjoint strips in x
+    parts = np.array_split(p, 10)
+    for a, b in zip(parts, parts[1:]):
+        assert a[:, 0].max() <= b[:, 0].min()
