@@ -133,6 +133,7 @@ class Index:
             coord_bits = 30 if dim == 2 else 21
         self.dim, self.kind, self.leaf_size, self.coord_bits, self.fanout = dim, kind, leaf_size, coord_bits, fanout
         self.cfg = Config(dim, kind, leaf_size, coord_bits, fanout, radix_bits)
+        self._ids_per_box = 64.0  # running estimate that sizes range_report outputs
         h = ctypes.c_void_p()
         pts = pts.contiguous()
         ids = _u32(ids).contiguous()
@@ -206,11 +207,12 @@ class Index:
         return out
 
     def range_report(self, boxes: torch.Tensor, capacity: int | None = None, sort: bool = False, stream=None):
-        """(offsets[q+1], ids[total]); grows the output once if capacity is too small."""
+        """(offsets[q+1], ids[total]); grows the output once if capacity is too small.  Without a
+        capacity the output is sized from the ids per box of this index's earlier calls."""
         boxes = boxes.contiguous()
         nq = int(boxes.shape[0])
         off = torch.empty(nq + 1, dtype=torch.int64, device=boxes.device)
-        cap = capacity if capacity is not None else max(1024, 64 * nq)
+        cap = capacity if capacity is not None else max(1024, int(nq * self._ids_per_box * 1.25) + 1024)
         total = ctypes.c_int64(0)
         for _ in range(2):
             ids = torch.empty(max(cap, 1), dtype=torch.int32, device=boxes.device)
@@ -220,6 +222,8 @@ class Index:
                 cap = int(total.value)
                 continue
             _check(st)
+            if nq:
+                self._ids_per_box = max(1.0, 0.5 * self._ids_per_box + 0.5 * total.value / nq)
             return off, ids[:total.value]
         _check(st)
 

@@ -7,13 +7,16 @@ that has arrived and fits the device-memory budget, cuts the admitted sequence
 into epochs at the updates, and for each epoch
   * coalesces its queries -- all k-NN requests with the same k into one
     psi_knn call, all range counts into one call, all range lists into one
-    call -- and runs the groups concurrently on separate CUDA streams, with
-    their host-to-device copies on those streams;
+    call -- and launches the groups on the query stream(s), inputs copied from
+    pinned host memory on the same stream;
   * then applies the epoch's update on the main stream once the queries that
-    read the previous tree state are done.
+    read the previous tree state are done; consecutive inserts with no query
+    between them are applied as one batch.
 Requests that arrive while a round is on the GPU are admitted in the next
-round, as slots and memory free up.  Results are copied back on the query
-streams and each request's future is completed with its own slice.
+round, as slots and memory free up.  A finisher thread copies each group's
+results into pinned host memory on a copy stream and completes every
+request's future with its own slice (a numpy view of pinned memory, held until
+the caller drops it), so the worker never waits for results.
 
 The plain form (`serve_plain`) answers one request at a time in arrival order.
 """
@@ -33,13 +36,15 @@ KINDS = ("insert", "delete", "knn", "count", "report")
 
 
 class Request:
-    __slots__ = ("kind", "a", "b", "k", "arrival", "seq", "future", "done", "est_bytes")
+    __slots__ = ("kind", "a", "b", "k", "arrival", "seq", "future", "done", "est_bytes", "t_admit", "t_launch")
 
     def __init__(self, kind: str, a: np.ndarray, b: np.ndarray | None = None, k: int = 0):
         assert kind in KINDS
         self.kind, self.a, self.b, self.k = kind, a, b, k
         self.arrival = 0.0
         self.done = 0.0
+        self.t_admit = 0.0   # trace: taken by the worker
+        self.t_launch = 0.0  # trace: its work enqueued on the device
         self.seq = -1
         self.future = Future()
         n = len(a)
@@ -56,11 +61,23 @@ def _dev(a: np.ndarray, dev, stream) -> torch.Tensor:
         return torch.from_numpy(a).to(dev)
 
 
+def _warm_pinned(total: int):
+    """Puts pinned blocks of sizes 64 KiB, 128 KiB, ... (two of each, about
+    `total` bytes in all) into the host caching allocator, so that staging and
+    result copies later come from the cache rather than from fresh page-locked
+    allocations, which are slow and stall the device."""
+    keep, size = [], 1 << 16
+    while 4 * size <= total:
+        keep += [torch.empty(size, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        size <<= 1
+    del keep
+
+
 class Server:
     """Continuous-batching request loop around a psi.Index."""
 
     def __init__(self, index: "psi.Index", mem_budget: int | None = None, query_streams: int = 1,
-                 stage_bytes: int = 256 << 20):
+                 warm_pinned_bytes: int = 512 << 20):
         self.ix = index
         self.dev = torch.device("cuda", torch.cuda.current_device())
         free, _ = torch.cuda.mem_get_info(self.dev)
@@ -68,12 +85,7 @@ class Server:
         self.main = torch.cuda.Stream(self.dev)
         self.qs = [torch.cuda.Stream(self.dev) for _ in range(query_streams)]
         self.copy = torch.cuda.Stream(self.dev)  # result copies: updates never wait on them
-        # pinned staging: two input halves used alternately by the worker, one
-        # result buffer used by the finisher (larger payloads fall back to pageable copies)
-        self.stage_in = [torch.empty(stage_bytes // 2, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-        self.stage_in_ev = [None, None]
-        self.stage_turn = 0
-        self.stage_out = torch.empty(stage_bytes, dtype=torch.uint8, pin_memory=True)
+        _warm_pinned(warm_pinned_bytes)
         self.pending = collections.deque()
         self.lock = threading.Condition()
         self.seq = 0
@@ -115,9 +127,11 @@ class Server:
             while not self.pending and not self.stop_flag:
                 self.lock.wait()
             out, used = [], 0
+            now = time.perf_counter()
             while self.pending and used + self.pending[0].est_bytes <= self.budget:
                 r = self.pending.popleft()
                 used += r.est_bytes
+                r.t_admit = now
                 out.append(r)
             return out
 
@@ -128,53 +142,55 @@ class Server:
                 if self.stop_flag:
                     return
                 continue
-            epochs, cur = [], []
+            epochs, cur = [], []  # (queries, [updates]): one delete, or inserts applied together
             for r in batch:
                 if r.kind in ("insert", "delete"):
-                    epochs.append((cur, r))
+                    if (r.kind == "insert" and not cur and epochs and epochs[-1][1]
+                            and epochs[-1][1][0].kind == "insert"):
+                        epochs[-1][1].append(r)
+                    else:
+                        epochs.append((cur, [r]))
                     cur = []
                 else:
                     cur.append(r)
             epochs.append((cur, None))
             self.rounds.append((len(batch), len(epochs)))
             try:
-                for queries, update in epochs:
+                for queries, updates in epochs:
                     self._run_queries(queries)
-                    if update is not None:
-                        self._run_update(update)
+                    if updates:
+                        self._run_update(updates)
             except Exception as e:  # fail every request of the round, keep serving
                 for r in batch:
                     if not r.future.done():
                         r.future.set_exception(e)
 
     def _to_dev(self, a: np.ndarray, s) -> torch.Tensor:
-        """Host array -> device through a pinned staging half (async on s)."""
+        """Host array -> device: a pinned copy (host caching allocator), sent
+        asynchronously on stream s; the pinned block is not reused before that
+        copy is done."""
         a = np.ascontiguousarray(a)
         if a.dtype == np.uint32:
             a = a.view(np.int32)
-        half = self.stage_in[self.stage_turn]
-        if a.nbytes > half.numel():
-            return _dev(a, self.dev, s)
-        ev = self.stage_in_ev[self.stage_turn]
-        if ev is not None:
-            ev.synchronize()  # the previous copy out of this half is done
-        view = half[: a.nbytes]
-        view.numpy()[:] = a.reshape(-1).view(np.uint8)
+        h = torch.from_numpy(a).pin_memory()
         with torch.cuda.stream(s):
-            t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, device=self.dev)
-            t.view(-1).view(torch.uint8).copy_(view, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        self.stage_in_ev[self.stage_turn] = ev
-        self.stage_turn ^= 1
-        return t
+            return h.to(self.dev, non_blocking=True)
 
-    def _run_update(self, r: Request):
+    def _run_update(self, rs):
         s = self.main
         for q in self.qs:
             s.wait_stream(q)
-        pts = self._to_dev(r.a, s)
-        ids = self._to_dev(r.b, s)
+        r = rs[0]
+        if len(rs) > 1:  # consecutive inserts: one batch
+            a = np.concatenate([x.a for x in rs])
+            b = np.concatenate([x.b for x in rs])
+        else:
+            a, b = r.a, r.b
+        pts = self._to_dev(a, s)
+        ids = self._to_dev(b, s)
+        now = time.perf_counter()
+        for x in rs:
+            x.t_launch = now
         with torch.cuda.stream(s):
             if r.kind == "insert":
                 self.ix.insert(pts, ids, stream=s)
@@ -183,8 +199,10 @@ class Server:
                 nd = torch.zeros(1, dtype=torch.int64, device=self.dev)
                 self.ix.delete(pts, ids, nd, stream=s)
                 res = int(nd.item())
-        r.done = time.perf_counter()
-        r.future.set_result(res)
+        now = time.perf_counter()
+        for x in rs:
+            x.done = now
+            x.future.set_result(res)
 
     def _run_queries(self, reqs):
         if not reqs:
@@ -208,6 +226,9 @@ class Server:
                     out = self.ix.range_report(x, stream=s)
                 ev = torch.cuda.Event()
                 ev.record(s)
+            now = time.perf_counter()
+            for r in rs:
+                r.t_launch = now
             launched.append((kind, rs, offs, out, ev, x))
         # results are copied back and handed out by the finisher thread, so
         # the worker can launch the next epoch meanwhile
@@ -227,31 +248,27 @@ class Server:
 
     def _finish(self, launched):
         for kind, rs, offs, dout, ev, _keep in launched:
-            with torch.cuda.stream(self.copy):  # device-to-host reads after the group's kernels
-                self.copy.wait_event(ev)
-                total = sum(t.numel() * t.element_size() for t in dout)
-                if total <= self.stage_out.numel():
-                    outs, pos = [], 0
-                    for t in dout:
-                        nb = t.numel() * t.element_size()
-                        dst = self.stage_out[pos: pos + nb]
-                        dst.copy_(t.contiguous().view(-1).view(torch.uint8), non_blocking=True)
-                        outs.append((dst, t.dtype, t.shape))
-                        pos += nb
-                    self.copy.synchronize()
-                    out = tuple(torch.from_numpy(d.numpy().copy()).view(dt).reshape(sh) for d, dt, sh in outs)
-                else:
-                    out = tuple(t.cpu() for t in dout)
+            # device-to-host copies after the group's kernels, into pinned
+            # blocks of the host caching allocator; every request's result is
+            # a view of its slice (the block is reused once all views are gone)
+            self.copy.wait_event(ev)
+            with torch.cuda.stream(self.copy):
+                out = []
+                for t in dout:
+                    h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                    h.copy_(t, non_blocking=True)
+                    out.append(h.numpy())
+            self.copy.synchronize()
             now = time.perf_counter()
             for j, r in enumerate(rs):
                 a, b = offs[j], offs[j + 1]
                 if kind == "knn":
-                    res = (out[0][a:b].numpy().view(np.uint32), out[1][a:b].numpy())
+                    res = (out[0][a:b].view(np.uint32), out[1][a:b])
                 elif kind == "count":
-                    res = out[0][a:b].numpy()
+                    res = out[0][a:b]
                 else:
-                    off = out[0].numpy()
-                    res = (off[a:b + 1] - off[a], out[1][off[a]:off[b]].numpy().view(np.uint32))
+                    off = out[0]
+                    res = (off[a:b + 1] - off[a], out[1][off[a]:off[b]].view(np.uint32))
                 r.done = now
                 r.future.set_result(res)
 
@@ -276,6 +293,18 @@ def serve_plain(index: "psi.Index", req: Request):
         return index.range_count(x).cpu().numpy()
     off, rid = index.range_report(x)
     return off.cpu().numpy(), rid.cpu().numpy().view(np.uint32)
+
+
+def trace_breakdown(reqs, kind=None):
+    """Median milliseconds from arrival to admission, admission to launch, and
+    launch to completion (served requests only)."""
+    rs = [r for r in reqs if (kind is None or r.kind == kind) and r.t_admit > 0]
+    if not rs:
+        return None
+    med = lambda v: round(float(np.median(v)) * 1e3, 3)
+    return {"n": len(rs), "queue_ms": med([r.t_admit - r.arrival for r in rs]),
+            "admit_to_launch_ms": med([r.t_launch - r.t_admit for r in rs]),
+            "launch_to_done_ms": med([r.done - r.t_launch for r in rs])}
 
 
 def percentiles(reqs, kind=None):
