@@ -161,11 +161,28 @@ __device__ __forceinline__ void warp_sort_pairs(int64_t &d, uint32_t &i) {
   }
 }
 
+// Half-cleaners j = 16 .. 1 that sort a bitonic sequence of (d, i) pairs,
+// one per lane, ascending.
+__device__ __forceinline__ void warp_bitonic_clean(int64_t &d, uint32_t &i) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const int64_t od = __shfl_xor_sync(0xFFFFFFFFu, d, j);
+    const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, i, j);
+    const bool lower = (lane & j) == 0;
+    if (lower == pair_less(od, oi, d, i)) {
+      d = od;
+      i = oi;
+    }
+  }
+}
+
 // Scan one leaf: every point whose (d2, id) beats the current k-th enters the
-// list.  With a single register per lane (k <= 32) and many entrants -- the
-// first leaf of a query, when the list is still empty -- the entrants are
-// sorted across the warp and merged in one bitonic merge; otherwise they are
-// inserted one at a time.
+// list.  With many entrants (the seed leaves of a query, while the list is
+// still empty) the entrants are sorted across the warp and merged into the
+// list one 32-entry row at a time: a bitonic merge keeps the lower 32 of (row,
+// carry) in the row and carries the upper 32 on to the next row; otherwise
+// they are inserted one at a time.
 template <int D, int KPL>
 __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, const int32_t *qc, KList<KPL> &kl,
                                               int k) {
@@ -189,38 +206,49 @@ __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, 
     }
     const bool in = valid && kl.admits(d2, id);
     uint32_t m = __ballot_sync(0xFFFFFFFFu, in);
-    if (KPL == 1 && __popc(m) > 6) {
+    if (__popc(m) > 6) {
       int64_t cd = in ? d2 : INT64_MAX;
       uint32_t ci = in ? id : 0xFFFFFFFFu;
       warp_sort_pairs(cd, ci);
-      // reverse the sorted entrants against the sorted list: the lane-wise
-      // minimum is a bitonic sequence holding the 32 smallest of the union
-      const int64_t rd = __shfl_sync(0xFFFFFFFFu, cd, 31 - lane);
-      const uint32_t ri = __shfl_sync(0xFFFFFFFFu, ci, 31 - lane);
-      int64_t nd = kl.d[0];
-      uint32_t ni = kl.i[0];
-      if (pair_less(rd, ri, nd, ni)) {
-        nd = rd;
-        ni = ri;
-      }
 #pragma unroll
-      for (int j = 16; j > 0; j >>= 1) {
-        const int64_t od = __shfl_xor_sync(0xFFFFFFFFu, nd, j);
-        const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, ni, j);
-        const bool lower = (lane & j) == 0;
-        if (lower == pair_less(od, oi, nd, ni)) {
-          nd = od;
-          ni = oi;
+      for (int r = 0; r < KPL; ++r) {
+        if (__ballot_sync(0xFFFFFFFFu, cd != INT64_MAX) == 0) break;  // nothing left to place
+        // the row against the reversed carry: lane-wise minima are the 32
+        // smallest of both (a bitonic sequence), maxima the 32 largest
+        const int64_t rd = __shfl_sync(0xFFFFFFFFu, cd, 31 - lane);
+        const uint32_t ri = __shfl_sync(0xFFFFFFFFu, ci, 31 - lane);
+        int64_t lo_d = kl.d[r], hi_d = rd;
+        uint32_t lo_i = kl.i[r], hi_i = ri;
+        if (pair_less(rd, ri, lo_d, lo_i)) {
+          hi_d = lo_d;
+          hi_i = lo_i;
+          lo_d = rd;
+          lo_i = ri;
+        }
+        warp_bitonic_clean(lo_d, lo_i);
+        warp_bitonic_clean(hi_d, hi_i);
+        kl.d[r] = lo_d;
+        kl.i[r] = lo_i;
+        cd = hi_d;
+        ci = hi_i;
+      }
+      // entries past the k-th are dropped; the k-th bounds admission
+      const int rk = (k - 1) >> 5, lk = (k - 1) & 31;
+      int64_t vd = kl.d[0];
+      uint32_t vi = kl.i[0];
+#pragma unroll
+      for (int r = 0; r < KPL; ++r) {
+        if (r * 32 + lane >= k) {
+          kl.d[r] = INT64_MAX;
+          kl.i[r] = 0xFFFFFFFFu;
+        }
+        if (r == rk) {
+          vd = kl.d[r];
+          vi = kl.i[r];
         }
       }
-      if (lane >= k) {
-        nd = INT64_MAX;
-        ni = 0xFFFFFFFFu;
-      }
-      kl.d[0] = nd;
-      kl.i[0] = ni;
-      kl.kd = __shfl_sync(0xFFFFFFFFu, nd, k - 1);
-      kl.ki = __shfl_sync(0xFFFFFFFFu, ni, k - 1);
+      kl.kd = __shfl_sync(0xFFFFFFFFu, vd, lk);
+      kl.ki = __shfl_sync(0xFFFFFFFFu, vi, lk);
       continue;
     }
     while (m) {
