@@ -127,6 +127,9 @@ struct KnnSeed {
   const int64_t *node_off = nullptr;
   int phi = 0;
   const uint64_t *pkey = nullptr;
+  // P-Orth: the pool is key-sorted and contiguous, slots [0, n_slots); the seed
+  // is a slot range around the query's key
+  int64_t n_slots = 0;
 };
 
 // k-NN of nq queries, each starting at qroot[q] (or tv.root when qroot is

@@ -183,17 +183,17 @@ __device__ __forceinline__ void warp_bitonic_clean(int64_t &d, uint32_t &i) {
 // list one 32-entry row at a time: a bitonic merge keeps the lower 32 of (row,
 // carry) in the row and carries the upper 32 on to the next row; otherwise
 // they are inserted one at a time.
+// Slots [s0, s0 + cnt), except those in [skip_lo, skip_hi) (already scanned).
 template <int D, int KPL>
-__device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, const int32_t *qc, KList<KPL> &kl,
-                                              int k) {
+__device__ __forceinline__ void knn_scan_slots(const TreeView &t, uint32_t s0, int cnt, const int32_t *qc,
+                                               KList<KPL> &kl, int k, uint32_t skip_lo = 1, uint32_t skip_hi = 0) {
   const int lane = threadIdx.x & 31;
-  const uint32_t s0 = t.ref[node];
-  const int cnt = t.cnt[node];
   for (int b = 0; b < cnt; b += 32) {
     const int s = b + lane;
     int64_t d2 = INT64_MAX;
     uint32_t id = 0xFFFFFFFFu;
-    const bool valid = s < cnt;
+    const uint32_t sl = s0 + (uint32_t)s;
+    const bool valid = s < cnt && !(sl >= skip_lo && sl < skip_hi);
     if (valid) {
       const uint32_t slot = s0 + (uint32_t)s;
       id = t.pid[slot];
@@ -259,6 +259,12 @@ __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, 
       if (kl.admits(cd, ci)) kl.insert(cd, ci, k);
     }
   }
+}
+
+template <int D, int KPL>
+__device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, const int32_t *qc, KList<KPL> &kl,
+                                              int k, uint32_t skip_lo = 1, uint32_t skip_hi = 0) {
+  knn_scan_slots<D, KPL>(t, t.ref[node], t.cnt[node], qc, kl, k, skip_lo, skip_hi);
 }
 
 // Monotone non-decreasing 32-bit image of a non-negative distance (its float
@@ -329,29 +335,45 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
       lb = sd.node_off[sg];
       L = (sd.off[sg + 1] - sd.off[sg] + sd.phi - 1) / sd.phi;
     }
-    if (sd.qkey && root >= 0 && L > 0) {
+    // P-Orth (k > 32): the 32 * KPL points of the key-sorted pool around the
+    // query's key are scanned first, 32 at a time, and skipped point by point
+    // afterwards
+    const bool by_slots = sd.pkey && sd.n_slots > 0;
+    uint32_t sk_lo = 1, sk_hi = 0;
+    if (sd.qkey && root >= 0) {
       const uint64_t key = sd.qkey[qi] & sd.qkey_mask;
-      const int64_t j =
-          lb + (sd.sep_key ? seed_leaf([&](int64_t p) { return sd.sep_key[p]; }, L, key, sd.key_shift)
-                           : seed_leaf([&](int64_t p) { return sd.pkey[t.ref[lb + p]]; }, L, key, sd.key_shift));
-      const int64_t le = lb + L;
-      int64_t got = 0;
-      s_lo = j;
-      s_hi = j - 1;
-      while (got < a.k && (s_lo > lb || s_hi + 1 < le)) {
-        int64_t nx;
-        if (s_hi < s_lo || (s_hi + 1 < le && (s_lo == lb || s_hi - j <= j - s_lo)))
-          nx = ++s_hi;
-        else
-          nx = --s_lo;
-        knn_scan_leaf<D, KPL>(t, (uint32_t)nx, qc, kl, a.k);
-        got += t.cnt[nx];
-        if (STATS) {
-          ++n_leaf;
-          n_pts += t.cnt[nx];
+      if (by_slots) {
+        const int64_t pos = seed_leaf([&](int64_t p) { return sd.pkey[p]; }, sd.n_slots, key, sd.key_shift);
+        const int64_t want = min((int64_t)32 * KPL, sd.n_slots);
+        const int64_t lo = max((int64_t)0, min(pos - want / 2, sd.n_slots - want));
+        sk_lo = (uint32_t)lo;
+        sk_hi = (uint32_t)(lo + want);
+        knn_scan_slots<D, KPL>(t, sk_lo, (int)want, qc, kl, a.k);
+        if (STATS) n_pts += want;
+      } else if (L > 0) {
+        const int64_t j = lb + (sd.sep_key ? seed_leaf([&](int64_t p) { return sd.sep_key[p]; }, L, key, sd.key_shift)
+                                           : seed_leaf([&](int64_t p) { return sd.pkey[t.ref[lb + p]]; }, L, key,
+                                                       sd.key_shift));
+        const int64_t le = lb + L;
+        int64_t got = 0;
+        s_lo = j;
+        s_hi = j - 1;
+        while (got < a.k && (s_lo > lb || s_hi + 1 < le)) {
+          int64_t nx;
+          if (s_hi < s_lo || (s_hi + 1 < le && (s_lo == lb || s_hi - j <= j - s_lo)))
+            nx = ++s_hi;
+          else
+            nx = --s_lo;
+          knn_scan_leaf<D, KPL>(t, (uint32_t)nx, qc, kl, a.k);
+          got += t.cnt[nx];
+          if (STATS) {
+            ++n_leaf;
+            n_pts += t.cnt[nx];
+          }
         }
       }
     }
+    auto seeded = [&](uint32_t leaf) { return !by_slots && (int64_t)leaf >= s_lo && (int64_t)leaf <= s_hi; };
     uint32_t kdk = order_key(kl.kd);
     auto expand = [&](uint32_t node, int lvl) {
       const int nk = t.kids[node];
@@ -376,7 +398,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     };
     if (root >= 0) {
       if (t.kids[root] == 0) {
-        if (s_hi < s_lo) knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k);
+        if (!seeded((uint32_t)root)) knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k, sk_lo, sk_hi);
       } else {
         int lvl = 0;
         expand((uint32_t)root, 0);
@@ -396,8 +418,8 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
           if (lane == 0) s_mask[w][lvl] = m & ~(1u << src);
           __syncwarp();
           if (is_leaf) {
-            if ((int64_t)child >= s_lo && (int64_t)child <= s_hi) continue;  // scanned as a seed
-            knn_scan_leaf<D, KPL>(t, child, qc, kl, a.k);
+            if (seeded(child)) continue;  // scanned as a seed
+            knn_scan_leaf<D, KPL>(t, child, qc, kl, a.k, sk_lo, sk_hi);
             kdk = order_key(kl.kd);
             if (STATS) {
               ++n_leaf;
@@ -628,11 +650,19 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
   psi_status st = query_order(ix, q, nq, qo, s);
   if (st) return st;
   KnnSeed seed;
-  if (ix->cfg.kind != PSI_PORTH && qo.keys) {  // P-Orth leaves do not overlap: no seed needed
+  if (qo.keys) {
     seed.qkey = qo.keys;
-    seed.sep_key = ix->sep_key;
     seed.L = ix->L;
     seed.key_shift = qo.key_shift;
+    if (ix->cfg.kind == PSI_PORTH) {
+      // P-Orth leaves do not overlap and the search is near its floor; the
+      // seed pays off only in cutting single insertions into long lists
+      if (k <= 32) seed.qkey = nullptr;
+      seed.pkey = ix->pool.pkey;
+      seed.n_slots = ix->n;
+    } else {
+      seed.sep_key = ix->sep_key;
+    }
   }
   return run_knn_roots(ix->view(), q, nq, k, qo.order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s,
                        seed);
