@@ -378,6 +378,62 @@ __global__ void k_insert_apply(InsertArgs a) {
   }
 }
 
+// Insert that splits no leaf: every touched leaf appends its slice in place
+// (its block has room); untouched leaves are not visited.  A warp takes 32
+// leaves, one lane per leaf finds those with a slice.
+template <int D>
+__global__ void k_append_inplace(Leaves lv, Pool pool, const int32_t *sbeg, const int32_t *send, int64_t L,
+                                 const uint64_t *bkeys, const uint32_t *bvals, const int32_t *pts,
+                                 const uint32_t *ids) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < L; j0 += warps * 32) {
+    const int64_t jl = j0 + lane;
+    uint32_t todo = __ballot_sync(0xFFFFFFFFu, jl < L && send[jl] > sbeg[jl]);
+    while (todo) {
+      const int64_t j = j0 + __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t b = sbeg[j];
+      const int len = send[j] - (int)b;
+      const int cnt = lv.cnt[j];
+      const uint32_t s0 = lv.ref[j];
+      int32_t blo[D], bhi[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        blo[d] = INT32_MAX;
+        bhi[d] = INT32_MIN;
+      }
+      for (int t = lane; t < len; t += 32) {
+        const uint32_t v = bvals[b + t];
+        const uint32_t slot = s0 + (uint32_t)(cnt + t);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int32_t c = pts[(int64_t)v * D + d];
+          pool.px[d][slot] = c;
+          blo[d] = min(blo[d], c);
+          bhi[d] = max(bhi[d], c);
+        }
+        pool.pid[slot] = ids[v];
+        pool.pkey[slot] = bkeys[b + t];
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        blo[d] = __reduce_min_sync(0xFFFFFFFFu, blo[d]);
+        bhi[d] = __reduce_max_sync(0xFFFFFFFFu, bhi[d]);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          lv.lo[d][j] = min(lv.lo[d][j], blo[d]);
+          lv.hi[d][j] = max(lv.hi[d][j], bhi[d]);
+        }
+        lv.cnt[j] = cnt + len;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Remove the points named by each leaf's slice: a warp takes 32 leaves, one
 // lane per leaf finds those with a slice, then the warp compacts each of them.
 template <int D>
@@ -549,6 +605,20 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   PSI_CK(cudaStreamSynchronize(s));
   const int64_t Lnew = h[0], NB = h[1];
 
+  if (NB == 0) {  // no leaf overflows: append in place, the leaf list keeps its shape
+    Leaves lv = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
+    if (ix->D == 2)
+      PSI_LAUNCH_NAMED("k_append_inplace", k_append_inplace<2>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool,
+                       sbeg.p, send.p, L, b.keys, b.vals, pts, ids);
+    else
+      PSI_LAUNCH_NAMED("k_append_inplace", k_append_inplace<3>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool,
+                       sbeg.p, send.p, L, b.keys, b.vals, pts, ids);
+    ix->n += m;
+    if ((st = build_spac_summary(ix, s))) return st;
+    PSI_CK(cudaGetLastError());
+    return PSI_OK;
+  }
+
   const int64_t base_block = ix->pool_used;
   if ((st = grow_pool(ix, (base_block + NB) * ix->C, base_block * ix->C, s))) return st;
   PSI_LAUNCH(k_sort_overflow_leaves, warp_grid(ceil_div(L, 32)), 256, 0, s, ix->nodes.cnt, ix->nodes.ref, sbeg.p,
@@ -643,6 +713,12 @@ psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   PSI_CK(cudaMemcpyAsync(h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   PSI_CK(cudaStreamSynchronize(s));
   const int64_t Lnew = h[0];
+  if (Lnew == L) {  // no leaf emptied: the in-place edits above are the new leaves
+    ix->n -= h[1];
+    if ((st = build_spac_summary(ix, s))) return st;
+    PSI_CK(cudaGetLastError());
+    return PSI_OK;
+  }
   NodeArrays na;
   uint64_t *nsk = nullptr;
   uint32_t *nsi = nullptr;
