@@ -15,6 +15,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "psi_oracle.c")
+SRC_F = os.path.join(HERE, "psi_oracle_f.c")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 SPAC_Z, SPAC_H, PORTH = 0, 1, 2
@@ -24,10 +25,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (portable C11, no target-specific flags)."""
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     stale = not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "psi_oracle.h")))
+        os.path.getmtime(SRC), os.path.getmtime(SRC_F), os.path.getmtime(os.path.join(HERE, "psi_oracle.h")))
     if force or stale:
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", SRC, "-o", tmp])
+        # -ffp-contract=off: every float/double operation rounds on its own (no fused multiply-add)
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", SRC, SRC_F, "-lm",
+                               "-o", tmp])
         os.replace(tmp, LIB)
     return LIB
 
@@ -75,6 +78,14 @@ def lib():
         L.or_range_report.restype = i64
         L.or_range_report.argtypes = [P, P, i64, P, P, i64]
         L.or_knn_brute_raw.argtypes = [P, P, i64, ctypes.c_int, P, i64, ctypes.c_int, P, P]
+        L.or_forth_build.restype = P
+        L.or_forth_build.argtypes = [P, P, P, i64]
+        L.or_forth_free.argtypes = [P]
+        L.or_forth_num_nodes.restype = i64
+        L.or_forth_num_nodes.argtypes = [P]
+        L.or_forth_export.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.or_fknn_brute.argtypes = [P, P, i64, ctypes.c_int, P, i64, ctypes.c_int, P, P]
+        L.or_frange_count_brute.argtypes = [P, i64, ctypes.c_int, P, i64, P]
         L.or_range_count_brute_raw.argtypes = [P, i64, ctypes.c_int, P, i64, P]
         L.or_porth.restype = i64
         L.or_porth.argtypes = [P, i64, P, P, P, P, P, P]
@@ -228,3 +239,81 @@ class Index:
         if n:
             lib().or_porth(self._h, n, _ptr(depth), _ptr(prefix), _ptr(cnt), _ptr(lo), _ptr(hi), _ptr(leaf))
         return {"depth": depth, "prefix": prefix, "count": cnt, "lo": lo, "hi": hi, "is_leaf": leaf}
+
+
+# ---------------------------------------------------------------------------
+# SFC-free P-Orth over float coordinates (psi_oracle_f.c)
+# ---------------------------------------------------------------------------
+FMAXD = 8
+
+
+class _FCfg(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("phi", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("lo", ctypes.c_float * FMAXD), ("hi", ctypes.c_float * FMAXD)]
+
+
+def fcfg(dim, phi, lo, hi, max_depth=48):
+    c = _FCfg(dim, phi, max_depth)
+    for d in range(dim):
+        c.lo[d] = float(lo[d])
+        c.hi[d] = float(hi[d])
+    return c
+
+
+class FOrth:
+    """The float P-Orth of a point set: node arrays in breadth-first order."""
+
+    def __init__(self, pts, ids, lo, hi, phi=32, max_depth=48):
+        self.pts = _c(pts, np.float32)
+        self.dim = self.pts.shape[1]
+        self.ids = _c(ids, np.uint32)
+        cfg = fcfg(self.dim, phi, lo, hi, max_depth)
+        h = lib().or_forth_build(ctypes.byref(cfg), _ptr(self.pts), _ptr(self.ids), len(self.pts))
+        if not h:
+            raise ValueError("a point lies outside the region")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().or_forth_free(self._h)
+            self._h = None
+
+    def nodes(self):
+        n = int(lib().or_forth_num_nodes(self._h))
+        D = self.dim
+        out = {"depth": np.empty(n, np.int32), "count": np.empty(n, np.int64), "kids": np.empty(n, np.int32),
+               "is_leaf": np.empty(n, np.int32), "lo": np.empty((n, D), np.float32),
+               "hi": np.empty((n, D), np.float32), "leaf_first": np.empty(n, np.int64),
+               "leaf_ids": np.empty(max(len(self.pts), 1), np.uint32)}
+        if n:
+            lib().or_forth_export(self._h, _ptr(out["depth"]), _ptr(out["count"]), _ptr(out["kids"]),
+                                  _ptr(out["is_leaf"]), _ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["leaf_first"]),
+                                  _ptr(out["leaf_ids"]))
+        return out
+
+    def knn(self, q, k):
+        return fknn_brute(self.pts, self.ids, q, k)
+
+    def range_count(self, boxes):
+        return frange_count_brute(self.pts, boxes)
+
+
+def fknn_brute(pts, ids, q, k):
+    """k-NN by definition, float points, double squared distances."""
+    pts = _c(pts, np.float32)
+    dim = pts.shape[1]
+    ids = _c(ids, np.uint32)
+    q = _c(q, np.float32).reshape(-1, dim)
+    oi = np.empty((len(q), k), np.uint32)
+    od = np.empty((len(q), k), np.float64)
+    lib().or_fknn_brute(_ptr(pts), _ptr(ids), len(pts), dim, _ptr(q), len(q), k, _ptr(oi), _ptr(od))
+    return oi, od
+
+
+def frange_count_brute(pts, boxes):
+    pts = _c(pts, np.float32)
+    dim = pts.shape[1]
+    boxes = _c(boxes, np.float32).reshape(-1, 2 * dim)
+    out = np.empty(len(boxes), np.int64)
+    lib().or_frange_count_brute(_ptr(pts), len(pts), dim, _ptr(boxes), len(boxes), _ptr(out))
+    return out

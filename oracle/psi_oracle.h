@@ -78,6 +78,27 @@ void or_knn_brute_raw(const int32_t *pts, const uint32_t *ids, int64_t n, int di
 void or_range_count_brute_raw(const int32_t *pts, int64_t n, int dim, const int32_t *boxes, int64_t nq,
                               int64_t *counts);
 
+/* ---- SFC-free P-Orth over float coordinates (psi_oracle_f.c) ---------- */
+#define OR_FMAXD 8
+typedef struct {
+  int dim;       /* 2 .. OR_FMAXD */
+  int phi;       /* leaf bound */
+  int max_depth; /* a node at this depth is a leaf */
+  float lo[OR_FMAXD], hi[OR_FMAXD]; /* root region H = [lo, hi) */
+} or_fcfg;
+typedef struct or_forth or_forth;
+/* NULL if a point lies outside H. */
+or_forth *or_forth_build(const or_fcfg *cfg, const float *pts, const uint32_t *ids, int64_t n);
+void or_forth_free(or_forth *t);
+int64_t or_forth_num_nodes(const or_forth *t);
+/* Node arrays in breadth-first order; leaf_first[u] = offset of leaf u's ids
+ * (ascending) in leaf_ids, -1 for internal nodes; boxes are [node][dim]. */
+void or_forth_export(const or_forth *t, int32_t *depth, int64_t *count, int32_t *kids, int32_t *is_leaf, float *blo,
+                     float *bhi, int64_t *leaf_first, uint32_t *leaf_ids);
+void or_fknn_brute(const float *pts, const uint32_t *ids, int64_t n, int dim, const float *q, int64_t nq, int k,
+                   uint32_t *out_ids, double *out_d2);
+void or_frange_count_brute(const float *pts, int64_t n, int dim, const float *boxes, int64_t nq, int64_t *counts);
+
 #ifdef __cplusplus
 }
 #endif
