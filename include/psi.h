@@ -237,6 +237,54 @@ psi_status psi_knn_instrumented(const psi_index *ix, const int32_t *d_q, int64_t
 psi_status psi_batch_knn_instrumented(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq,
                                       int32_t k, uint32_t *d_ids, int64_t *d_d2, uint64_t *d_stats, void *stream);
 
+/* ---- P-Orth over float coordinates, without space-filling curves ------- */
+/*
+ * The P-Orth of Sec 3 / Algorithm 1 for float32 coordinates in D = 2..5
+ * dimensions, built by splitting regions at their midpoints (no Morton keys,
+ * so coordinates need not be integers).  The root region is H = [lo, hi)^D;
+ * the midpoint of [lo, hi) is lo + 0.5f * (hi - lo) in float arithmetic (each
+ * operation rounded to nearest) and a point takes the upper half of a
+ * dimension iff its coordinate >= the midpoint; child c takes the upper half of
+ * dimension d iff bit d of c is set; a child exists iff it holds a point; a
+ * node is a leaf iff it holds at most leaf_size points, is at depth max_depth,
+ * or some midpoint is not strictly inside its range (precision exhausted).
+ * Nodes are numbered breadth first (children consecutive in child order).
+ * k-NN distances are sum over d of (double(q_d) - double(p_d))^2 with every
+ * operation rounded to nearest, in dimension order; ties by id; k > size pads
+ * with id 0xFFFFFFFF and +inf.  Range boxes are closed ([q][2][D]: lo then hi).
+ * An insert or delete rebuilds the tree from the updated point set (the tree
+ * is a function of the set, Sec 3.2), synchronising the stream; builds
+ * synchronise once per tree level.  Points outside H: PSI_ERR_RANGE.
+ */
+typedef struct psi_forth psi_forth;
+typedef struct {
+  int32_t dim;       /* 2..5 */
+  int32_t leaf_size; /* 1..64 */
+  int32_t max_depth; /* 0..48 */
+  float lo[8], hi[8]; /* root region H, first dim entries used, lo < hi */
+} psi_fconfig;
+
+psi_status psi_forth_build(const psi_fconfig *cfg, const float *d_pts /*[n][dim]*/, const uint32_t *d_ids, int64_t n,
+                           void *stream, psi_forth **out);
+psi_status psi_forth_insert(psi_forth *ix, const float *d_pts, const uint32_t *d_ids, int64_t m, void *stream);
+/* Deletes the (coordinates, id) pairs present; *d_num_deleted (device) gets their number. */
+psi_status psi_forth_delete(psi_forth *ix, const float *d_pts, const uint32_t *d_ids, int64_t m,
+                            int64_t *d_num_deleted, void *stream);
+psi_status psi_forth_knn(const psi_forth *ix, const float *d_q /*[q][dim]*/, int64_t q, int32_t k,
+                         uint32_t *d_ids /*[q][k]*/, double *d_d2 /*[q][k]*/, void *stream);
+psi_status psi_forth_range_count(const psi_forth *ix, const float *d_boxes, int64_t q, int64_t *d_counts,
+                                 void *stream);
+int64_t psi_forth_size(const psi_forth *ix);
+int64_t psi_forth_num_nodes(const psi_forth *ix);
+/* Node arrays (depth, count, number of children, ref = first child or, for a
+ * leaf, first point slot; boxes [N][dim]) and the points in slot order
+ * ([n][dim], ids); any pointer may be null. */
+psi_status psi_forth_export(const psi_forth *ix, int32_t *d_depth, int32_t *d_count, int32_t *d_kids, uint32_t *d_ref,
+                            float *d_lo, float *d_hi, float *d_pts, uint32_t *d_ids, void *stream);
+/* Waits for `stream`; reports a device-detected error (traversal overflow). */
+psi_status psi_forth_sync(psi_forth *ix, void *stream);
+void psi_forth_destroy(psi_forth *ix);
+
 /* Number of kernels this library has launched in the process. */
 int64_t psi_launch_count(void);
 

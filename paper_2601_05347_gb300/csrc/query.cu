@@ -19,6 +19,7 @@
 #include "bitonic.cuh"
 #include "index.cuh"
 #include "keys.cuh"
+#include "klist.cuh"
 
 namespace psi {
 
@@ -62,10 +63,6 @@ __device__ __forceinline__ int box_relation(const TreeView &t, uint32_t node, co
   return disjoint ? 0 : (inside ? 2 : 1);
 }
 
-__device__ __forceinline__ bool pair_less(int64_t da, uint32_t ia, int64_t db, uint32_t ib) {
-  return da < db || (da == db && ia < ib);
-}
-
 struct KnnArgs {
   TreeView t;
   const int32_t *q;
@@ -79,110 +76,9 @@ struct KnnArgs {
   int *status;
 };
 
-template <int KPL>
-struct KList {
-  int64_t d[KPL];
-  uint32_t i[KPL];
-  int64_t kd;  // k-th entry (warp-uniform)
-  uint32_t ki;
-
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-      d[r] = INT64_MAX;
-      i[r] = 0xFFFFFFFFu;
-    }
-    kd = INT64_MAX;
-    ki = 0xFFFFFFFFu;
-  }
-  __device__ __forceinline__ bool admits(int64_t cd, uint32_t ci) const { return pair_less(cd, ci, kd, ki); }
-
-  // Insert a warp-uniform candidate into the sorted list of k entries.
-  __device__ __forceinline__ void insert(int64_t cd, uint32_t ci, int k) {
-    const int lane = threadIdx.x & 31;
-    int pos = 32 * KPL;
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, pair_less(cd, ci, d[r], i[r]));
-      if (m && pos == 32 * KPL) pos = r * 32 + __ffs(m) - 1;
-    }
-    if (pos >= k) return;
-#pragma unroll
-    for (int r = KPL - 1; r >= 0; --r) {
-      int64_t ud = __shfl_up_sync(0xFFFFFFFFu, d[r], 1);
-      uint32_t ui = __shfl_up_sync(0xFFFFFFFFu, i[r], 1);
-      if (r > 0) {
-        const int64_t cd2 = __shfl_sync(0xFFFFFFFFu, d[r > 0 ? r - 1 : 0], 31);
-        const uint32_t ci2 = __shfl_sync(0xFFFFFFFFu, i[r > 0 ? r - 1 : 0], 31);
-        if (lane == 0) {
-          ud = cd2;
-          ui = ci2;
-        }
-      }
-      const int e = r * 32 + lane;
-      if (e > pos) {
-        d[r] = ud;
-        i[r] = ui;
-      } else if (e == pos) {
-        d[r] = cd;
-        i[r] = ci;
-      }
-    }
-    const int rk = (k - 1) >> 5, lk = (k - 1) & 31;
-    int64_t vd = d[0];
-    uint32_t vi = i[0];
-#pragma unroll
-    for (int r = 1; r < KPL; ++r)
-      if (r == rk) {
-        vd = d[r];
-        vi = i[r];
-      }
-    kd = __shfl_sync(0xFFFFFFFFu, vd, lk);
-    ki = __shfl_sync(0xFFFFFFFFu, vi, lk);
-  }
-};
-
-// Ascending warp bitonic sort of (d, i) pairs, one per lane.
-__device__ __forceinline__ void warp_sort_pairs(int64_t &d, uint32_t &i) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int64_t od = __shfl_xor_sync(0xFFFFFFFFu, d, j);
-      const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, i, j);
-      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
-      const bool other_less = pair_less(od, oi, d, i);
-      if (keep_min == other_less) {
-        d = od;
-        i = oi;
-      }
-    }
-  }
-}
-
-// Half-cleaners j = 16 .. 1 that sort a bitonic sequence of (d, i) pairs,
-// one per lane, ascending.
-__device__ __forceinline__ void warp_bitonic_clean(int64_t &d, uint32_t &i) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 16; j > 0; j >>= 1) {
-    const int64_t od = __shfl_xor_sync(0xFFFFFFFFu, d, j);
-    const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, i, j);
-    const bool lower = (lane & j) == 0;
-    if (lower == pair_less(od, oi, d, i)) {
-      d = od;
-      i = oi;
-    }
-  }
-}
-
 // Scan one leaf: every point whose (d2, id) beats the current k-th enters the
-// list.  With many entrants (the seed leaves of a query, while the list is
-// still empty) the entrants are sorted across the warp and merged into the
-// list one 32-entry row at a time: a bitonic merge keeps the lower 32 of (row,
-// carry) in the row and carries the upper 32 on to the next row; otherwise
-// they are inserted one at a time.
+// list (klist_offer: in bulk when many enter at once, the seed leaves of a
+// query; one at a time otherwise).
 // Slots [s0, s0 + cnt), except those in [skip_lo, skip_hi) (already scanned).
 template <int D, int KPL>
 __device__ __forceinline__ void knn_scan_slots(const TreeView &t, uint32_t s0, int cnt, const int32_t *qc,
@@ -204,60 +100,7 @@ __device__ __forceinline__ void knn_scan_slots(const TreeView &t, uint32_t s0, i
         d2 += dd * dd;
       }
     }
-    const bool in = valid && kl.admits(d2, id);
-    uint32_t m = __ballot_sync(0xFFFFFFFFu, in);
-    if (__popc(m) > 6) {
-      int64_t cd = in ? d2 : INT64_MAX;
-      uint32_t ci = in ? id : 0xFFFFFFFFu;
-      warp_sort_pairs(cd, ci);
-#pragma unroll
-      for (int r = 0; r < KPL; ++r) {
-        if (__ballot_sync(0xFFFFFFFFu, cd != INT64_MAX) == 0) break;  // nothing left to place
-        // the row against the reversed carry: lane-wise minima are the 32
-        // smallest of both (a bitonic sequence), maxima the 32 largest
-        const int64_t rd = __shfl_sync(0xFFFFFFFFu, cd, 31 - lane);
-        const uint32_t ri = __shfl_sync(0xFFFFFFFFu, ci, 31 - lane);
-        int64_t lo_d = kl.d[r], hi_d = rd;
-        uint32_t lo_i = kl.i[r], hi_i = ri;
-        if (pair_less(rd, ri, lo_d, lo_i)) {
-          hi_d = lo_d;
-          hi_i = lo_i;
-          lo_d = rd;
-          lo_i = ri;
-        }
-        warp_bitonic_clean(lo_d, lo_i);
-        warp_bitonic_clean(hi_d, hi_i);
-        kl.d[r] = lo_d;
-        kl.i[r] = lo_i;
-        cd = hi_d;
-        ci = hi_i;
-      }
-      // entries past the k-th are dropped; the k-th bounds admission
-      const int rk = (k - 1) >> 5, lk = (k - 1) & 31;
-      int64_t vd = kl.d[0];
-      uint32_t vi = kl.i[0];
-#pragma unroll
-      for (int r = 0; r < KPL; ++r) {
-        if (r * 32 + lane >= k) {
-          kl.d[r] = INT64_MAX;
-          kl.i[r] = 0xFFFFFFFFu;
-        }
-        if (r == rk) {
-          vd = kl.d[r];
-          vi = kl.i[r];
-        }
-      }
-      kl.kd = __shfl_sync(0xFFFFFFFFu, vd, lk);
-      kl.ki = __shfl_sync(0xFFFFFFFFu, vi, lk);
-      continue;
-    }
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1;
-      const int64_t cd = __shfl_sync(0xFFFFFFFFu, d2, src);
-      const uint32_t ci = __shfl_sync(0xFFFFFFFFu, id, src);
-      if (kl.admits(cd, ci)) kl.insert(cd, ci, k);
-    }
+    klist_offer(kl, valid && kl.admits(d2, id), d2, id, k);
   }
 }
 

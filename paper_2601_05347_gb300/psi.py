@@ -79,6 +79,16 @@ def lib():
             "psi_batch_destroy": (st, [P]),
             "psi_batch_num_leaves": (i64, [P, i32]),
             "psi_batch_export_index": (st, [P, i32, P, P, P, P, P]),
+            "psi_forth_build": (st, [P, P, P, i64, P, P]),
+            "psi_forth_insert": (st, [P, P, P, i64, P]),
+            "psi_forth_delete": (st, [P, P, P, i64, P, P]),
+            "psi_forth_knn": (st, [P, P, i64, i32, P, P, P]),
+            "psi_forth_range_count": (st, [P, P, i64, P, P]),
+            "psi_forth_size": (i64, [P]),
+            "psi_forth_num_nodes": (i64, [P]),
+            "psi_forth_export": (st, [P, P, P, P, P, P, P, P, P, P]),
+            "psi_forth_sync": (st, [P, P]),
+            "psi_forth_destroy": (None, [P]),
             "psi_launch_count": (i64, []),
             "psi_profile_enable": (None, [ctypes.c_int]),
             "psi_profile_reset": (None, []),
@@ -343,6 +353,87 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class FConfig(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("lo", ctypes.c_float * 8), ("hi", ctypes.c_float * 8)]
+
+
+class FOrth:
+    """P-Orth over float32 coordinates in D = 2..5, built by midpoint splits of the region [lo, hi)^D."""
+
+    def __init__(self, pts: torch.Tensor, ids: torch.Tensor, lo, hi, *, leaf_size: int = 32, max_depth: int = 48,
+                 stream=None):
+        pts = pts.contiguous()
+        self.dim = int(pts.shape[1])
+        self.cfg = FConfig(self.dim, leaf_size, max_depth)
+        for d in range(self.dim):
+            self.cfg.lo[d] = float(lo[d])
+            self.cfg.hi[d] = float(hi[d])
+        h = ctypes.c_void_p()
+        ids = _u32(ids).contiguous()
+        _check(lib().psi_forth_build(ctypes.byref(self.cfg), _ptr(pts), _ptr(ids), int(pts.shape[0]),
+                                     _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psi_forth_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self) -> int:
+        return int(lib().psi_forth_size(self._h))
+
+    @property
+    def num_nodes(self) -> int:
+        return int(lib().psi_forth_num_nodes(self._h))
+
+    def sync(self, stream=None):
+        _check(lib().psi_forth_sync(self._h, _stream(stream)))
+
+    def insert(self, pts: torch.Tensor, ids: torch.Tensor, stream=None):
+        _check(lib().psi_forth_insert(self._h, _ptr(pts.contiguous()), _ptr(_u32(ids).contiguous()),
+                                      int(pts.shape[0]), _stream(stream)))
+
+    def delete(self, pts: torch.Tensor, ids: torch.Tensor, num_deleted: torch.Tensor | None = None, stream=None):
+        _check(lib().psi_forth_delete(self._h, _ptr(pts.contiguous()), _ptr(_u32(ids).contiguous()),
+                                      int(pts.shape[0]), _ptr(num_deleted), _stream(stream)))
+
+    def knn(self, q: torch.Tensor, k: int, stream=None):
+        q = q.contiguous()
+        nq = int(q.shape[0])
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        out_d2 = torch.empty((nq, k), dtype=torch.float64, device=q.device)
+        _check(lib().psi_forth_knn(self._h, _ptr(q), nq, k, _ptr(out_ids), _ptr(out_d2), _stream(stream)))
+        return out_ids, out_d2
+
+    def range_count(self, boxes: torch.Tensor, stream=None):
+        boxes = boxes.contiguous()
+        nq = int(boxes.shape[0])
+        out = torch.empty(nq, dtype=torch.int64, device=boxes.device)
+        _check(lib().psi_forth_range_count(self._h, _ptr(boxes), nq, _ptr(out), _stream(stream)))
+        return out
+
+    def nodes(self, stream=None):
+        N, n, D = self.num_nodes, len(self), self.dim
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {"depth": torch.empty(N, dtype=torch.int32, device=dev), "count": torch.empty(N, dtype=torch.int32, device=dev),
+               "kids": torch.empty(N, dtype=torch.int32, device=dev), "ref": torch.empty(N, dtype=torch.int32, device=dev),
+               "lo": torch.empty((N, D), dtype=torch.float32, device=dev),
+               "hi": torch.empty((N, D), dtype=torch.float32, device=dev),
+               "pts": torch.empty((n, D), dtype=torch.float32, device=dev),
+               "ids": torch.empty(n, dtype=torch.int32, device=dev)}
+        if N or n:
+            _check(lib().psi_forth_export(self._h, *(_ptr(out[k]) for k in ("depth", "count", "kids", "ref", "lo", "hi",
+                                                                              "pts", "ids")), _stream(stream)))
+        return out
 
 
 def encode(pts: torch.Tensor, kind: int | str = SPAC_Z, coord_bits: int | None = None, stream=None) -> torch.Tensor:
