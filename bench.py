@@ -927,6 +927,49 @@ def run_incremental(n=100_000_000, ratios=(0.1, 0.01, 0.001, 0.0001), nq=10_000_
     return out
 
 
+def run_forth(scale: float = 1.0):
+    """The P-Orth over float coordinates (no space-filling curve): 2D Varden 1e8 (the points of the 2D
+    clustered configuration scaled into [0, 1)^2), 3D uniform 1e8 and 5D uniform 2e7 in [0, 1)^D: build,
+    10-NN at data points, range counts of cubes holding about 1e3 points."""
+    import torch
+    from paper_2601_05347_gb300 import psi
+    out = {}
+    for name, dim, n, nq in (("2d_varden", 2, int(1e8 * scale), int(1e7 * scale)),
+                             ("3d_uniform", 3, int(1e8 * scale), int(1e7 * scale)),
+                             ("5d_uniform", 5, int(2e7 * scale), int(2e6 * scale))):
+        if name == "2d_varden":
+            P = (gen.varden(n, 2, BITS, gen.config_seed(1, 0), x_range=(0, 1 << (BITS - 1))).astype(np.float64)
+                 / float(1 << BITS)).astype(np.float32)
+        else:
+            P = (gen.uniform(n, dim, 24, gen.config_seed(6, dim)).astype(np.float64) / float(1 << 24)).astype(np.float32)
+        dp = torch.from_numpy(P).cuda()
+        di = torch.arange(n, dtype=torch.int32, device="cuda")
+        dq = torch.from_numpy(P[gen.sample_with_replacement(n, nq, gen.config_seed(6, 10 + dim))]).cuda()
+        side = (1e3 / n) ** (1.0 / dim)  # uniform: cubes of ~1e3 expected points
+        if name == "2d_varden":
+            side = float(gen.half_side_for_count((P * (1 << 24)).astype(np.int32), 1e3, gen.config_seed(6, 30))) / (1 << 24) * 2
+        cen = P[gen.sample_with_replacement(n, 50_000, gen.config_seed(6, 20 + dim))]
+        boxes = torch.from_numpy(np.concatenate([cen - side / 2, cen + side / 2], axis=1).astype(np.float32)).cuda()
+        lo, hi = [0.0] * dim, [1.0] * dim
+        psi.FOrth(dp, di, lo, hi).close()  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = psi.FOrth(dp, di, lo, hi, leaf_size=32)
+        torch.cuda.synchronize()
+        build_ms = (time.perf_counter() - t0) * 1e3
+        knn_ms, _ = _timed(lambda: ix.knn(dq, 10))
+        cnt_ms, c = _timed(lambda: ix.range_count(boxes))
+        out[name] = {"n": n, "build_ms": round(build_ms, 2), "build_Mpts_s": round(n / build_ms / 1e3, 1),
+                     "nodes": ix.num_nodes, "knn10_Mq_s": round(nq / knn_ms / 1e3, 2),
+                     "range_count_Mq_s": round(5e4 / cnt_ms / 1e3, 2),
+                     "mean_count": round(float(c.double().mean()), 1)}
+        print(json.dumps({f"forth {name}": out[name]}), file=sys.stderr, flush=True)
+        ix.close()
+        del dp, di, dq, boxes
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # oracle timings (the CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -1043,7 +1086,8 @@ def main():
         __graft_entry__.build()
         print(json.dumps({"metric": "other configurations", "config1_2d_uniform_1e6_spac_z": run_config1(),
                           "config2_2d_varden_1e8_spac_h_updates": run_config2(),
-                          "config3_3d_1e8": run_config3()}), flush=True)
+                          "config3_3d_1e8": run_config3(),
+                          "float_porth": run_forth()}), flush=True)
     elif args.incremental:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

@@ -545,21 +545,42 @@ FView fview(const psi_forth *ix) {
   return v;
 }
 
-// Squared distance of the query to a box (0 inside); each term is rounded as
-// the point distance is, so it never exceeds the distance of a point inside.
+// Lower bound of the squared distance from the query to a box (0 inside), in
+// float with every operation rounded toward -inf: it never exceeds the exact
+// box distance, hence never the exact distance of a point inside.  FP64
+// throughput is a small fraction of FP32 on this part, so only the distances
+// that are reported are computed in double.
 template <int D>
-__device__ __forceinline__ double fbox_mindist(const FView &t, uint32_t u, const float *qc) {
-  double s = 0.0;
+__device__ __forceinline__ float fbox_lower(const FView &t, uint32_t u, const float *qc) {
+  float s = 0.0f;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const float lo = t.lo[d][u], hi = t.hi[d][u], q = qc[d];
-    const double g = q < lo ? __dsub_rn((double)lo, (double)q) : (q > hi ? __dsub_rn((double)q, (double)hi) : 0.0);
-    s = __dadd_rn(s, __dmul_rn(g, g));
+    const float g = q < lo ? __fsub_rd(lo, q) : (q > hi ? __fsub_rd(q, hi) : 0.0f);
+    s = __fadd_rd(s, __fmul_rd(g, g));
   }
   return s;
 }
 
-__device__ __forceinline__ uint32_t forder_key(double md) { return __float_as_uint(__double2float_rn(md)); }
+// The reported squared distance: double, each operation rounded to nearest.
+template <int D>
+__device__ __forceinline__ double fpoint_d2(const float *qc, const float *const *px, uint32_t slot) {
+  double d2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double g = __dsub_rn((double)qc[d], (double)px[d][slot]);
+    d2 = __dadd_rn(d2, __dmul_rn(g, g));
+  }
+  return d2;
+}
+
+// Pruning key: the float bits of a non-negative distance (monotone).  A box or
+// point is skipped only when its key exceeds the k-th's by more than kSlack:
+// a float lower bound and a double value rounded to nearest of the same exact
+// distance lie within two float units of each other.
+__device__ __forceinline__ uint32_t fkey(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ uint32_t fkey(double x) { return __float_as_uint(__double2float_rn(x)); }
+constexpr uint32_t kSlack = 2;
 
 struct FKnnArgs {
   FView t;
@@ -588,23 +609,32 @@ __global__ __launch_bounds__(FQW * 32) void k_fknn(FKnnArgs a) {
     for (int d = 0; d < D; ++d) qc[d] = a.q[q * D + d];
     KList<KPL, double> kl;
     kl.init();
+    auto limit = [&]() { return kl.kd == DistInf<double>::v() ? 0xFFFFFFFEu : fkey(kl.kd) + kSlack; };
     auto scan = [&](uint32_t u) {
       const uint32_t s0 = t.ref[u];
       const int cnt = t.cnt[u];
       for (int b = 0; b < cnt; b += 32) {
         const int j = b + lane;
-        double d2 = DistInf<double>::v();
-        uint32_t id = 0xFFFFFFFFu;
+        // float lower bound first; the double distance only where it may enter
+        bool maybe = false;
         if (j < cnt) {
-          id = t.pid[s0 + j];
-          d2 = 0.0;
+          float lb = 0.0f;
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            const double g = __dsub_rn((double)qc[d], (double)t.px[d][s0 + j]);
-            d2 = __dadd_rn(d2, __dmul_rn(g, g));
+            const float x = t.px[d][s0 + j], qd = qc[d];
+            const float g = qd < x ? __fsub_rd(x, qd) : __fsub_rd(qd, x);
+            lb = __fadd_rd(lb, __fmul_rd(g, g));
           }
+          maybe = fkey(lb) <= limit();
         }
-        klist_offer(kl, j < cnt && kl.admits(d2, id), d2, id, a.k);
+        if (__ballot_sync(0xFFFFFFFFu, maybe) == 0) continue;
+        double d2 = DistInf<double>::v();
+        uint32_t id = 0xFFFFFFFFu;
+        if (maybe) {
+          id = t.pid[s0 + j];
+          d2 = fpoint_d2<D>(qc, t.px, s0 + j);
+        }
+        klist_offer(kl, maybe && kl.admits(d2, id), d2, id, a.k);
       }
     };
     auto expand = [&](uint32_t u, int lvl) {
@@ -613,11 +643,11 @@ __global__ __launch_bounds__(FQW * 32) void k_fknn(FKnnArgs a) {
       uint32_t key = 0xFFFFFFFFu;
       bool leafc = false;
       if (lane < nk) {
-        key = forder_key(fbox_mindist<D>(t, c0 + lane, qc));
+        key = fkey(fbox_lower<D>(t, c0 + lane, qc));
         leafc = t.kids[c0 + lane] == 0;
       }
       s_key[w][lvl][lane] = key;
-      const uint32_t mk = __ballot_sync(0xFFFFFFFFu, key <= forder_key(kl.kd));
+      const uint32_t mk = __ballot_sync(0xFFFFFFFFu, key <= limit());
       const uint32_t lf = __ballot_sync(0xFFFFFFFFu, leafc);
       if (lane == 0) {
         s_c0[w][lvl] = c0;
@@ -633,7 +663,7 @@ __global__ __launch_bounds__(FQW * 32) void k_fknn(FKnnArgs a) {
         int lvl = 0;
         expand(0, 0);
         while (lvl >= 0) {
-          const uint32_t kdk = forder_key(kl.kd);
+          const uint32_t kdk = limit();
           const uint32_t key = s_key[w][lvl][lane];
           const uint32_t m = s_mask[w][lvl] & __ballot_sync(0xFFFFFFFFu, key <= kdk);
           if (m == 0) {
