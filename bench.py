@@ -882,7 +882,7 @@ def run_incremental(n=100_000_000, ratios=(0.1, 0.01, 0.001, 0.0001), nq=10_000_
         for kind in ("spac_h", "spac_z", "porth"):
             for ratio in ratios:
                 key = f"{dist}/{kind}/{ratio * 100:g}pct"
-                if kind == "porth" and ratio < 0.01:
+                if kind == "porth" and ratio < 0.001:
                     out[key] = {"skipped": "P-Orth batch updates re-derive the whole tree (O(n) per batch)"}
                     continue
                 b = max(1, int(n * ratio))
