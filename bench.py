@@ -672,6 +672,8 @@ def run_served(n_base: int, R: int, rank: int = 0, upd=(1e3, 1e5), qry=(1e2, 1e5
         r1 = served_at_load(reqs, fresh, clone, util * capacity, rank)
         identical &= r1.pop("identical")
         out_loads[f"{util:.1f}x"] = r1
+        print(json.dumps({f"served {util:.1f}x": {"throughput": r1["throughput_req_per_s"], "all": r1["all"]}}),
+              file=sys.stderr, flush=True)
     return {"resident_points": n_base, "requests": R, "plain_capacity_req_per_s": round(capacity, 1),
             "loads": out_loads,
             "results_identical": identical}
@@ -1101,8 +1103,10 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         r = run_served(500_000_000, 1000, 0, upd=(1e3, 1e7), qry=(1e2, 1e6))
-        print(json.dumps({"metric": "served p50/p99 latency, 5e8 resident 2D points", "value": r["all"]["served"]["p99_ms"],
-                          "unit": "ms (p99, all requests)", "n_gpus": 1, "higher_is_better": False,
+        print(json.dumps({"metric": "served p50/p99 latency, 5e8 resident 2D points",
+                          "value": r["loads"]["1.0x"]["all"]["served"]["p99_ms"],
+                          "unit": "ms (p99, all requests, arrivals at the plain form's capacity)", "n_gpus": 1,
+                          "higher_is_better": False,
                           "config": {"workload": "served: SPaC-H, 5e8 Varden points, Poisson mixed stream"},
                           "served": r}), flush=True)
     elif args.batched:
