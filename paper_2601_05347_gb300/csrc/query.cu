@@ -1,15 +1,17 @@
 // query.cu -- batched k-NN, range count and range list (Sec 2.2) on either
-// tree layout (SPaC summary tree or P-Orth), one warp per query.
+// tree layout (SPaC summary tree or P-Orth), one warp per query, queries taken
+// in curve order so that neighbouring warps walk the same nodes out of L2.
 //
-// k-NN: depth-first traversal that visits children in increasing order of
+// k-NN: depth-first traversal that enters children in increasing order of
 // their box distance (Appendix "Implementation Details": subtrees are visited
 // in increasing minimum distance to the query) and prunes a subtree whose box
-// is farther than the current k-th best.  The k best (d2, id) pairs are kept
-// sorted across the warp: entry e = r*32 + lane lives in register r of lane
-// `lane`; a candidate is inserted by one ballot per register and one shuffle
-// shift.  Squared distances are exact int64 (|dx| < 2^31 for coordinates in
-// [0, 2^31)).  A node's children are evaluated one per lane and ordered with a
-// warp bitonic sort before they are pushed on the warp's shared-memory stack.
+// is farther than the current k-th best.  A node's children are evaluated one
+// per lane; each level of the current path keeps its children's distance keys
+// and a bitmask of those still to visit in shared memory, and a warp minimum
+// picks the next one.  The search starts from seed leaves at the query's own
+// curve position (SPaC; P-Orth for k > 32).  The k best (d2, id) pairs live in
+// a KList (klist.cuh).  Squared distances are exact int64 (|dx| < 2^31 for
+// coordinates in [0, 2^31)).
 //
 // Range count: children inside the box add their subtree count; children that
 // straddle the box are descended; straddling leaves are scanned.
