@@ -86,7 +86,7 @@ __global__ void k_porth_gather(const uint64_t *skeys, const uint32_t *svals, con
   }
 }
 
-constexpr int LT = 1024;  // positions per block in the leaf-depth kernel
+constexpr int LT = 256;  // positions per block in the leaf-depth kernel (8 blocks per SM overlap their loads)
 
 // Leaf depth of every point and leaf-start flags.
 __global__ __launch_bounds__(LT) void k_leaf_depth(const uint64_t *keys, int64_t n, int phi, int K, int D, int bits,
@@ -108,10 +108,32 @@ __global__ __launch_bounds__(LT) void k_leaf_depth(const uint64_t *keys, int64_t
     sm[t] = (int8_t)m;
   }
   __syncthreads();
+  // maximum over each window [t, t + phi] by doubling: after the round with
+  // step k every entry holds the maximum of the 2k entries from it (-1, "no
+  // pair", is neutral); the window is then two overlapping power-of-two spans
+  const int w = phi + 1;
+  int p2 = 1;
+  while (2 * p2 <= w) p2 *= 2;
+  for (int k = 1; k < p2; k *= 2) {
+    int8_t v[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int t = threadIdx.x + r * LT;
+      v[r] = -1;
+      if (t < LT + phi) v[r] = (int8_t)max((int)sm[t], t + k < LT + phi ? (int)sm[t + k] : -1);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int t = threadIdx.x + r * LT;
+      if (t < LT + phi) sm[t] = v[r];
+    }
+    __syncthreads();
+  }
   const int64_t i = base + threadIdx.x;
   if (i < n) {
-    int M = -1;
-    for (int t = threadIdx.x; t <= threadIdx.x + phi; ++t) M = max(M, (int)sm[t]);
+    const int t = threadIdx.x;
+    const int M = max((int)sm[t], (int)sm[t + w - p2]);
     ldepth[i] = min(M + 1, bits);
   }
 }
