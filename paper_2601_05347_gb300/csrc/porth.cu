@@ -267,42 +267,50 @@ __global__ void k_link(LinkArgs a) {
 }
 
 // Boxes of the nodes of one depth: leaves from their points, internal nodes
-// from their children (one warp per node).
+// from their children.
 template <int D>
 __global__ void k_boxes(NodeArrays nodes, Pool pool, int64_t off, int64_t cnt) {
-  const int lane = threadIdx.x & 31;
+  // an 8-lane group per node (at most 2^D <= 8 children; leaf points 8 at a
+  // time), four nodes per warp
+  const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
+  const unsigned gmask = 0xFFu << (g * 8);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = off + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); x < off + cnt; x += warps) {
+  for (int64_t x0 = off + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; x0 < off + cnt;
+       x0 += warps * 4) {
+    const int64_t x = x0 + g;
+    const bool valid = x < off + cnt;
     int32_t lo[D], hi[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       lo[d] = INT32_MAX;
       hi[d] = INT32_MIN;
     }
-    const int nk = nodes.kids[x];
-    const uint32_t r = nodes.ref[x];
-    if (nk == 0) {
-      const int c = nodes.cnt[x];
-      for (int s = lane; s < c; s += 32)
+    if (valid) {
+      const int nk = nodes.kids[x];
+      const uint32_t r = nodes.ref[x];
+      if (nk == 0) {
+        const int c = nodes.cnt[x];
+        for (int s = gl; s < c; s += 8)
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const int32_t v = pool.px[d][r + s];
+            lo[d] = min(lo[d], v);
+            hi[d] = max(hi[d], v);
+          }
+      } else if (gl < nk) {
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          const int32_t v = pool.px[d][r + s];
-          lo[d] = min(lo[d], v);
-          hi[d] = max(hi[d], v);
+          lo[d] = nodes.lo[d][r + gl];
+          hi[d] = nodes.hi[d][r + gl];
         }
-    } else if (lane < nk) {
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        lo[d] = nodes.lo[d][r + lane];
-        hi[d] = nodes.hi[d][r + lane];
       }
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      lo[d] = __reduce_min_sync(0xFFFFFFFFu, lo[d]);
-      hi[d] = __reduce_max_sync(0xFFFFFFFFu, hi[d]);
+      lo[d] = __reduce_min_sync(gmask, lo[d]);
+      hi[d] = __reduce_max_sync(gmask, hi[d]);
     }
-    if (lane == 0)
+    if (valid && gl == 0)
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         nodes.lo[d][x] = lo[d];
@@ -472,7 +480,7 @@ psi_status porth_derive(psi_index *ix, cudaStream_t s) {
   for (int l = maxd; l >= 0; --l) {
     const int64_t cnt = doff[l + 1] - doff[l];
     if (!cnt) continue;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cnt, 8), (int64_t)num_sms() * 32));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cnt, 32), (int64_t)num_sms() * 32));
     if (D == 2)
       PSI_LAUNCH_NAMED("k_boxes", k_boxes<2>, g, 256, 0, s, ix->nodes, ix->pool, doff[l], cnt);
     else
