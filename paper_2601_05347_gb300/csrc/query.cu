@@ -72,7 +72,8 @@ struct KnnArgs {
   int k;
   const uint32_t *order;
   const int32_t *qroot;  // per-query root (many indexes in one node array), or null
-  KnnSeed seed;  // SPaC: leaves scanned before the search
+  KnnSeed seed;        // SPaC: leaves scanned before the search
+  int64_t leaf_limit;  // >= 0: the leaves are exactly the nodes [0, leaf_limit) (one SPaC index)
   uint32_t *out_id;
   int64_t *out_d2;
   int *status;
@@ -226,9 +227,9 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
       const uint32_t c = c0 + (uint32_t)lane;
       uint32_t key = 0xFFFFFFFFu;
       bool leafc = false;
-      if (lane < nk && t.cnt[c] > 0) {
+      if (lane < nk) {  // every node of every layout holds a point
         key = order_key(box_mindist<D>(t, c, qc));
-        leafc = t.kids[c] == 0;
+        leafc = a.leaf_limit >= 0 ? (int64_t)c < a.leaf_limit : t.kids[c] == 0;
       }
       s_key[w][lvl][lane] = key;
       const uint32_t mk = __ballot_sync(0xFFFFFFFFu, key <= kdk);
@@ -459,9 +460,9 @@ psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, QueryO
 
 psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
                          const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status,
-                         unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed) {
+                         unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed, int64_t leaf_limit) {
   if (nq == 0) return PSI_OK;
-  KnnArgs a{tv, q, nq, k, order, qroot, seed, out_id, out_d2, status};
+  KnnArgs a{tv, q, nq, k, order, qroot, seed, leaf_limit, out_id, out_d2, status};
   KnnStats stats{d_stats};
   const int g = query_grid(nq);
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
@@ -510,7 +511,7 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
     }
   }
   return run_knn_roots(ix->view(), q, nq, k, qo.order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s,
-                       seed);
+                       seed, ix->cfg.kind == PSI_PORTH ? -1 : ix->L);
 }
 
 psi_status run_range_count(const psi_index *ix, const int32_t *boxes, int64_t nq, int64_t *counts, cudaStream_t s) {
