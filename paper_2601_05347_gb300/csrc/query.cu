@@ -40,15 +40,26 @@ constexpr int QW = 4;         // warps per block
 constexpr int STACK = 256;    // stack entries per warp (>= depth * fanout)
 constexpr uint32_t INSIDE = 0x80000000u;
 
+// Pruning key of a child box: the float bits of a lower bound of its squared
+// distance to the query, computed on the FP32 pipe (the ALU pipe is the
+// k-NN kernel's bottleneck): each gap is an exact int32 difference converted,
+// squared and summed with rounding toward -inf, so the bound never exceeds the
+// exact distance; a float at or below the exact k-th distance is at or below
+// that distance rounded to nearest, so comparing float bits never prunes a box
+// that holds a neighbour.
 template <int D>
-__device__ __forceinline__ int64_t box_mindist(const TreeView &t, uint32_t node, const int32_t *qc) {
-  int64_t s = 0;
+__device__ __forceinline__ uint32_t box_key(const TreeView &t, uint32_t node, const int32_t *qc) {
+  float s = 0.0f;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    const int64_t lo = t.lo[d][node], hi = t.hi[d][node], q = qc[d];
-    const int64_t dd = q < lo ? lo - q : (q > hi ? q - hi : 0);
-    s += dd * dd;
+    const int32_t lo = t.lo[d][node], hi = t.hi[d][node], q = qc[d];
+    const int32_t g = q < lo ? lo - q : (q > hi ? q - hi : 0);
+    const float gf = __int2float_rd(g);
+    s = __fadd_rd(s, __fmul_rd(gf, gf));
   }
+  return __float_as_uint(s);
+}
+
   return s;
 }
 
@@ -228,7 +239,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
       uint32_t key = 0xFFFFFFFFu;
       bool leafc = false;
       if (lane < nk) {  // every node of every layout holds a point
-        key = order_key(box_mindist<D>(t, c, qc));
+        key = box_key<D>(t, c, qc);
         leafc = a.leaf_limit >= 0 ? (int64_t)c < a.leaf_limit : t.kids[c] == 0;
       }
       s_key[w][lvl][lane] = key;
