@@ -60,9 +60,6 @@ __device__ __forceinline__ uint32_t box_key(const TreeView &t, uint32_t node, co
   return __float_as_uint(s);
 }
 
-  return s;
-}
-
 // 0: disjoint, 1: straddles, 2: node box inside the query box.
 template <int D>
 __device__ __forceinline__ int box_relation(const TreeView &t, uint32_t node, const int32_t *blo, const int32_t *bhi) {
