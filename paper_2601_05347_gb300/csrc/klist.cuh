@@ -28,6 +28,21 @@ __device__ __forceinline__ bool pair_less(T da, uint32_t ia, T db, uint32_t ib) 
   return da < db || (da == db && ia < ib);
 }
 
+// Non-negative int64 distances (INT64_MAX as +inf): the 96-bit number
+// (d, id) is compared by one subtraction with borrow through its three words.
+template <>
+__device__ __forceinline__ bool pair_less<int64_t>(int64_t da, uint32_t ia, int64_t db, uint32_t ib) {
+  uint32_t t, r;
+  asm("sub.cc.u32 %0, %2, %3;\n\t"
+      "subc.cc.u32 %0, %4, %5;\n\t"
+      "subc.cc.u32 %0, %6, %7;\n\t"
+      "subc.u32 %1, 0, 0;"
+      : "=&r"(t), "=r"(r)
+      : "r"(ia), "r"(ib), "r"((uint32_t)da), "r"((uint32_t)db), "r"((uint32_t)((uint64_t)da >> 32)),
+        "r"((uint32_t)((uint64_t)db >> 32)));
+  return r != 0;
+}
+
 template <int KPL, typename T = int64_t>
 struct KList {
   T d[KPL];
