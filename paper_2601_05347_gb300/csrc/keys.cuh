@@ -13,8 +13,8 @@
 // composes its own symmetry into the state: digit 0 exchanges the axes,
 // digit 3 exchanges and reverses them, digits 1 and 2 leave the state alone.
 // The four symmetries form a Klein four-group, so composition is XOR of the
-// two state bits.  Three levels are consumed per step through a 256-entry
-// table (state, 3 x-bits, 3 y-bits) -> (6 key bits, next state) that every
+// two state bits.  Four levels are consumed per step through a 1024-entry
+// table (state, 4 x-bits, 4 y-bits) -> (8 key bits, next state) that every
 // thread block derives from the automaton into shared memory.
 //
 // Hilbert keys (3D; the paper defines Hilbert keys in 2D only, so the 3D curve
@@ -81,30 +81,48 @@ __device__ __forceinline__ uint32_t hilbert_step(uint32_t &state, uint32_t rx, u
   return digit;
 }
 
-// Fills the 256-entry three-level table; call with all threads, then sync.
-__device__ __forceinline__ void hilbert_table_init(uint8_t *tab) {
-  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
-    uint32_t st = (uint32_t)e >> 6, xb = ((uint32_t)e >> 3) & 7u, yb = (uint32_t)e & 7u, d = 0;
-    for (int l = 2; l >= 0; --l) d = (d << 2) | hilbert_step(st, (xb >> l) & 1u, (yb >> l) & 1u);
-    tab[e] = (uint8_t)((d << 2) | st);
+// Fills the 1024-entry four-level table (state, 4 x-bits, 4 y-bits) ->
+// (8 key bits, next state << 8) as uint16; call with all threads, then sync.
+__device__ __forceinline__ void hilbert_table_init(uint8_t *tab8) {
+  uint16_t *tab = reinterpret_cast<uint16_t *>(tab8);
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    uint32_t st = (uint32_t)e >> 8, xb = ((uint32_t)e >> 4) & 15u, yb = (uint32_t)e & 15u, d = 0;
+    for (int l = 3; l >= 0; --l) d = (d << 2) | hilbert_step(st, (xb >> l) & 1u, (yb >> l) & 1u);
+    tab[e] = (uint16_t)(d | (st << 8));
   }
 }
 
-__device__ __forceinline__ uint64_t hilbert2_key(const uint8_t *tab, uint32_t x, uint32_t y, int bits) {
-  uint32_t st = 0;
-  uint64_t d = 0;
-  int l = bits - 1;
-  for (; l >= 0 && ((l + 1) % 3) != 0; --l) d = (d << 2) | hilbert_step(st, (x >> l) & 1u, (y >> l) & 1u);
-  for (; l >= 2; l -= 3) {
-    uint32_t e = tab[(st << 6) | (((x >> (l - 2)) & 7u) << 3) | ((y >> (l - 2)) & 7u)];
-    d = (d << 6) | (e >> 2);
-    st = e & 3u;
+// The key over `bits` levels, walked as a curve of 32 levels: the 32 - bits
+// levels above the point's own are quadrant 0 (digit 0), and each of them
+// exchanges the axes, so the walk is the same with x and y exchanged when
+// their number is odd.  Level l's digit lands on key bits 2l, 2l + 1; eight
+// fully unrolled steps of four levels.  Coordinate bits at and above `bits`
+// are ignored.
+__device__ __forceinline__ uint64_t hilbert2_key(const uint8_t *tab8, uint32_t x, uint32_t y, int bits) {
+  const uint16_t *tab = reinterpret_cast<const uint16_t *>(tab8);
+  const uint32_t m = (1u << bits) - 1u;  // bits <= 31
+  x &= m;
+  y &= m;
+  if ((32 - bits) & 1) {
+    const uint32_t t = x;
+    x = y;
+    y = t;
   }
-  return d;
+  uint32_t st = 0, khi = 0, klo = 0;  // st: state << 8
+#pragma unroll
+  for (int s = 28; s >= 0; s -= 4) {
+    const uint32_t e = tab[st | (((x >> s) & 15u) << 4) | ((y >> s) & 15u)];
+    if (s >= 16)
+      khi |= (e & 255u) << (2 * s - 32);
+    else
+      klo |= (e & 255u) << (2 * s);
+    st = e & 0x300u;
+  }
+  return ((uint64_t)khi << 32) | klo;
 }
 
 // Bytes of shared memory for the curve tables of either dimension.
-constexpr int kCurveTabBytes = 1536;
+constexpr int kCurveTabBytes = 2048;
 
 // The 3D automaton state: perm index (0..5) x 16 + reflections x 2 + parity;
 // permutations in lexicographic order (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0).

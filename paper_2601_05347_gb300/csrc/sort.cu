@@ -15,8 +15,13 @@
 //                     look-back table, bounded spin on predecessors, shared-
 //                     memory staging so that each digit's run is written out
 //                     contiguously.
-// The first digit pass of an encoding sort reads the points, not keys, so the
-// keys are never written before they are sorted.
+// An encoding sort computes Morton keys from the points in its first digit
+// pass, so they are never written before they are sorted; Hilbert keys, whose
+// arithmetic costs more than an 8-byte write and read, are computed once in
+// the histogram pass and written out.  Once a position (< n) and the key bits
+// not yet sorted fit 64 bits, the middle passes move them as one packed word
+// and the last pass writes (key, position) pairs again: Morton keys recomputed
+// from the point, Hilbert keys gathered from the written ones.
 // Equal keys (duplicate points) are then put in id order by k_tie_runs /
 // k_tie_long (a later canonical leaf layout depends on it).
 #include "common.cuh"
@@ -67,7 +72,7 @@ struct OnesweepSmem {
 
 struct PassArgs {
   const uint64_t *kin;
-  const uint32_t *vin;
+  const uint32_t *vin;  // null: the values are the input positions
   uint64_t *kout;
   uint32_t *vout;
   const int32_t *pts;
@@ -83,14 +88,32 @@ struct PassArgs {
   uint32_t *lookback_next;  // table of the next pass: this pass zeroes it (or null)
   uint32_t *tile_ctr;
   int *status;
+  // Packed words (IO_PACK .. IO_UNPACK below): value << kr | key >> drop.
+  const uint64_t *kfull = nullptr;  // keys in input order (IO_UNPACK gathers them), or null
+  uint64_t kmask = ~0ull;  // (1 << kr) - 1: the key bits of a packed word
+  int kr = 0;
+  int drop = 0;
 };
 
-// Digit histograms of all passes in one read.  With 8-bit digits the counts go
+// What a digit pass reads and writes.  An encoding sort whose positions
+// (values < n) and not yet sorted key bits fit one 64-bit word packs them
+// together for its middle passes, which then move 8 instead of 12 bytes per
+// pair; its last pass recomputes the full key from the point at the position.
+enum : int {
+  IO_PAIRS = 0,   // (key, value) in, (key, value) out
+  IO_PACK = 1,    // (key, value) in, packed word out
+  IO_KEYS = 2,    // packed word in and out
+  IO_UNPACK = 3,  // packed word in, (key from the point, value) out
+};
+
+// Digit histograms of all passes in one read; when encoding with kst set, the
+// keys are also written out (in input order) for the digit passes to read.  With 8-bit digits the counts go
 // to 4 shared copies (lane % 4 picks one) so that lanes of a warp hitting the
 // same digit -- common for the top digits of clustered input -- rarely collide.
 template <int MODE, int D, int CURVE, int RB>
 __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const int32_t *pts, int bits, int key_shift,
-                                                   int64_t n, int passes, uint32_t *hist, int *status) {
+                                                   int64_t n, int passes, uint32_t *hist, int *status,
+                                                   uint64_t *kst) {
   using R = Radix<RB>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][passes][RADIX]
@@ -114,6 +137,7 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
         bool bad;
         k = point_key<D, CURVE>(htab, c, bits, bad) >> key_shift;
         bad_any |= bad;
+        if (kst) kst[i] = k;
       }
       const uint32_t act = __activemask();
       for (int p = 0; p < passes; ++p) {
@@ -167,7 +191,7 @@ __global__ void k_hist_scan(const uint32_t *hist, uint32_t *gbase) {
   }
 }
 
-template <int MODE, int D, int CURVE, int RB>
+template <int MODE, int D, int CURVE, int RB, int IO = IO_PAIRS>
 __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
   using R = Radix<RB>;
   constexpr int RADIX = R::RADIX, DPT = R::DPT;
@@ -180,7 +204,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
     uint32_t *z = reinterpret_cast<uint32_t *>(&sm.wh[0][0]);
     for (int i = tid; i < (int)(sizeof(sm.wh) / 4); i += ST) z[i] = 0;
   }
-  if (MODE == 1) curve_table_init<D, CURVE>(sm.htab);
+  if (MODE == 1 || IO == IO_UNPACK) curve_table_init<D, CURVE>(sm.htab);
   if (a.hist_next)
     for (int i = tid; i < RADIX; i += ST) sm.nh[i] = 0;
   if (a.gbase) {
@@ -214,7 +238,12 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
   const int tile_n = (int)min((int64_t)TILE, a.n - base);
   const int wbase = w * (SI * 32);
 
-  if (MODE == 0) {  // the values are read after the keys are written: start them towards L2 now
+  // digit of a key (of the key bits of a packed word)
+  auto digit = [&](uint64_t k, int sh) -> uint32_t {
+    if (IO >= IO_KEYS) k &= a.kmask;
+    return (uint32_t)(k >> sh) & (RADIX - 1);
+  };
+  if (MODE == 0 && IO <= IO_PACK && a.vin) {  // the values are read after the keys are ranked: start them towards L2 now
     for (int i = tid * 32; i < tile_n; i += ST * 32)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a.vin + base + i));
   }
@@ -243,7 +272,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
   if (a.hist_next) {  // the next pass's digit of every key of the tile
 #pragma unroll
     for (int j = 0; j < SI; ++j)
-      if (wbase + j * 32 + lane < tile_n) atomicAdd(&sm.nh[(uint32_t)(key[j] >> a.shift_next) & (RADIX - 1)], 1u);
+      if (wbase + j * 32 + lane < tile_n) atomicAdd(&sm.nh[digit(key[j], a.shift_next)], 1u);
   }
   // Stable rank of each key among equal digits of its warp (items in
   // (item, lane) order = input order).
@@ -252,7 +281,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
   for (int j = 0; j < SI; ++j) {
     const int li = wbase + j * 32 + lane;
     const bool valid = li < tile_n;
-    const uint32_t dg = valid ? ((uint32_t)(key[j] >> a.shift) & (RADIX - 1)) : 0xFFFFFFFFu;
+    const uint32_t dg = valid ? digit(key[j], a.shift) : 0xFFFFFFFFu;
     // lanes holding the same digit, from one ballot per digit bit
     uint32_t peers = __ballot_sync(0xFFFFFFFFu, valid);
 #pragma unroll
@@ -347,40 +376,98 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
   }
   __syncthreads();
 
-  // Stage keys at their tile-local positions, then write each digit's run out.
+  // Stage keys (packed words) at their tile-local positions, then write each
+  // digit's run out.
 #pragma unroll
   for (int j = 0; j < SI; ++j) {
     const int li = wbase + j * 32 + lane;
     if (li < tile_n) {
-      const uint32_t dg = (uint32_t)(key[j] >> a.shift) & (RADIX - 1);
+      const uint32_t dg = digit(key[j], a.shift);
       const uint32_t lp = sm.off[dg] + sm.wh[w][dg] + rank[j];
-      sm.stage[lp] = key[j];
+      sm.stage[lp] = IO == IO_PACK ? key[j] >> a.drop : key[j];
+      if (IO == IO_PACK) sm.dig[lp] = (typename R::Digit)dg;
       rank[j] = lp;
     }
   }
-  __syncthreads();
+  if (IO == IO_PACK) {  // each pair's value joins its word (a position this thread staged)
 #pragma unroll
-  for (int i = 0; i < SI; ++i) {
-    const int p = tid + i * ST;
-    if (p < tile_n) {
-      const uint64_t k = sm.stage[p];
-      const uint32_t dg = (uint32_t)(k >> a.shift) & (RADIX - 1);
-      sm.dig[p] = (typename R::Digit)dg;
-      a.kout[sm.glob[dg] + p] = k;
+    for (int j = 0; j < SI; ++j) {
+      const int li = wbase + j * 32 + lane;
+      if (li < tile_n) sm.stage[rank[j]] |= (uint64_t)(MODE == 1 || !a.vin ? (uint32_t)(base + li) : a.vin[base + li])
+                                            << a.kr;
     }
   }
   __syncthreads();
-  uint32_t *s_v = reinterpret_cast<uint32_t *>(sm.stage);
+  if (IO == IO_UNPACK && a.kfull) {
+    // the stored key of every position is requested before the first is written
+    uint64_t kf[SI];
 #pragma unroll
-  for (int j = 0; j < SI; ++j) {
-    const int li = wbase + j * 32 + lane;
-    if (li < tile_n) s_v[rank[j]] = (MODE == 1) ? (uint32_t)(base + li) : a.vin[base + li];
+    for (int i = 0; i < SI; ++i) {
+      const int p = tid + i * ST;
+      if (p < tile_n) kf[i] = a.kfull[sm.stage[p] >> a.kr];
+    }
+#pragma unroll
+    for (int i = 0; i < SI; ++i) {
+      const int p = tid + i * ST;
+      if (p < tile_n) {
+        const uint64_t wd = sm.stage[p];
+        const uint64_t o = (uint64_t)sm.glob[digit(wd, a.shift)] + p;
+        a.kout[o] = kf[i];
+        a.vout[o] = (uint32_t)(wd >> a.kr);
+      }
+    }
+  } else if (IO == IO_UNPACK) {
+    // the points of half the positions are requested before their keys are computed
+#pragma unroll
+    for (int h = 0; h < SI; h += SI / 2) {
+      int32_t c[SI / 2][D];
+#pragma unroll
+      for (int i = 0; i < SI / 2; ++i) {
+        const int p = tid + (h + i) * ST;
+        if (p < tile_n) {
+          const int64_t v = (int64_t)(sm.stage[p] >> a.kr);
+#pragma unroll
+          for (int d = 0; d < D; ++d) c[i][d] = a.pts[v * D + d];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < SI / 2; ++i) {
+        const int p = tid + (h + i) * ST;
+        if (p < tile_n) {
+          const uint64_t wd = sm.stage[p];
+          const uint64_t o = (uint64_t)sm.glob[digit(wd, a.shift)] + p;
+          bool bad;
+          a.kout[o] = point_key<D, CURVE>(sm.htab, c[i], a.bits, bad) >> a.key_shift;
+          a.vout[o] = (uint32_t)(wd >> a.kr);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < SI; ++i) {
+      const int p = tid + i * ST;
+      if (p < tile_n) {
+        const uint64_t k = sm.stage[p];
+        const uint32_t dg = IO == IO_PACK ? (uint32_t)sm.dig[p] : digit(k, a.shift);
+        if (IO == IO_PAIRS) sm.dig[p] = (typename R::Digit)dg;
+        a.kout[sm.glob[dg] + p] = k;
+      }
+    }
   }
-  __syncthreads();
+  if (IO == IO_PAIRS) {
+    __syncthreads();
+    uint32_t *s_v = reinterpret_cast<uint32_t *>(sm.stage);
 #pragma unroll
-  for (int i = 0; i < SI; ++i) {
-    const int p = tid + i * ST;
-    if (p < tile_n) a.vout[sm.glob[sm.dig[p]] + p] = s_v[p];
+    for (int j = 0; j < SI; ++j) {
+      const int li = wbase + j * 32 + lane;
+      if (li < tile_n) s_v[rank[j]] = (MODE == 1 || !a.vin) ? (uint32_t)(base + li) : a.vin[base + li];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SI; ++i) {
+      const int p = tid + i * ST;
+      if (p < tile_n) a.vout[sm.glob[sm.dig[p]] + p] = s_v[p];
+    }
   }
   if (a.hist_next)
     for (int i = tid; i < RADIX; i += ST)
@@ -483,24 +570,38 @@ __global__ __launch_bounds__(1024) void k_tie_long(const uint64_t *keys, uint32_
 
 template <int MODE, int D, int CURVE, int RB>
 static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_t n, int passes, uint32_t *hist,
-                              int *status, cudaStream_t s) {
+                              int *status, cudaStream_t s, uint64_t *kst = nullptr) {
   using R = Radix<RB>;
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
   const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX + kCurveTabBytes;
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
   PSI_LAUNCH_NAMED("k_sort_hist", kern, std::max(grid, 1), 256, smem, s, kin, enc.pts, enc.bits, enc.key_shift, n,
-                   passes, hist, status);
+                   passes, hist, status, kst);
   return PSI_OK;
 }
 
-template <int MODE, int D, int CURVE, int RB>
+template <int MODE, int D, int CURVE, int RB, int IO = IO_PAIRS>
 static psi_status launch_pass(const PassArgs &a, int64_t tiles, cudaStream_t s) {
-  auto kern = k_onesweep<MODE, D, CURVE, RB>;
+  auto kern = k_onesweep<MODE, D, CURVE, RB, IO>;
   const size_t smem = sizeof(OnesweepSmem<RB>);
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   PSI_LAUNCH_NAMED("k_onesweep", kern, (unsigned)tiles, ST, smem, s, a);
   return PSI_OK;
+}
+
+// The passes of a packed sort (8-bit digits only).
+template <int RB>
+static psi_status launch_packed(const EncodeSpec &enc, const PassArgs &a, int64_t tiles, int io, cudaStream_t s) {
+  if constexpr (RB == 8) {
+    if (io == IO_PACK) return launch_pass<0, 2, 0, RB, IO_PACK>(a, tiles, s);
+    if (io == IO_KEYS) return launch_pass<0, 2, 0, RB, IO_KEYS>(a, tiles, s);
+    // the last pass: Morton keys are recomputed; stored (Hilbert) keys gathered
+    if (a.kfull || enc.dim == 2) return launch_pass<0, 2, 0, RB, IO_UNPACK>(a, tiles, s);
+    return launch_pass<0, 3, 0, RB, IO_UNPACK>(a, tiles, s);
+  }
+  set_error("sort: packed passes need 8-bit digits");
+  return PSI_ERR_INVALID;
 }
 
 // Digit width: 8 unless 10 or 11 is asked for.  Wider digits save passes but
@@ -529,25 +630,50 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   PSI_CK(cudaMemsetAsync(lookback.p, 0, sizeof(uint32_t) * tiles * R::RADIX, s));
   PSI_CK(cudaMemsetAsync(ctr.p, 0, sizeof(uint32_t) * passes, s));
 
+  // Hilbert keys cost more arithmetic than their 8-byte write and read: the
+  // histogram pass computes them once and writes them out; the first digit
+  // pass reads them (values = positions) and the last pass of a packed sort
+  // gathers them.  Morton keys are recomputed from the points where needed.
+  const bool stored = encode && enc.curve == CURVE_HILBERT;
+  Buf<uint64_t> kst;
+  if (stored && (st = kst.alloc(n, s))) return st;
+
   // digit 0 is counted up front; every pass counts the next digit of its keys
   if (!encode)
     st = launch_hist<0, 2, 0, RB>(keys_in, enc, n, 1, hist.p, d_status, s);
   else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
     st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
   else if (enc.dim == 2)
-    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
+    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p);
   else if (enc.curve == CURVE_MORTON)
     st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
   else
-    st = launch_hist<1, 3, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
+    st = launch_hist<1, 3, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p);
   if (st) return st;
 
+  // Packed middle passes (8-bit digits, encoding sorts): pass pk writes
+  // value << kr | key >> drop once the value (a position < n) and the key bits
+  // not yet sorted fit 64 bits; passes pk+1 .. passes-2 move those words alone;
+  // the last pass writes the pairs again.  Worth it with one middle pass or more.
+  int pk = passes;
+  int kr = 0, drop = 0;
+  if (encode && RB == 8) {
+    const int vbits = n > 1 ? 64 - __builtin_clzll((uint64_t)(n - 1)) : 1;
+    int p = 1;
+    while (p < passes && vbits + key_bits - RB * (p + 1) > 64) ++p;
+    if (p + 2 <= passes - 1) {
+      pk = p;
+      drop = RB * (pk + 1);
+      kr = key_bits - drop;
+    }
+  }
   uint64_t *kb[2] = {kbuf0, kbuf1};
   uint32_t *vb[2] = {vbuf0, vbuf1};
   for (int p = 0; p < passes; ++p) {
     PassArgs a;
-    a.kin = p == 0 ? keys_in : kb[(p - 1) & 1];
+    a.kin = p == 0 ? (stored ? kst.p : keys_in) : kb[(p - 1) & 1];
     a.vin = p == 0 ? vals_in : vb[(p - 1) & 1];
+    a.kfull = stored ? kst.p : nullptr;
     a.kout = kb[p & 1];
     a.vout = vb[p & 1];
     a.pts = enc.pts;
@@ -563,16 +689,21 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     a.lookback_next = p + 1 < passes ? lookback.p + (size_t)((p + 1) & 1) * tiles * R::RADIX : nullptr;
     a.tile_ctr = ctr.p + p;
     a.status = d_status;
-    if (p > 0 || !encode)
+    if (p > pk) {
+      a.shift = p * RB - drop;
+      a.shift_next = (p + 1) * RB - drop;
+      a.kmask = (1ull << kr) - 1;
+    }
+    a.kr = kr;
+    a.drop = drop;
+    if (p >= pk)
+      st = launch_packed<RB>(enc, a, tiles, p == pk ? IO_PACK : (p + 1 < passes ? IO_KEYS : IO_UNPACK), s);
+    else if (p > 0 || !encode || stored)
       st = launch_pass<0, 2, 0, RB>(a, tiles, s);
-    else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
+    else if (enc.dim == 2)  // Morton keys computed from the points
       st = launch_pass<1, 2, 0, RB>(a, tiles, s);
-    else if (enc.dim == 2)
-      st = launch_pass<1, 2, 1, RB>(a, tiles, s);
-    else if (enc.curve == CURVE_MORTON)
-      st = launch_pass<1, 3, 0, RB>(a, tiles, s);
     else
-      st = launch_pass<1, 3, 1, RB>(a, tiles, s);
+      st = launch_pass<1, 3, 0, RB>(a, tiles, s);
     if (st) return st;
   }
   out->keys = kb[(passes - 1) & 1];

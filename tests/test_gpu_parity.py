@@ -147,6 +147,21 @@ def test_every_digit_width_gives_the_same_index(radix, kind, dim, bits):
     assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
 
 
+@pytest.mark.parametrize("kind,dim,bits,n", [("spac_h", 2, 30, (1 << 20) + 3), ("spac_z", 2, 30, 1 << 20),
+                                              ("spac_h", 3, 21, (1 << 20) + 5), ("porth", 3, 21, (1 << 20) + 1)])
+def test_build_across_the_packed_sort_thresholds(kind, dim, bits, n):
+    # an encoding sort packs (position, unsorted key bits) into one word from the
+    # first pass after which they fit 64 bits: pass 1 up to 2^20 points, pass 2
+    # (2D) or 3 (3D) beyond; its last pass recomputes the keys from the points
+    p, ids = points(n, dim, bits, 71 + n % 97, clustered=n % 2 == 1)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
+    if kind == "porth":
+        check_porth_nodes(ix, o)
+    else:
+        check_spac_layout(ix, o)
+
+
 @pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
 @pytest.mark.parametrize("dup", [False, True])
 def test_spac_build_layout_3d_and_duplicates(kind, dup):
