@@ -136,24 +136,51 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # per-kernel algorithmic byte model (2D, per launch)
 # ---------------------------------------------------------------------------
+def sort_bytes(items: int, key_bits: int, stored: bool, dim: int = 2) -> tuple[float, float]:
+    """Algorithmic HBM bytes of one encoding key sort (8-bit digits): (histogram
+    pass, all digit passes).  Mirrors the library's plan: Hilbert keys are
+    computed once in the histogram pass and written (stored); once a position
+    and the unsorted key bits fit 64 bits, pass pk packs them into one word, the
+    middle passes move 8-B words and the last pass writes the pairs again."""
+    pt = 4 * dim
+    passes = (key_bits + 7) // 8
+    vbits = max(1, (items - 1).bit_length())
+    p = 1
+    while p < passes and vbits + key_bits - 8 * (p + 1) > 64:
+        p += 1
+    pk = p if p + 2 <= passes - 1 else passes
+    hist = pt + (8 if stored else 0)
+    per = 0
+    for q in range(passes):
+        if q == 0:
+            per += (8 if stored else pt) + 12  # key (or point) read; key + value written
+        elif q < pk:
+            per += 24  # (key, value) read and written
+        elif q == pk:
+            per += 12 + 8  # pairs read, words written
+        elif q < passes - 1:
+            per += 16  # words read and written
+        else:
+            per += 8 + (8 if stored else pt) + 12  # word read, key (or point) gathered, pair written
+    return float(hist * items), float(per * items)
+
+
 def kernel_bytes(name: str, w, launches: int) -> float | None:
     """Algorithmic HBM bytes of all launches of a kernel in one step.
 
-    k_onesweep   one digit pass over (key 8 B, value 4 B): read + write 24 B per
-                 pair; the first pass of an encoding sort reads the 8-B point
-                 instead of the key and value (20 B).
-    k_sort_hist  reads each key (or 8-B point) once: 8 B per item.
+    k_onesweep, k_sort_hist  the encoding key sorts of the step (`sort_bytes`):
+                 build, insert batch, delete batch (60-bit Hilbert keys) and the
+                 query order (top 48 key bits).
     k_leaf_gather reads sorted key + position (12 B) and gathers point + id
                  (12 B), writes x, y, id, key (20 B): 44 B per point.
     """
     n, mi, md = w["n"], w["m_ins"], w["m_del"]
+    sorts = [sort_bytes(n, 60, True), sort_bytes(mi, 60, True), sort_bytes(md, 60, True),
+             sort_bytes(w["n_knn"], 48, True)]
     if name == "k_onesweep":
-        # sorts per step at 8-bit digits: build, insert batch, delete batch (60-bit keys, 8 passes)
-        # and the query order (top 48 key bits, 6 passes); the first pass of each reads points
-        sorts = [(n, 8), (mi, 8), (md, 8), (w["n_knn"], 6)]
-        return float(sum(items * (20 + (passes - 1) * 24) for items, passes in sorts))
+        return sum(b for _, b in sorts)
     if name == "k_sort_hist":
-        return float(8 * (n + mi + md + w["n_knn"]))
+        return sum(h for h, _ in sorts)
     if name == "k_leaf_gather":
         return float(44 * n)
     return None

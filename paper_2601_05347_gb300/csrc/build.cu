@@ -97,36 +97,39 @@ NodeW node_w(const NodeArrays &a) {
 // One warp per group of GL consecutive leaves: gather each leaf's points by
 // their sorted positions into its block (structure of arrays), reduce the
 // boxes, write the leaf nodes and their separators (the first (key, id) of
-// each leaf).  All sorted positions of the group are loaded first, then all
+// each leaf; lane u writes leaf u's).  All sorted positions of the group are loaded first, then all
 // gathers are issued, so a warp keeps GL x 3 independent loads in flight
 // instead of waiting on each leaf's dependent position -> point chain.
 constexpr int GL = 4;
 
 template <int D>
-__global__ void k_leaf_gather(const uint64_t *skeys, const uint32_t *svals, const int32_t *pts, const uint32_t *ids,
-                              int64_t n, int phi, int C, PoolW pool, NodeW nodes, uint64_t *sep_key,
-                              uint32_t *sep_id, int64_t L) {
+__global__ __launch_bounds__(256, 3) void k_leaf_gather(const uint64_t *skeys, const uint32_t *svals, const int32_t *pts,
+                                                     const uint32_t *ids, int64_t n, int phi, int C, PoolW pool,
+                                                     NodeW nodes, uint64_t *sep_key, uint32_t *sep_id, int64_t L) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * GL < L; g += warps) {
+    const int64_t leaf0 = g * GL;
     for (int s0 = 0; s0 < phi; s0 += 32) {  // phi <= 64: at most two rounds
-      uint32_t v[GL];
+      const int s = s0 + lane;
+      uint32_t v[GL], id[GL], okm = 0;
       uint64_t k[GL];
       int32_t c[GL][D];
-      uint32_t id[GL];
-      bool ok[GL];
 #pragma unroll
       for (int u = 0; u < GL; ++u) {
-        const int64_t leaf = g * GL + u;
-        const int64_t b = leaf * phi;
-        const int s = s0 + lane;
-        ok[u] = leaf < L && s < phi && b + s < n;
-        v[u] = ok[u] ? svals[b + s] : 0u;
-        k[u] = ok[u] ? skeys[b + s] : 0ull;
+        const int64_t i = (leaf0 + u) * phi + s;
+        v[u] = 0u;
+        k[u] = 0ull;
+        id[u] = 0u;
+        if (leaf0 + u < L && s < phi && i < n) {
+          okm |= 1u << u;
+          v[u] = svals[i];
+          k[u] = skeys[i];
+        }
       }
 #pragma unroll
       for (int u = 0; u < GL; ++u) {
-        if (ok[u]) {
+        if (okm >> u & 1u) {
 #pragma unroll
           for (int d = 0; d < D; ++d) c[u][d] = pts[(int64_t)v[u] * D + d];
           id[u] = ids[v[u]];
@@ -134,47 +137,57 @@ __global__ void k_leaf_gather(const uint64_t *skeys, const uint32_t *svals, cons
       }
 #pragma unroll
       for (int u = 0; u < GL; ++u) {
-        if (!ok[u]) continue;
-        const int64_t leaf = g * GL + u;
-        const int64_t slot = leaf * C + s0 + lane;
+        if (okm >> u & 1u) {
+          const int64_t slot = (leaf0 + u) * C + s;
 #pragma unroll
-        for (int d = 0; d < D; ++d) pool.px[d][slot] = c[u][d];
-        pool.pid[slot] = id[u];
-        pool.pkey[slot] = k[u];
+          for (int d = 0; d < D; ++d) pool.px[d][slot] = c[u][d];
+          pool.pid[slot] = id[u];
+          pool.pkey[slot] = k[u];
+        }
       }
+      // each leaf's box and first (key, id), kept by lane u for leaf u
+      int32_t mlo[D], mhi[D];
+      uint64_t mk = 0;
+      uint32_t mid = 0;
 #pragma unroll
       for (int u = 0; u < GL; ++u) {
-        const int64_t leaf = g * GL + u;
-        if (leaf >= L) break;
-        const int64_t b = leaf * phi;
-        const int cnt = (int)min((int64_t)phi, n - b);
-        int32_t lo[D], hi[D];
+        const bool ok = okm >> u & 1u;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          lo[d] = ok[u] ? c[u][d] : INT32_MAX;
-          hi[d] = ok[u] ? c[u][d] : INT32_MIN;
-          lo[d] = __reduce_min_sync(0xFFFFFFFFu, lo[d]);
-          hi[d] = __reduce_max_sync(0xFFFFFFFFu, hi[d]);
+          const int32_t lo = __reduce_min_sync(0xFFFFFFFFu, ok ? c[u][d] : INT32_MAX);
+          const int32_t hi = __reduce_max_sync(0xFFFFFFFFu, ok ? c[u][d] : INT32_MIN);
+          if (lane == u) {
+            mlo[d] = lo;
+            mhi[d] = hi;
+          }
         }
-        if (lane == 0) {
-          if (s0 == 0) {
+        const uint64_t fk = __shfl_sync(0xFFFFFFFFu, k[u], 0);
+        const uint32_t fi = __shfl_sync(0xFFFFFFFFu, id[u], 0);
+        if (lane == u) {
+          mk = fk;
+          mid = fi;
+        }
+      }
+      const int64_t leaf = leaf0 + lane;
+      if (lane < GL && leaf < L) {
+        const int cnt = (int)min((int64_t)phi, n - leaf * phi);
+        if (s0 == 0) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-              nodes.lo[d][leaf] = lo[d];
-              nodes.hi[d][leaf] = hi[d];
-            }
-            nodes.cnt[leaf] = cnt;
-            nodes.ref[leaf] = (uint32_t)(leaf * C);
-            nodes.kids[leaf] = 0;
-            nodes.depth[leaf] = 0;
-            sep_key[leaf] = k[u];
-            sep_id[leaf] = id[u];
-          } else if (s0 < cnt) {  // second round of a leaf wider than a warp
+          for (int d = 0; d < D; ++d) {
+            nodes.lo[d][leaf] = mlo[d];
+            nodes.hi[d][leaf] = mhi[d];
+          }
+          nodes.cnt[leaf] = cnt;
+          nodes.ref[leaf] = (uint32_t)(leaf * C);
+          nodes.kids[leaf] = 0;
+          nodes.depth[leaf] = 0;
+          sep_key[leaf] = mk;
+          sep_id[leaf] = mid;
+        } else if (s0 < cnt) {  // second round of a leaf wider than a warp
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-              nodes.lo[d][leaf] = min(nodes.lo[d][leaf], lo[d]);
-              nodes.hi[d][leaf] = max(nodes.hi[d][leaf], hi[d]);
-            }
+          for (int d = 0; d < D; ++d) {
+            nodes.lo[d][leaf] = min(nodes.lo[d][leaf], mlo[d]);
+            nodes.hi[d][leaf] = max(nodes.hi[d][leaf], mhi[d]);
           }
         }
       }

@@ -43,6 +43,7 @@ constexpr int MAX_PASSES = 8;  // 64-bit keys at 8-bit digits
 
 constexpr uint32_t LB_AGG = 1u << 30, LB_PRE = 2u << 30, LB_VAL = (1u << 30) - 1;
 constexpr int LB_W = 8;  // predecessor tiles read per look-back step
+constexpr int HIST_U = 4;  // items per thread per round of the histogram pass
 
 // Digit width RB in {8, 10, 11}: RADIX digits, DPT digits per thread in the
 // tile epilogue; per-warp counters fit 16 bits (a warp ranks 512 keys).
@@ -72,7 +73,7 @@ struct OnesweepSmem {
 
 struct PassArgs {
   const uint64_t *kin;
-  const uint32_t *vin;  // null: the values are the input positions
+  const uint32_t *vin;
   uint64_t *kout;
   uint32_t *vout;
   const int32_t *pts;
@@ -123,31 +124,51 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   __syncthreads();
   bool bad_any = false;
   uint32_t *mine = shp + (threadIdx.x % R::HIST_PARTS) * passes * R::RADIX;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-    int64_t i = i0 + threadIdx.x;
-    if (i < n) {
-      uint64_t k;
-      if (MODE == 0) {
-        k = kin[i];
-      } else {
-        int32_t c[D];
+  // HIST_U items per thread per round, their loads issued together
+  const int64_t chunk = (int64_t)blockDim.x * HIST_U;
+  const int64_t stride = (int64_t)gridDim.x * chunk;
+  for (int64_t i0 = (int64_t)blockIdx.x * chunk; i0 < n; i0 += stride) {
+    uint64_t k[HIST_U];
+    bool ok[HIST_U];
+    if (MODE == 0) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) c[d] = pts[i * D + d];
-        bool bad;
-        k = point_key<D, CURVE>(htab, c, bits, bad) >> key_shift;
-        bad_any |= bad;
-        if (kst) kst[i] = k;
+      for (int u = 0; u < HIST_U; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+        ok[u] = i < n;
+        k[u] = ok[u] ? kin[i] : 0ull;
       }
-      const uint32_t act = __activemask();
-      for (int p = 0; p < passes; ++p) {
-        uint32_t dg = (uint32_t)(k >> (p * RB)) & (R::RADIX - 1);
-        int all_same;
-        __match_all_sync(act, dg, &all_same);
-        if (all_same) {
-          if ((lanemask_lt() & act) == 0) atomicAdd(&shp[p * R::RADIX + dg], (uint32_t)__popc(act));
-        } else {
-          atomicAdd(&mine[p * R::RADIX + dg], 1u);
+    } else {
+      int32_t c[HIST_U][D];
+#pragma unroll
+      for (int u = 0; u < HIST_U; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x + threadIdx.x;
+        ok[u] = i < n;
+#pragma unroll
+        for (int d = 0; d < D; ++d) c[u][d] = ok[u] ? pts[i * D + d] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < HIST_U; ++u) {
+        bool bad;
+        k[u] = point_key<D, CURVE>(htab, c[u], bits, bad) >> key_shift;
+        if (ok[u]) {
+          bad_any |= bad;
+          if (kst) kst[i0 + (int64_t)u * blockDim.x + threadIdx.x] = k[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < HIST_U; ++u) {
+      const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok[u]);
+      if (ok[u]) {
+        for (int p = 0; p < passes; ++p) {
+          uint32_t dg = (uint32_t)(k[u] >> (p * RB)) & (R::RADIX - 1);
+          int all_same;
+          __match_all_sync(act, dg, &all_same);
+          if (all_same) {
+            if ((lanemask_lt() & act) == 0) atomicAdd(&shp[p * R::RADIX + dg], (uint32_t)__popc(act));
+          } else {
+            atomicAdd(&mine[p * R::RADIX + dg], 1u);
+          }
         }
       }
     }
@@ -191,6 +212,8 @@ __global__ void k_hist_scan(const uint32_t *hist, uint32_t *gbase) {
   }
 }
 
+// MODE 0: keys and values read; 1: keys computed from the points, values =
+// positions; 2: keys read, values = positions.
 template <int MODE, int D, int CURVE, int RB, int IO = IO_PAIRS>
 __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
   using R = Radix<RB>;
@@ -243,7 +266,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
     if (IO >= IO_KEYS) k &= a.kmask;
     return (uint32_t)(k >> sh) & (RADIX - 1);
   };
-  if (MODE == 0 && IO <= IO_PACK && a.vin) {  // the values are read after the keys are ranked: start them towards L2 now
+  if (MODE == 0 && IO <= IO_PACK) {  // the values are read after the keys are ranked: start them towards L2 now
     for (int i = tid * 32; i < tile_n; i += ST * 32)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a.vin + base + i));
   }
@@ -257,7 +280,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
     key[j] = ~0ull;
     if (li < tile_n) {
       const int64_t gi = base + li;
-      if (MODE == 0) {
+      if (MODE != 1) {
         key[j] = a.kin[gi];
       } else {
         int32_t c[D];
@@ -393,8 +416,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
 #pragma unroll
     for (int j = 0; j < SI; ++j) {
       const int li = wbase + j * 32 + lane;
-      if (li < tile_n) sm.stage[rank[j]] |= (uint64_t)(MODE == 1 || !a.vin ? (uint32_t)(base + li) : a.vin[base + li])
-                                            << a.kr;
+      if (li < tile_n) sm.stage[rank[j]] |= (uint64_t)(MODE != 0 ? (uint32_t)(base + li) : a.vin[base + li]) << a.kr;
     }
   }
   __syncthreads();
@@ -460,7 +482,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
 #pragma unroll
     for (int j = 0; j < SI; ++j) {
       const int li = wbase + j * 32 + lane;
-      if (li < tile_n) s_v[rank[j]] = (MODE == 1 || !a.vin) ? (uint32_t)(base + li) : a.vin[base + li];
+      if (li < tile_n) s_v[rank[j]] = MODE != 0 ? (uint32_t)(base + li) : a.vin[base + li];
     }
     __syncthreads();
 #pragma unroll
@@ -575,7 +597,10 @@ static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
   const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX + kCurveTabBytes;
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
+  // all blocks resident at once (the grid-stride rounds stay balanced)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) per_sm = 0;
+  const int grid = (int)std::min<int64_t>(ceil_div(n, 256 * HIST_U), (int64_t)num_sms() * std::max(per_sm, 1));
   PSI_LAUNCH_NAMED("k_sort_hist", kern, std::max(grid, 1), 256, smem, s, kin, enc.pts, enc.bits, enc.key_shift, n,
                    passes, hist, status, kst);
   return PSI_OK;
@@ -698,8 +723,10 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     a.drop = drop;
     if (p >= pk)
       st = launch_packed<RB>(enc, a, tiles, p == pk ? IO_PACK : (p + 1 < passes ? IO_KEYS : IO_UNPACK), s);
-    else if (p > 0 || !encode || stored)
+    else if (p > 0 || !encode)
       st = launch_pass<0, 2, 0, RB>(a, tiles, s);
+    else if (stored)  // written keys, values = positions
+      st = launch_pass<2, 2, 0, RB>(a, tiles, s);
     else if (enc.dim == 2)  // Morton keys computed from the points
       st = launch_pass<1, 2, 0, RB>(a, tiles, s);
     else
