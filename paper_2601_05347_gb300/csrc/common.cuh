@@ -39,6 +39,19 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // (key, id) lexicographic order
+// Adds the sum of v over all threads of the block to *ctr with one global
+// atomic (a counter every thread would otherwise hit serialises in L2).  Every
+// thread of the block must call it; blockDim.x is a multiple of 32.
+__device__ __forceinline__ void block_count_add(unsigned long long *ctr, uint32_t v) {
+  __shared__ unsigned long long s_sum;
+  if (threadIdx.x == 0) s_sum = 0;
+  __syncthreads();
+  const uint32_t w = __reduce_add_sync(0xFFFFFFFFu, v);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_sum, (unsigned long long)w);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_sum) atomicAdd(ctr, s_sum);
+}
+
 __device__ __forceinline__ bool kid_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
   return ka < kb || (ka == kb && ia < ib);
 }

@@ -882,7 +882,7 @@ __global__ void k_fto_aos(FPoints p, int64_t n, float *out, uint32_t *ids) {
 template <int D>
 __global__ void k_fmark(FPoints p, int64_t n, const uint64_t *bkeys, const uint32_t *bvals, const float *bpts,
                         int64_t m, int32_t *keep, unsigned long long *deleted) {
-  unsigned long long del = 0;
+  uint32_t del = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t id = p.id[i];
     int64_t lo = 0, hi = m;
@@ -903,7 +903,7 @@ __global__ void k_fmark(FPoints p, int64_t n, const uint64_t *bkeys, const uint3
     keep[i] = !hit;
     del += hit;
   }
-  if (del) atomicAdd(deleted, del);
+  block_count_add(deleted, (uint32_t)del);
 }
 
 template <int D>

@@ -368,6 +368,7 @@ template <int D>
 __global__ void k_mark_deleted(const uint64_t *pkey, const uint32_t *pid, Pool pool, int64_t n, const uint64_t *bkeys,
                                const uint32_t *bvals, const int32_t *pts, const uint32_t *ids, int64_t m,
                                int32_t *keep, unsigned long long *deleted) {
+  uint32_t removed = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = bkeys[j];
     const uint32_t v = bvals[j];
@@ -384,9 +385,10 @@ __global__ void k_mark_deleted(const uint64_t *pkey, const uint32_t *pid, Pool p
       bool same = true;
 #pragma unroll
       for (int d = 0; d < D; ++d) same &= pool.px[d][lo] == pts[(int64_t)v * D + d];
-      if (same && atomicExch(&keep[lo], 0) == 1) atomicAdd(deleted, 1ull);
+      if (same && atomicExch(&keep[lo], 0) == 1) ++removed;
     }
   }
+  block_count_add(deleted, removed);
 }
 
 template <int D>

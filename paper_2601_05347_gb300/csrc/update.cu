@@ -211,9 +211,8 @@ struct InsertArgs {
   int64_t L, Lnew;
   int64_t base_block;
   const uint64_t *bkeys;
-  const uint32_t *bvals;
-  const int32_t *pts;
-  const uint32_t *ids;
+  const uint32_t *rid;  // batch records (k_batch_records): id and point of each sorted entry
+  const int32_t *rpt;
   int C, phi;
 };
 
@@ -221,7 +220,7 @@ struct InsertArgs {
 __device__ __forceinline__ bool leaf_before_slice(const InsertArgs &a, uint32_t ls, int64_t bi) {
   const uint64_t lk = a.pool.pkey[ls], sk = a.bkeys[bi];
   if (lk != sk) return lk < sk;
-  return a.pool.pid[ls] <= a.ids[a.bvals[bi]];
+  return a.pool.pid[ls] <= a.rid[bi];
 }
 
 // A warp takes 32 new leaf positions: a lane copies the descriptor of an
@@ -272,16 +271,15 @@ __global__ void k_insert_apply(InsertArgs a) {
       // untouched or append: the leaf keeps its block and separator
       for (int s = lane; s < len; s += 32) {
         const int64_t bi = a.sbeg[j] + s;
-        const uint32_t v = a.bvals[bi];
         const uint32_t slot = s0 + (uint32_t)(cnt + s);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          const int32_t c = a.pts[(int64_t)v * D + d];
+          const int32_t c = a.rpt[bi * D + d];
           a.pool.px[d][slot] = c;
           blo[d] = min(blo[d], c);
           bhi[d] = max(bhi[d], c);
         }
-        a.pool.pid[slot] = a.ids[v];
+        a.pool.pid[slot] = a.rid[bi];
         a.pool.pkey[slot] = a.bkeys[bi];
       }
 #pragma unroll
@@ -335,16 +333,16 @@ __global__ void k_insert_apply(InsertArgs a) {
         a.pool.pid[dst] = a.pool.pid[src];
         a.pool.pkey[dst] = a.pool.pkey[src];
       } else {
-        const uint32_t v = a.bvals[sb + si];
+        const int64_t bi = sb + si;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          const int32_t cc = a.pts[(int64_t)v * D + d];
+          const int32_t cc = a.rpt[bi * D + d];
           a.pool.px[d][dst] = cc;
           blo[d] = min(blo[d], cc);
           bhi[d] = max(bhi[d], cc);
         }
-        a.pool.pid[dst] = a.ids[v];
-        a.pool.pkey[dst] = a.bkeys[sb + si];
+        a.pool.pid[dst] = a.rid[bi];
+        a.pool.pkey[dst] = a.bkeys[bi];
       }
     }
 #pragma unroll
@@ -383,8 +381,7 @@ __global__ void k_insert_apply(InsertArgs a) {
 // leaves, one lane per leaf finds those with a slice.
 template <int D>
 __global__ void k_append_inplace(Leaves lv, Pool pool, const int32_t *sbeg, const int32_t *send, int64_t L,
-                                 const uint64_t *bkeys, const uint32_t *bvals, const int32_t *pts,
-                                 const uint32_t *ids) {
+                                 const uint64_t *bkeys, const uint32_t *rid, const int32_t *rpt) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < L; j0 += warps * 32) {
@@ -404,16 +401,15 @@ __global__ void k_append_inplace(Leaves lv, Pool pool, const int32_t *sbeg, cons
         bhi[d] = INT32_MIN;
       }
       for (int t = lane; t < len; t += 32) {
-        const uint32_t v = bvals[b + t];
         const uint32_t slot = s0 + (uint32_t)(cnt + t);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          const int32_t c = pts[(int64_t)v * D + d];
+          const int32_t c = rpt[(b + t) * D + d];
           pool.px[d][slot] = c;
           blo[d] = min(blo[d], c);
           bhi[d] = max(bhi[d], c);
         }
-        pool.pid[slot] = ids[v];
+        pool.pid[slot] = rid[b + t];
         pool.pkey[slot] = bkeys[b + t];
       }
 #pragma unroll
@@ -434,96 +430,141 @@ __global__ void k_append_inplace(Leaves lv, Pool pool, const int32_t *sbeg, cons
   }
 }
 
-// Remove the points named by each leaf's slice: a warp takes 32 leaves, one
-// lane per leaf finds those with a slice, then the warp compacts each of them.
+// The sorted batch as records: the id and the point of each (key-sorted)
+// entry, so that a leaf finds what its slice names in one read.
 template <int D>
+__global__ void k_batch_records(const uint32_t *bvals, const int32_t *pts, const uint32_t *ids, int64_t m,
+                                uint32_t *rid, int32_t *rpt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = bvals[i];
+    rid[i] = ids[v];
+#pragma unroll
+    for (int d = 0; d < D; ++d) rpt[i * D + d] = pts[(int64_t)v * D + d];
+  }
+}
+
+// Remove the points named by each leaf's slice: a warp takes 32 leaves, one
+// lane per leaf finds those with a slice, then the warp compacts them two at a
+// time (both leaves' points and slice entries requested before either is
+// compacted).  R rows of 32 slots cover a leaf's block (R * 32 >= C).
+constexpr int DG = 2;
+
+template <int D, int R>
 __global__ void k_delete_leaves(Leaves lv, Pool pool, const int32_t *sbeg, const int32_t *send, int64_t L,
-                                const uint64_t *bkeys, const uint32_t *bvals, const int32_t *pts,
-                                const uint32_t *ids, unsigned long long *deleted) {
+                                const uint64_t *bkeys, const uint32_t *rid, const int32_t *rpt,
+                                unsigned long long *deleted) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  uint32_t removed = 0;  // lane 0: points this warp removed
   for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < L; j0 += warps * 32) {
     const int64_t jl = j0 + lane;
     uint32_t todo = __ballot_sync(0xFFFFFFFFu, jl < L && send[jl] > sbeg[jl]);
-   while (todo) {
-    const int64_t j = j0 + __ffs(todo) - 1;
-    todo &= todo - 1;
-    const int64_t b = sbeg[j], e = send[j];
-    const int cnt = lv.cnt[j];
-    const uint32_t s0 = lv.ref[j];
-    uint64_t k[MAXPL];
-    uint32_t id[MAXPL];
-    int32_t c[MAXPL][D];
-    bool keep[MAXPL];
+    while (todo) {
+      int64_t j[DG];
+      int cnt[DG];
+      uint32_t s0[DG];
+      int32_t b[DG], e[DG];
 #pragma unroll
-    for (int r = 0; r < MAXPL; ++r) {
-      const int x = r * 32 + lane;
-      keep[r] = false;
-      if (x < cnt) {
-        k[r] = pool.pkey[s0 + x];
-        id[r] = pool.pid[s0 + x];
-#pragma unroll
-        for (int d = 0; d < D; ++d) c[r][d] = pool.px[d][s0 + x];
-        // is (k, id) in the slice?
-        int64_t lo = b, hi = e;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (kid_less(bkeys[mid], ids[bvals[mid]], k[r], id[r]))
-            lo = mid + 1;
-          else
-            hi = mid;
+      for (int g = 0; g < DG; ++g) {
+        cnt[g] = 0;
+        s0[g] = 0;
+        b[g] = e[g] = 0;
+        j[g] = -1;
+        if (todo) {
+          j[g] = j0 + __ffs(todo) - 1;
+          todo &= todo - 1;
+          cnt[g] = lv.cnt[j[g]];
+          s0[g] = lv.ref[j[g]];
+          b[g] = sbeg[j[g]];
+          e[g] = send[j[g]];
         }
-        bool hit = false;
-        if (lo < e && bkeys[lo] == k[r] && ids[bvals[lo]] == id[r]) {
-          hit = true;
-          const uint32_t v = bvals[lo];
-#pragma unroll
-          for (int d = 0; d < D; ++d) hit &= pts[(int64_t)v * D + d] == c[r][d];
-        }
-        keep[r] = !hit;
       }
-    }
-    __syncwarp();
-    int out = 0;
-    int32_t blo[D], bhi[D];
+      uint64_t k[DG][R];
+      uint32_t id[DG][R];
+      int32_t c[DG][R][D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      blo[d] = INT32_MAX;
-      bhi[d] = INT32_MIN;
-    }
+      for (int g = 0; g < DG; ++g)
 #pragma unroll
-    for (int r = 0; r < MAXPL; ++r) {
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep[r]);
-      if (keep[r]) {
-        const uint32_t dst = s0 + (uint32_t)(out + __popc(m & lanemask_lt()));
-        pool.pkey[dst] = k[r];
-        pool.pid[dst] = id[r];
+        for (int r = 0; r < R; ++r) {
+          const int x = r * 32 + lane;
+          if (x < cnt[g]) {
+            k[g][r] = pool.pkey[s0[g] + x];
+            id[g][r] = pool.pid[s0[g] + x];
+#pragma unroll
+            for (int d = 0; d < D; ++d) c[g][r][d] = pool.px[d][s0[g] + x];
+          }
+        }
+      bool keep[DG][R];
+#pragma unroll
+      for (int g = 0; g < DG; ++g)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int x = r * 32 + lane;
+          keep[g][r] = false;
+          if (x < cnt[g]) {
+            // is (k, id) in the slice?
+            int32_t lo = b[g], hi = e[g];
+            while (lo < hi) {
+              const int32_t mid = (lo + hi) >> 1;
+              if (kid_less(bkeys[mid], rid[mid], k[g][r], id[g][r]))
+                lo = mid + 1;
+              else
+                hi = mid;
+            }
+            bool hit = lo < e[g] && bkeys[lo] == k[g][r] && rid[lo] == id[g][r];
+            if (hit) {
+#pragma unroll
+              for (int d = 0; d < D; ++d) hit &= rpt[(int64_t)lo * D + d] == c[g][r][d];
+            }
+            keep[g][r] = !hit;
+          }
+        }
+      __syncwarp();
+#pragma unroll
+      for (int g = 0; g < DG; ++g) {
+        if (j[g] < 0) break;  // warp-uniform
+        int out = 0;
+        int32_t blo[D], bhi[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          pool.px[d][dst] = c[r][d];
-          blo[d] = min(blo[d], c[r][d]);
-          bhi[d] = max(bhi[d], c[r][d]);
+          blo[d] = INT32_MAX;
+          bhi[d] = INT32_MIN;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep[g][r]);
+          if (keep[g][r]) {
+            const uint32_t dst = s0[g] + (uint32_t)(out + __popc(m & lanemask_lt()));
+            pool.pkey[dst] = k[g][r];
+            pool.pid[dst] = id[g][r];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              pool.px[d][dst] = c[g][r][d];
+              blo[d] = min(blo[d], c[g][r][d]);
+              bhi[d] = max(bhi[d], c[g][r][d]);
+            }
+          }
+          out += __popc(m);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          blo[d] = __reduce_min_sync(0xFFFFFFFFu, blo[d]);
+          bhi[d] = __reduce_max_sync(0xFFFFFFFFu, bhi[d]);
+        }
+        if (lane == 0) {
+          lv.cnt[j[g]] = out;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            lv.lo[d][j[g]] = blo[d];
+            lv.hi[d][j[g]] = bhi[d];
+          }
+          removed += (uint32_t)(cnt[g] - out);
         }
       }
-      out += __popc(m);
+      __syncwarp();
     }
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      blo[d] = __reduce_min_sync(0xFFFFFFFFu, blo[d]);
-      bhi[d] = __reduce_max_sync(0xFFFFFFFFu, bhi[d]);
-    }
-    if (lane == 0) {
-      lv.cnt[j] = out;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        lv.lo[d][j] = blo[d];
-        lv.hi[d][j] = bhi[d];
-      }
-      if (cnt - out) atomicAdd(deleted, (unsigned long long)(cnt - out));
-    }
-    __syncwarp();
-   }
   }
+  block_count_add(deleted, removed);
 }
 
 __global__ void k_nonempty(const int32_t *cnt, int64_t L, int32_t *keep) {
@@ -582,11 +623,26 @@ int warp_grid(int64_t warps) {
 
 psi_status spac_build_fresh(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t n, cudaStream_t s);
 
+// Records (id, point) of the sorted batch, read by the leaf kernels.
+static psi_status batch_records(const psi_index *ix, const Batch &b, const int32_t *pts, const uint32_t *ids,
+                                int64_t m, cudaStream_t s, Buf<uint32_t> &rid, Buf<int32_t> &rpt) {
+  psi_status st;
+  if ((st = rid.alloc(m, s)) || (st = rpt.alloc(m * ix->D, s))) return st;
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_batch_records", k_batch_records<2>, grid_for(m), 256, 0, s, b.vals, pts, ids, m, rid.p, rpt.p);
+  else
+    PSI_LAUNCH_NAMED("k_batch_records", k_batch_records<3>, grid_for(m), 256, 0, s, b.vals, pts, ids, m, rid.p, rpt.p);
+  return PSI_OK;
+}
+
 psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, cudaStream_t s) {
   if (ix->L == 0) return spac_build_fresh(ix, pts, ids, m, s);
   psi_status st;
   Batch b;
   if ((st = sort_batch(ix, pts, ids, m, s, b))) return st;
+  Buf<uint32_t> rid;
+  Buf<int32_t> rpt;
+  if ((st = batch_records(ix, b, pts, ids, m, s, rid, rpt))) return st;
   const int64_t L = ix->L;
   Buf<int32_t> bleaf, sbeg, send, outl, nblk;
   Buf<int64_t> pos, boff, tot;
@@ -609,10 +665,10 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
     Leaves lv = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
     if (ix->D == 2)
       PSI_LAUNCH_NAMED("k_append_inplace", k_append_inplace<2>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool,
-                       sbeg.p, send.p, L, b.keys, b.vals, pts, ids);
+                       sbeg.p, send.p, L, b.keys, rid.p, rpt.p);
     else
       PSI_LAUNCH_NAMED("k_append_inplace", k_append_inplace<3>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool,
-                       sbeg.p, send.p, L, b.keys, b.vals, pts, ids);
+                       sbeg.p, send.p, L, b.keys, rid.p, rpt.p);
     ix->n += m;
     if ((st = build_spac_summary(ix, s))) return st;
     PSI_CK(cudaGetLastError());
@@ -658,9 +714,8 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   a.Lnew = Lnew;
   a.base_block = base_block;
   a.bkeys = b.keys;
-  a.bvals = b.vals;
-  a.pts = pts;
-  a.ids = ids;
+  a.rid = rid.p;
+  a.rpt = rpt.p;
   a.C = ix->C;
   a.phi = ix->phi;
   if (ix->D == 2)
@@ -698,13 +753,26 @@ psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   PSI_CK(cudaMemsetAsync(del.p, 0, sizeof(unsigned long long), s));
   PSI_LAUNCH(k_locate, grid_for(m), 256, 0, s, b.keys, b.vals, ids, m, ix->sep_key, ix->sep_id, L, bleaf.p);
   PSI_LAUNCH(k_slices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p);
+  Buf<uint32_t> rid;
+  Buf<int32_t> rpt;
+  if ((st = batch_records(ix, b, pts, ids, m, s, rid, rpt))) return st;
   Leaves lv = leaves_of(ix->nodes, ix->sep_key, ix->sep_id);
-  if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<2>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
-                     b.keys, b.vals, pts, ids, del.p);
-  else
-    PSI_LAUNCH_NAMED("k_delete_leaves", k_delete_leaves<3>, warp_grid(ceil_div(L, 32)), 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
-                     b.keys, b.vals, pts, ids, del.p);
+  const int g = warp_grid(ceil_div(L, 32));
+  if (ix->D == 2) {
+    if (ix->C <= 64)
+      PSI_LAUNCH_NAMED("k_delete_leaves", (k_delete_leaves<2, 2>), g, 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+                       b.keys, rid.p, rpt.p, del.p);
+    else
+      PSI_LAUNCH_NAMED("k_delete_leaves", (k_delete_leaves<2, MAXPL>), g, 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+                       b.keys, rid.p, rpt.p, del.p);
+  } else {
+    if (ix->C <= 64)
+      PSI_LAUNCH_NAMED("k_delete_leaves", (k_delete_leaves<3, 2>), g, 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+                       b.keys, rid.p, rpt.p, del.p);
+    else
+      PSI_LAUNCH_NAMED("k_delete_leaves", (k_delete_leaves<3, MAXPL>), g, 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
+                       b.keys, rid.p, rpt.p, del.p);
+  }
   PSI_LAUNCH(k_nonempty, grid_for(L), 256, 0, s, ix->nodes.cnt, L, keep.p);
   if ((st = scan_i32_to_i64(keep.p, pos.p, L, tot.p, s))) return st;
   PSI_LAUNCH(k_copy_i64, 1, 1, 0, s, del.p, tot.p + 1);
