@@ -45,6 +45,15 @@ constexpr uint32_t LB_AGG = 1u << 30, LB_PRE = 2u << 30, LB_VAL = (1u << 30) - 1
 constexpr int LB_W = 8;  // predecessor tiles read per look-back step
 constexpr int HIST_U = 4;  // items per thread per round of the histogram pass
 
+// An event destroyed with its scope.
+struct EventGuard {
+  cudaEvent_t e = nullptr;
+  ~EventGuard() {
+    if (e) cudaEventDestroy(e);
+  }
+};
+constexpr int64_t kPackMin = int64_t(1) << 22;  // smallest encoding sort that may pack
+
 // Digit width RB in {8, 10, 11}: RADIX digits, DPT digits per thread in the
 // tile epilogue; per-warp counters fit 16 bits (a warp ranks 512 keys).
 template <int RB>
@@ -114,7 +123,7 @@ enum : int {
 template <int MODE, int D, int CURVE, int RB>
 __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const int32_t *pts, int bits, int key_shift,
                                                    int64_t n, int passes, uint32_t *hist, int *status,
-                                                   uint64_t *kst) {
+                                                   uint64_t *kst, unsigned long long *near, int near_shift) {
   using R = Radix<RB>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][passes][RADIX]
@@ -123,6 +132,7 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   if (MODE == 1) curve_table_init<D, CURVE>(htab);
   __syncthreads();
   bool bad_any = false;
+  uint32_t n_near = 0;  // input neighbours (i, i + 1) whose keys agree above near_shift
   uint32_t *mine = shp + (threadIdx.x % R::HIST_PARTS) * passes * R::RADIX;
   // HIST_U items per thread per round, their loads issued together
   const int64_t chunk = (int64_t)blockDim.x * HIST_U;
@@ -156,6 +166,14 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
         }
       }
     }
+    if (near) {
+#pragma unroll
+      for (int u = 0; u < HIST_U; ++u) {
+        const uint64_t kn = __shfl_down_sync(0xFFFFFFFFu, k[u], 1);
+        const bool okn = __shfl_down_sync(0xFFFFFFFFu, ok[u], 1);
+        n_near += (threadIdx.x & 31) < 31 && ok[u] && okn && ((k[u] ^ kn) >> near_shift) == 0;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < HIST_U; ++u) {
       const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok[u]);
@@ -174,6 +192,7 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
     }
   }
   if (bad_any) atomicOr(status, ST_RANGE);
+  if (near) block_count_add(near, n_near);
   __syncthreads();
   for (int i = threadIdx.x; i < passes * R::RADIX; i += blockDim.x) {
     uint32_t v = 0;
@@ -592,7 +611,8 @@ __global__ __launch_bounds__(1024) void k_tie_long(const uint64_t *keys, uint32_
 
 template <int MODE, int D, int CURVE, int RB>
 static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_t n, int passes, uint32_t *hist,
-                              int *status, cudaStream_t s, uint64_t *kst = nullptr) {
+                              int *status, cudaStream_t s, uint64_t *kst = nullptr,
+                              unsigned long long *near = nullptr, int near_shift = 0) {
   using R = Radix<RB>;
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
   const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX + kCurveTabBytes;
@@ -602,7 +622,7 @@ static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) per_sm = 0;
   const int grid = (int)std::min<int64_t>(ceil_div(n, 256 * HIST_U), (int64_t)num_sms() * std::max(per_sm, 1));
   PSI_LAUNCH_NAMED("k_sort_hist", kern, std::max(grid, 1), 256, smem, s, kin, enc.pts, enc.bits, enc.key_shift, n,
-                   passes, hist, status, kst);
+                   passes, hist, status, kst, near, near_shift);
   return PSI_OK;
 }
 
@@ -663,38 +683,71 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   Buf<uint64_t> kst;
   if (stored && (st = kst.alloc(n, s))) return st;
 
+  // Packed middle passes (8-bit digits, encoding sorts of at least kPackMin
+  // pairs): pass pk writes value << kr | key >> drop once the value (a
+  // position < n) and the key bits not yet sorted fit 64 bits; passes pk+1 ..
+  // passes-2 move those words alone; the last pass writes the pairs again,
+  // reading each key (or point) at its position.  Those reads are local only
+  // when the input is: the histogram pass counts input neighbours whose keys
+  // share their top 24 bits, and the sort packs when at least half do.  Not
+  // during stream capture (the count is read on the host).
+  int pk = passes, p_pack = passes;
+  int kr = 0, drop = 0;
+  if (encode && RB == 8 && n >= kPackMin) {
+    const int vbits = 64 - __builtin_clzll((uint64_t)(n - 1));
+    int p = 1;
+    while (p < passes && vbits + key_bits - RB * (p + 1) > 64) ++p;
+    if (p + 2 <= passes - 1) p_pack = p;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (p_pack < passes && (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone))
+      p_pack = passes;
+  }
+  // the count reaches the host through a pinned word behind an event, read
+  // only when pass p_pack is about to be launched (the passes before it are
+  // queued meanwhile)
+  static thread_local unsigned long long *h_near = nullptr;
+  if (p_pack < passes && !h_near &&
+      cudaHostAlloc((void **)&h_near, sizeof(unsigned long long), cudaHostAllocPortable) != cudaSuccess) {
+    h_near = nullptr;
+    p_pack = passes;
+  }
+  Buf<unsigned long long> nearc;
+  EventGuard near_ev;
+  if (p_pack < passes) {
+    if ((st = nearc.alloc(1, s))) return st;
+    PSI_CK(cudaMemsetAsync(nearc.p, 0, sizeof(unsigned long long), s));
+    PSI_CK(cudaEventCreateWithFlags(&near_ev.e, cudaEventDisableTiming));
+  }
+  const int near_shift = std::max(0, key_bits - 24);
+
   // digit 0 is counted up front; every pass counts the next digit of its keys
   if (!encode)
     st = launch_hist<0, 2, 0, RB>(keys_in, enc, n, 1, hist.p, d_status, s);
   else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
-    st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
+    st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s, nullptr, nearc.p, near_shift);
   else if (enc.dim == 2)
-    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p);
+    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p, nearc.p, near_shift);
   else if (enc.curve == CURVE_MORTON)
-    st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s);
+    st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s, nullptr, nearc.p, near_shift);
   else
-    st = launch_hist<1, 3, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p);
+    st = launch_hist<1, 3, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p, nearc.p, near_shift);
   if (st) return st;
-
-  // Packed middle passes (8-bit digits, encoding sorts): pass pk writes
-  // value << kr | key >> drop once the value (a position < n) and the key bits
-  // not yet sorted fit 64 bits; passes pk+1 .. passes-2 move those words alone;
-  // the last pass writes the pairs again.  Worth it with one middle pass or more.
-  int pk = passes;
-  int kr = 0, drop = 0;
-  if (encode && RB == 8) {
-    const int vbits = n > 1 ? 64 - __builtin_clzll((uint64_t)(n - 1)) : 1;
-    int p = 1;
-    while (p < passes && vbits + key_bits - RB * (p + 1) > 64) ++p;
-    if (p + 2 <= passes - 1) {
-      pk = p;
-      drop = RB * (pk + 1);
-      kr = key_bits - drop;
-    }
+  if (p_pack < passes) {
+    PSI_CK(cudaMemcpyAsync(h_near, nearc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PSI_CK(cudaEventRecord(near_ev.e, s));
   }
+
   uint64_t *kb[2] = {kbuf0, kbuf1};
   uint32_t *vb[2] = {vbuf0, vbuf1};
   for (int p = 0; p < passes; ++p) {
+    if (p == p_pack) {
+      PSI_CK(cudaEventSynchronize(near_ev.e));
+      if (2 * *h_near >= (unsigned long long)n) {
+        pk = p_pack;
+        drop = RB * (pk + 1);
+        kr = key_bits - drop;
+      }
+    }
     PassArgs a;
     a.kin = p == 0 ? (stored ? kst.p : keys_in) : kb[(p - 1) & 1];
     a.vin = p == 0 ? vals_in : vb[(p - 1) & 1];

@@ -147,13 +147,19 @@ def test_every_digit_width_gives_the_same_index(radix, kind, dim, bits):
     assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
 
 
-@pytest.mark.parametrize("kind,dim,bits,n", [("spac_h", 2, 30, (1 << 20) + 3), ("spac_z", 2, 30, 1 << 20),
-                                              ("spac_h", 3, 21, (1 << 20) + 5), ("porth", 3, 21, (1 << 20) + 1)])
-def test_build_across_the_packed_sort_thresholds(kind, dim, bits, n):
-    # an encoding sort packs (position, unsorted key bits) into one word from the
-    # first pass after which they fit 64 bits: pass 1 up to 2^20 points, pass 2
-    # (2D) or 3 (3D) beyond; its last pass recomputes the keys from the points
-    p, ids = points(n, dim, bits, 71 + n % 97, clustered=n % 2 == 1)
+@pytest.mark.parametrize("kind,dim,bits,n,clustered", [("spac_h", 2, 30, (1 << 22) + 3, True),
+                                                        ("spac_z", 2, 30, (1 << 22) + 5, True),
+                                                        ("porth", 3, 21, (1 << 22) + 1, True),
+                                                        ("spac_h", 3, 21, (1 << 22) + 7, True),
+                                                        ("spac_h", 2, 30, 1 << 22, False)])
+def test_build_across_the_packed_sort_threshold(kind, dim, bits, n, clustered):
+    # an encoding sort of at least 2^22 pairs whose input is locally ordered
+    # (walk-ordered clustered points) packs (position, unsorted key bits) into
+    # one word for its middle passes, from pass 2 at this size; its last pass
+    # reads each key (Hilbert: written by the histogram pass; Morton: recomputed
+    # from the point) back at its position.  Uniform input in random order
+    # keeps (key, value) pairs throughout.
+    p, ids = points(n, dim, bits, 71 + n % 97, clustered=clustered)
     ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
     o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
     if kind == "porth":
@@ -195,6 +201,22 @@ def query_points(nq, dim, bits, seed, data):
         take = gen.sample_with_replacement(len(data), nq // 3, seed + 1)
         q[: nq // 3] = data[take]
     return q
+
+
+@pytest.mark.parametrize("kind,dim", [("spac_h", 2), ("spac_z", 3)])
+def test_knn_of_many_walk_ordered_queries(kind, dim):
+    # 2^22 + 3 queries along random walks: the curve-order sort of the queries
+    # packs its middle passes; every answer row must still belong to its query
+    bits = 30 if dim == 2 else 21
+    p, ids = points(200_000, dim, bits, 91, clustered=True)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
+    q = gen.varden((1 << 22) + 3, dim, bits, 92)
+    gi, gd = ix.knn(T(q), 10)
+    gi, gd = U32(gi), gd.cpu().numpy()
+    rows = np.sort(gen.sample_with_replacement(len(q), 20_000, 93))
+    oi, od = o.knn(q[rows], 10)
+    assert (gi[rows] == oi).all() and (gd[rows] == od).all()
 
 
 @pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("spac_z", 3, 21),
