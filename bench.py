@@ -136,11 +136,15 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # per-kernel algorithmic byte model (2D, per launch)
 # ---------------------------------------------------------------------------
-def sort_bytes(items: int, key_bits: int, stored: bool, dim: int = 2) -> tuple[float, float]:
+PACK_MIN = 1 << 22  # smallest encoding sort the library packs
+
+
+def sort_bytes(items: int, key_bits: int, stored: bool, dim: int = 2, local: bool = False) -> tuple[float, float]:
     """Algorithmic HBM bytes of one encoding key sort (8-bit digits): (histogram
     pass, all digit passes).  Mirrors the library's plan: Hilbert keys are
-    computed once in the histogram pass and written (stored); once a position
-    and the unsorted key bits fit 64 bits, pass pk packs them into one word, the
+    computed once in the histogram pass and written (stored); a sort of at
+    least PACK_MIN pairs whose input is locally ordered packs, once a position
+    and the unsorted key bits fit 64 bits, both into one word at pass pk: the
     middle passes move 8-B words and the last pass writes the pairs again."""
     pt = 4 * dim
     passes = (key_bits + 7) // 8
@@ -148,7 +152,7 @@ def sort_bytes(items: int, key_bits: int, stored: bool, dim: int = 2) -> tuple[f
     p = 1
     while p < passes and vbits + key_bits - 8 * (p + 1) > 64:
         p += 1
-    pk = p if p + 2 <= passes - 1 else passes
+    pk = p if (local and items >= PACK_MIN and p + 2 <= passes - 1) else passes
     hist = pt + (8 if stored else 0)
     per = 0
     for q in range(passes):
@@ -169,13 +173,14 @@ def kernel_bytes(name: str, w, launches: int) -> float | None:
     """Algorithmic HBM bytes of all launches of a kernel in one step.
 
     k_onesweep, k_sort_hist  the encoding key sorts of the step (`sort_bytes`):
-                 build, insert batch, delete batch (60-bit Hilbert keys) and the
-                 query order (top 48 key bits).
+                 build (walk-ordered: packs), insert batch, delete batch
+                 (60-bit Hilbert keys, below PACK_MIN) and the query order (top
+                 48 key bits, queries in random order: pairs throughout).
     k_leaf_gather reads sorted key + position (12 B) and gathers point + id
                  (12 B), writes x, y, id, key (20 B): 44 B per point.
     """
     n, mi, md = w["n"], w["m_ins"], w["m_del"]
-    sorts = [sort_bytes(n, 60, True), sort_bytes(mi, 60, True), sort_bytes(md, 60, True),
+    sorts = [sort_bytes(n, 60, True, local=True), sort_bytes(mi, 60, True), sort_bytes(md, 60, True),
              sort_bytes(w["n_knn"], 48, True)]
     if name == "k_onesweep":
         return sum(b for _, b in sorts)

@@ -1,0 +1,42 @@
+"""The algorithmic bytes behind the bench's sort roofline: one digit pass moves
+(key 8 B, value 4 B) in and out; an encoding sort of at least 2^22 locally
+ordered pairs packs (position, unsorted key bits) into one 8-B word for its
+middle passes.  Each figure is the per-pass sum written out by hand."""
+import bench
+
+
+def test_pairs_sort_of_hilbert_keys():
+    # 8 passes of 60-bit keys: pass 0 reads the written key (8) and writes a pair (12),
+    # seven more passes move pairs (24); the histogram pass reads the point and writes the key
+    hist, passes = bench.sort_bytes(1000, 60, True)
+    assert hist == 1000 * (8 + 8)
+    assert passes == 1000 * (20 + 7 * 24)
+
+
+def test_pairs_sort_of_morton_keys_in_3d():
+    # Morton keys are not written: histogram and first pass read the 12-B point
+    hist, passes = bench.sort_bytes(1000, 63, False, dim=3)
+    assert hist == 1000 * 12
+    assert passes == 1000 * (12 + 12 + 7 * 24)
+
+
+def test_packed_sort_of_a_walk_ordered_1e8_build():
+    # 27-bit positions: 27 + 60 - 8 * 3 <= 64, so pass 2 packs; passes 3..6 move words; pass 7 unpacks
+    n = 100_000_000
+    hist, passes = bench.sort_bytes(n, 60, True, local=True)
+    assert hist == n * 16
+    assert passes == n * (20 + 24 + (12 + 8) + 4 * 16 + (8 + 8 + 12))
+
+
+def test_packing_needs_size_and_local_order():
+    big = 1 << 22
+    assert bench.sort_bytes(big, 60, True, local=False) == bench.sort_bytes(big, 60, True)
+    assert bench.sort_bytes(big - 1, 60, True, local=True) == ((big - 1) * 16, (big - 1) * (20 + 7 * 24))
+    _, packed = bench.sort_bytes(big, 60, True, local=True)
+    assert packed < big * (20 + 7 * 24)
+
+
+def test_query_order_sort_is_six_passes_of_pairs():
+    # 1e7 queries in random order, top 48 key bits
+    hist, passes = bench.sort_bytes(10_000_000, 48, True)
+    assert passes == 10_000_000 * (20 + 5 * 24)
