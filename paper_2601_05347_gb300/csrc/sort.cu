@@ -699,8 +699,11 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     while (p < passes && vbits + key_bits - RB * (p + 1) > 64) ++p;
     if (p + 2 <= passes - 1) p_pack = p;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (p_pack < passes && (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone))
+    if (p_pack < passes && cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();  // a refused query: sort unpacked, leave no error behind
       p_pack = passes;
+    }
+    if (cs != cudaStreamCaptureStatusNone) p_pack = passes;
   }
   // the count reaches the host through a pinned word behind an event, read
   // only when pass p_pack is about to be launched (the passes before it are
@@ -708,15 +711,20 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   static thread_local unsigned long long *h_near = nullptr;
   if (p_pack < passes && !h_near &&
       cudaHostAlloc((void **)&h_near, sizeof(unsigned long long), cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
     h_near = nullptr;
     p_pack = passes;
   }
   Buf<unsigned long long> nearc;
   EventGuard near_ev;
+  if (p_pack < passes && cudaEventCreateWithFlags(&near_ev.e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();  // e.g. another thread capturing in global mode: sort unpacked
+    near_ev.e = nullptr;
+    p_pack = passes;
+  }
   if (p_pack < passes) {
     if ((st = nearc.alloc(1, s))) return st;
     PSI_CK(cudaMemsetAsync(nearc.p, 0, sizeof(unsigned long long), s));
-    PSI_CK(cudaEventCreateWithFlags(&near_ev.e, cudaEventDisableTiming));
   }
   const int near_shift = std::max(0, key_bits - 24);
 
