@@ -73,6 +73,27 @@ def _warm_pinned(total: int):
     del keep
 
 
+def plan_epochs(batch):
+    """Splits an admitted round (arrival order) into epochs (queries, updates):
+    the queries of an epoch run against the tree as every earlier update left
+    it, then its updates apply -- one delete, or consecutive inserts with no
+    query between them as one batch (the point set, and so every query result,
+    is the same as inserting them one by one).  The last epoch has no update."""
+    epochs, cur = [], []
+    for r in batch:
+        if r.kind in ("insert", "delete"):
+            if (r.kind == "insert" and not cur and epochs and epochs[-1][1]
+                    and epochs[-1][1][0].kind == "insert"):
+                epochs[-1][1].append(r)
+            else:
+                epochs.append((cur, [r]))
+            cur = []
+        else:
+            cur.append(r)
+    epochs.append((cur, None))
+    return epochs
+
+
 class Server:
     """Continuous-batching request loop around a psi.Index."""
 
@@ -142,18 +163,7 @@ class Server:
                 if self.stop_flag:
                     return
                 continue
-            epochs, cur = [], []  # (queries, [updates]): one delete, or inserts applied together
-            for r in batch:
-                if r.kind in ("insert", "delete"):
-                    if (r.kind == "insert" and not cur and epochs and epochs[-1][1]
-                            and epochs[-1][1][0].kind == "insert"):
-                        epochs[-1][1].append(r)
-                    else:
-                        epochs.append((cur, [r]))
-                    cur = []
-                else:
-                    cur.append(r)
-            epochs.append((cur, None))
+            epochs = plan_epochs(batch)
             self.rounds.append((len(batch), len(epochs)))
             try:
                 for queries, updates in epochs:
