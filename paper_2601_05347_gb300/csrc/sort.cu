@@ -7,21 +7,23 @@
 // pass per digit that ranks a tile in shared memory and obtains the tile's
 // global digit offsets by decoupled look-back over earlier tiles):
 //   * k_sort_hist     reads every key once (computing it from the point when
-//                     encoding) and accumulates all digit histograms;
-//   * k_hist_scan     turns them into per-digit global bases;
+//                     encoding) and counts the first digit;
 //   * k_onesweep      per digit: warp-level ranking (peer lanes from one ballot
 //                     per digit bit) into per-warp shared counters (stable),
-//                     tile totals published to a
-//                     look-back table, bounded spin on predecessors, shared-
-//                     memory staging so that each digit's run is written out
-//                     contiguously.
+//                     tile totals published to a look-back table, bounded spin
+//                     on predecessors, shared-memory staging so that each
+//                     digit's run is written out contiguously; it also counts
+//                     the next digit of its keys for the following pass;
+//   * k_hist_scan     (the allocation-free sort) scans histograms of all digits.
 // An encoding sort computes Morton keys from the points in its first digit
 // pass, so they are never written before they are sorted; Hilbert keys, whose
 // arithmetic costs more than an 8-byte write and read, are computed once in
-// the histogram pass and written out.  Once a position (< n) and the key bits
-// not yet sorted fit 64 bits, the middle passes move them as one packed word
-// and the last pass writes (key, position) pairs again: Morton keys recomputed
-// from the point, Hilbert keys gathered from the written ones.
+// the histogram pass and written out.  A sort of at least kPackMin pairs whose
+// input is locally ordered (most neighbouring inputs share their top 24 key
+// bits, counted by the histogram pass) packs, once a position (< n) and the key
+// bits not yet sorted fit 64 bits, both into one word for its middle passes;
+// its last pass writes (key, position) pairs again: Morton keys recomputed from
+// the point, Hilbert keys gathered from the written ones.
 // Equal keys (duplicate points) are then put in id order by k_tie_runs /
 // k_tie_long (a later canonical leaf layout depends on it).
 #include "common.cuh"
