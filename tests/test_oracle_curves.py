@@ -100,6 +100,18 @@ def test_hilbert_self_similar_at_30_bits():
     assert O.hilbert2(0, 0, 30) == 0
 
 
+def test_hilbert_lower_left_quadrant_is_the_mirrored_curve():
+    # the first quadrant of a curve of b + 1 levels is the b-level curve mirrored
+    # about the diagonal (x and y exchanged), so two extra levels change nothing
+    rng = np.random.default_rng(4)
+    for bits in (1, 2, 5, 13, 29):
+        for x, y in rng.integers(0, 1 << bits, size=(200, 2)):
+            x, y = int(x), int(y)
+            assert O.hilbert2(x, y, bits + 1) == O.hilbert2(y, x, bits)
+            if bits + 2 <= 31:
+                assert O.hilbert2(x, y, bits + 2) == O.hilbert2(x, y, bits)
+
+
 def hilbert3_inverse(bits):
     side = 1 << bits
     cells = [None] * (side ** 3)
