@@ -709,7 +709,9 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   }
   // the count reaches the host through a pinned word behind an event, read
   // only when pass p_pack is about to be launched (the passes before it are
-  // queued meanwhile)
+  // queued meanwhile).  One word per host thread, allocated on its first
+  // packing sort and kept for the thread's lifetime (a sort on that thread
+  // finishes with the word before the next one starts).
   static thread_local unsigned long long *h_near = nullptr;
   if (p_pack < passes && !h_near &&
       cudaHostAlloc((void **)&h_near, sizeof(unsigned long long), cudaHostAllocPortable) != cudaSuccess) {
