@@ -14,10 +14,13 @@
 //   delete: every leaf point whose (key, id) occurs in the slice (and whose
 //           coordinates match) is removed; survivors are compacted in place
 //           and the box recomputed; empty leaves are dropped.
-// Only touched leaves move data.  The leaf list is then rewritten from a scan
-// of per-leaf output counts and the summary tree rebuilt over it -- the
-// paper's join-based rebalancing is replaced by this relayout of the (small)
-// leaf directory.
+// Only touched leaves move data; they read the sorted batch as records (id
+// and point per entry, gathered once by k_batch_records).  The leaf list is
+// then rewritten from a scan of per-leaf output counts and the summary tree
+// rebuilt over it -- the paper's join-based rebalancing is replaced by this
+// relayout of the (small) leaf directory.  Leaves that deletes leave under
+// phi / 2 are not merged with their neighbours (no query depends on leaf
+// shape).
 #include "index.cuh"
 
 namespace psi {
