@@ -15,7 +15,11 @@ P = ctypes.c_void_p(1 << 20)  # a non-null pointer that is never dereferenced: t
 @pytest.fixture(scope="module")
 def L():
     _build.build()
-    return psi.lib()
+    lib = psi.lib()
+    yield lib
+    # a successful call clears the message: later modules see the library as loaded fresh
+    assert lib.psi_sort_pairs(NULL, NULL, 0, 60, NULL) == OK
+    assert lib.psi_last_error() == b""
 
 
 def cfg(dim=2, kind=psi.SPAC_Z, leaf=32, bits=30, fanout=0, radix=0):
