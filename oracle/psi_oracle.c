@@ -7,7 +7,7 @@
  * (key, id, point) records; every update re-derives the canonical layout from
  * that array.  Each function names the passage it follows.
  *
- * Readings of passages the paper leaves open (listed again in the design doc):
+ * Readings of passages the paper leaves open:
  *   - Morton bit order: key bit D*i + d is bit i of coordinate d (x lowest).
  *   - Hilbert orientation: Hilbert's 1891 curve starting at (0,0), visiting the
  *     quadrants lower-left, upper-left, upper-right, lower-right, ending at

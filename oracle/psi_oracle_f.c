@@ -9,7 +9,7 @@
  * nothing with the CUDA library's level-synchronous partition.  Compile with
  * -ffp-contract=off: every float and double operation is rounded on its own.
  *
- * Readings of passages the paper leaves open (listed again in the design doc):
+ * Readings of passages the paper leaves open:
  *   - The root region H = [lo, hi)^D is given by the caller; every point must
  *     lie in it.
  *   - Midpoint of [lo, hi): mid = lo + 0.5f * (hi - lo) in float arithmetic; a

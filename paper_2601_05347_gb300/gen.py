@@ -7,7 +7,7 @@ of a stream with seed s is ``mix(s + (i + 1) * 0x9E3779B97F4A7C15)`` with the
 published finaliser, so any slice of any stream can be regenerated
 independently and identically on any machine.
 
-Workload recipe (restated in the design doc):
+Workload recipe:
   * Uniform: each coordinate is the top ``bits`` bits of one 64-bit draw.
   * Varden (random walks, the generator of Gan and Tao 2017 as the paper uses
     it): ``clusters`` walkers each produce a contiguous share of the points;

@@ -52,9 +52,11 @@ SIZES = [0, 1, 31, 32, 33, 1000, 4095, 4097, 12345, 70001, 5, 800, 0, 3000, 9000
 
 @pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
 @pytest.mark.parametrize("threads", [256, 512, 1024])
-def test_batch_layout_and_knn_match_oracle(kind, threads):
+@pytest.mark.parametrize("phi", [16, 32, 64])
+def test_batch_layout_and_knn_match_oracle(kind, threads, phi):
+    # every leaf size and block size the autotuner can choose
     pts, ids, off = make_batch(SIZES)
-    b = psi.Batch(off, kind=kind, leaf_size=32, threads=threads)
+    b = psi.Batch(off, kind=kind, leaf_size=phi, threads=threads)
     b.build(T(pts), T(ids))
     q, qoff = queries(SIZES, pts, off, 2, 30, 5)
     gi, gd = b.knn(T(q), T(qoff), 10)
@@ -62,7 +64,7 @@ def test_batch_layout_and_knn_match_oracle(kind, threads):
     gi, gd = gi.cpu().numpy().view(np.uint32), gd.cpu().numpy()
     okind = O.SPAC_Z if kind == "spac_z" else O.SPAC_H
     for i, n in enumerate(SIZES):
-        o = O.Index(pts[off[i]:off[i + 1]], ids[off[i]:off[i + 1]], kind=okind, phi=32)
+        o = O.Index(pts[off[i]:off[i + 1]], ids[off[i]:off[i + 1]], kind=okind, phi=phi)
         lv = o.levels()
         gl = b.leaves(i)
         if n == 0:

@@ -1,7 +1,13 @@
 """Parity at the benchmark's full size (1e8 2D clustered points, SPaC-H, leaf
-size 32, the same calls bench.py times): sampled k-NN answers and range counts
-against the oracle's definitions over the raw point arrays, plus structural
-properties that hold at any size."""
+size 32, the same calls bench.py times).
+
+- The build's whole leaf layout (every leaf's count, box, separator and
+  points) and every summary level equal the oracle's canonical build.
+- After one 1e6-point insert and one 1e6-point delete, 10^4 sampled k-NN
+  answers out of the 1e7 queries, 200 sampled range counts and the sorted ids
+  of 200 sampled range-report boxes equal the oracle index of the live set.
+- Structural properties that hold at any size (counts add up, every leaf
+  within 1..2*phi, report offsets equal the counts)."""
 import numpy as np
 import pytest
 
@@ -11,6 +17,43 @@ from oracle import oracle as O  # noqa: E402
 from paper_2601_05347_gb300 import gen  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+
+def _layout_equal(ix, o):
+    """Leaf-by-leaf equality of a fresh build with the oracle's canonical one."""
+    lv = o.levels()
+    gl = ix.leaves()
+    assert ix.num_leaves == len(lv[0]["count"])
+    assert (gl["count"].cpu().numpy() == lv[0]["count"]).all()
+    assert (gl["lo"].cpu().numpy() == lv[0]["lo"]).all()
+    assert (gl["hi"].cpu().numpy() == lv[0]["hi"]).all()
+    assert (gl["sep_key"].cpu().numpy().view(np.uint64) == lv[0]["first_key"]).all()
+    assert (gl["sep_id"].cpu().numpy().view(np.uint32) == lv[0]["first_id"]).all()
+    del gl
+    gp = ix.points()
+    gk = gp["keys"].cpu().numpy().view(np.uint64)
+    gi = gp["ids"].cpu().numpy().view(np.uint32)
+    leaf = gp["leaf"].cpu().numpy()
+    ok, oi, opts = o.points()
+    # the export lists leaves in order; a fresh leaf holds its points in
+    # (key, id) order, so no re-sort is needed unless the kernel chose another
+    # order inside a leaf (then the sets per leaf must still agree)
+    if not ((gk == ok).all() and (gi == oi).all()):
+        order = np.lexsort((gi, gk, leaf))
+        gk, gi = gk[order], gi[order]
+        assert (gk == ok).all() and (gi == oi).all()
+        assert (gp["pts"].cpu().numpy()[order] == opts).all()
+    else:
+        assert (gp["pts"].cpu().numpy() == opts).all()
+    del gp, gk, gi, leaf, ok, oi, opts
+    nd = ix.nodes()
+    depth = nd["depth"].cpu().numpy()
+    cnt, lo, hi = nd["count"].cpu().numpy(), nd["lo"].cpu().numpy(), nd["hi"].cpu().numpy()
+    for lvl, want in enumerate(lv):
+        sel = depth == lvl
+        assert sel.sum() == len(want["count"])
+        assert (cnt[sel] == want["count"]).all()
+        assert (lo[sel] == want["lo"]).all() and (hi[sel] == want["hi"]).all()
 
 
 def test_full_size_build_update_query_sampled():
@@ -24,33 +67,40 @@ def test_full_size_build_update_query_sampled():
     dsel = gen.sample_without_replacement(n, 1_000_000, gen.config_seed(1, 2))
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else a).to(dev)
     ix = psi.Index(T(pts), T(ids), kind="spac_h", leaf_size=32)
+    o = O.Index(pts, ids, dim=2, kind=O.SPAC_H, phi=32, bits=30)
+    _layout_equal(ix, o)
     ix.insert(T(ins), T(ins_ids))
     nd = torch.zeros(1, dtype=torch.int64, device=dev)
     ix.delete(T(pts[dsel]), T(ids[dsel]), nd)
     ix.sync()
+    o.insert(ins, ins_ids)
+    assert o.delete(pts[dsel], ids[dsel]) == 1_000_000
     assert int(nd.item()) == 1_000_000
-    assert len(ix) == n
+    assert len(ix) == len(o) == n
     # structure at any size: counts add up, every leaf within 1..2*phi
-    lv = ix.leaves()
-    cnt = lv["count"].cpu().numpy()
+    cnt = ix.leaves()["count"].cpu().numpy()
     assert int(cnt.sum()) == n and cnt.min() >= 1 and cnt.max() <= 64
-    # the live set, for the sampled checks
-    keep = np.ones(n, bool)
-    keep[dsel] = False
-    live_p = np.concatenate([pts[keep], ins])
-    live_i = np.concatenate([ids[keep], ins_ids])
-    # 1e7 queries as in the benchmark; 6 sampled answers checked one by one
+    # 1e7 queries as in the benchmark; 1e4 sampled answers checked
     q = pts[gen.sample_with_replacement(n, 10_000_000, gen.config_seed(1, 3))]
     gi, gd = ix.knn(T(q), 10)
-    sample = gen.sample_with_replacement(len(q), 6, 12345)
-    oi, od = O.knn_brute_raw(live_p, live_i, q[sample], 10)
+    sample = gen.sample_without_replacement(len(q), 10_000, 12345)
+    oi, od = o.knn(q[sample], 10)
     assert (gi[T(sample)].cpu().numpy().view(np.uint32) == oi).all()
     assert (gd[T(sample)].cpu().numpy() == od).all()
+    # the oracle's own search agrees with brute force on a few of them
+    bi, bd = O.knn_brute_raw(*o.points()[2:0:-1], q[sample[:4]], 10)
+    assert (bi == oi[:4]).all() and (bd == od[:4]).all()
+    # 5e4 range boxes of about 1e3 points as in the benchmark; 200 sampled
     boxes = gen.centred_boxes(pts[gen.sample_with_replacement(n, 50_000, 7)], 8643, 30)
     gc = ix.range_count(T(boxes)).cpu().numpy()
-    bs = gen.sample_with_replacement(len(boxes), 6, 99)
-    assert (gc[bs] == O.range_count_brute_raw(live_p, boxes[bs])).all()
+    bs = gen.sample_without_replacement(len(boxes), 200, 99)
+    assert (gc[bs] == o.range_count(boxes[bs])).all()
     off, rid = ix.range_report(T(boxes))
     off = off.cpu().numpy()
+    rid = rid.cpu().numpy().view(np.uint32)
     assert (np.diff(off) == gc).all()
+    ooff, orid = o.range_report(boxes[bs])
+    for t, b in enumerate(bs):
+        got = np.sort(rid[off[b]:off[b + 1]])
+        assert (got == orid[ooff[t]:ooff[t + 1]]).all()
     ix.close()

@@ -310,13 +310,17 @@ def spac_invariants(ix):
     assert all((pair < nxt[leaf]) & ((pair >= sep[leaf]) | (leaf == 0)))
 
 
-@pytest.mark.parametrize("kind,dim,bits", [("spac_z", 2, 30), ("spac_h", 2, 30), ("porth", 2, 30), ("spac_h", 3, 21),
-                                           ("porth", 3, 21)])
-def test_updates_match_oracle(kind, dim, bits):
+@pytest.mark.parametrize("kind,dim,bits,phi", [("spac_z", 2, 30, 32), ("spac_h", 2, 30, 32), ("porth", 2, 30, 32),
+                                               ("spac_h", 3, 21, 32), ("porth", 3, 21, 32),
+                                               ("spac_h", 2, 30, 64), ("spac_z", 3, 21, 64), ("spac_z", 2, 30, 64),
+                                               ("spac_h", 3, 21, 64), ("porth", 3, 21, 64)])
+def test_updates_match_oracle(kind, dim, bits, phi):
+    # phi = 64: leaf blocks of 128 slots, so the update kernels run their
+    # four-rows-per-lane instances
     n = 50000
     p, ids = points(n, dim, bits, 41, clustered=True)
-    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
-    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=phi, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=phi, bits=bits)
     live_p, live_i = p, ids
     rng_seed = 5
     for step, (m_ins, m_del, ood) in enumerate([(5000, 3000, False), (20000, 1000, True), (100, 30000, False),
