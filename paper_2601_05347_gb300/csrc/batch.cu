@@ -688,6 +688,7 @@ static psi_status batch_knn(psi_batch *b, const int32_t *d_q, const int64_t *d_q
   seed.node_off = b->d_node_off;
   seed.phi = b->phi;
   seed.pkey = b->pool.pkey;
+  seed.pos = reinterpret_cast<uint32_t *>(r.keys == b->qk0 ? b->qk1 : b->qk0);  // the sort's free key buffer
   return run_knn_roots(tv, d_q, nq, k, r.vals, b->d_qroot, b->D, d_ids, d_d2, b->d_status, d_stats, s, seed);
 }
 

@@ -130,6 +130,9 @@ struct KnnSeed {
   // P-Orth: the pool is key-sorted and contiguous, slots [0, n_slots); the seed
   // is a slot range around the query's key
   int64_t n_slots = 0;
+  // scratch of nq entries (required with qkey): the seed leaf node (or slot)
+  // of each query in curve order, written by the k-NN call before its search
+  uint32_t *pos = nullptr;
 };
 
 // k-NN of nq queries, each starting at qroot[q] (or tv.root when qroot is

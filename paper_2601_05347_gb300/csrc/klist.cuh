@@ -148,6 +148,21 @@ __device__ __forceinline__ void warp_bitonic_clean(T &d, uint32_t &i) {
   }
 }
 
+// Fills an empty list from one candidate per lane (`in`: the lane holds one):
+// sorted across the warp, the first min(k, 32) become the list.
+template <int KPL, typename T>
+__device__ __forceinline__ void klist_fill(KList<KPL, T> &kl, bool in, T d2, uint32_t id, int k) {
+  const int lane = threadIdx.x & 31;
+  T cd = in ? d2 : DistInf<T>::v();
+  uint32_t ci = in ? id : 0xFFFFFFFFu;
+  warp_sort_pairs(cd, ci);
+  if (lane < k) {
+    kl.d[0] = cd;
+    kl.i[0] = ci;
+  }
+  kl.refresh_kth(k);
+}
+
 // Offers one candidate per lane (`in`: it beats the current k-th).  With more
 // than six entrants they are sorted across the warp and merged into the list
 // row by row: the row against the reversed carry gives, lane-wise, the 32

@@ -32,6 +32,7 @@ struct QueryOrder {
   const uint32_t *order = nullptr;
   const uint64_t *keys = nullptr;
   int key_shift = 0;
+  uint32_t *spare = nullptr;  // nq free words (the key buffer the sort left unused)
 };
 
 namespace {
@@ -91,7 +92,8 @@ struct KnnArgs {
 // list (klist_offer: in bulk when many enter at once, the seed leaves of a
 // query; one at a time otherwise).
 // Slots [s0, s0 + cnt), except those in [skip_lo, skip_hi) (already scanned).
-template <int D, int KPL>
+// EMPTY: the list is known to be empty (the first leaf a query scans).
+template <int D, int KPL, bool EMPTY = false>
 __device__ __forceinline__ void knn_scan_slots(const TreeView &t, uint32_t s0, int cnt, const int32_t *qc,
                                                KList<KPL> &kl, int k, uint32_t skip_lo = 1, uint32_t skip_hi = 0) {
   const int lane = threadIdx.x & 31;
@@ -107,66 +109,102 @@ __device__ __forceinline__ void knn_scan_slots(const TreeView &t, uint32_t s0, i
       d2 = 0;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const int64_t dd = (int64_t)t.px[d][slot] - qc[d];
-        d2 += dd * dd;
+        // both in [0, 2^31): the difference is exact in 32 bits, its square
+        // one widening multiply
+        const int32_t dd = t.px[d][slot] - qc[d];
+        d2 += (int64_t)dd * dd;
       }
     }
-    klist_offer(kl, valid && kl.admits(d2, id), d2, id, k);
+    if (EMPTY && b == 0)  // the list holds nothing yet: every point enters
+      klist_fill(kl, valid, d2, id, k);
+    else
+      klist_offer(kl, valid && kl.admits(d2, id), d2, id, k);
   }
 }
 
-template <int D, int KPL>
+template <int D, int KPL, bool EMPTY = false>
 __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, const int32_t *qc, KList<KPL> &kl,
                                               int k, uint32_t skip_lo = 1, uint32_t skip_hi = 0) {
-  knn_scan_slots<D, KPL>(t, t.ref[node], t.cnt[node], qc, kl, k, skip_lo, skip_hi);
+  knn_scan_slots<D, KPL, EMPTY>(t, t.ref[node], t.cnt[node], qc, kl, k, skip_lo, skip_hi);
 }
 
-// Monotone non-decreasing 32-bit image of a non-negative distance (its float
-// bits, rounded to nearest).  a <= b implies key(a) <= key(b), so skipping a
-// node whose key exceeds key(k-th distance) never skips one that could hold a
-// neighbour; it may keep a few that cannot, which costs time, not exactness.
-__device__ __forceinline__ uint32_t order_key(int64_t md) { return __float_as_uint((float)md); }
+// 32-bit image of a non-negative distance for pruning: the float bits of the
+// distance rounded up, built from its two 32-bit halves (a conversion from a
+// 64-bit integer would run on the FP64 unit, which is very slow on this GPU).
+// A child key is its box distance rounded down, so a child whose key exceeds
+// the image of the k-th distance is farther than that distance: pruning by
+// keys never skips a node that could hold a neighbour; it may keep a few that
+// cannot, which costs time, not exactness.
+__device__ __forceinline__ uint32_t order_key(int64_t md) {
+  const uint32_t hi = (uint32_t)((uint64_t)md >> 32), lo = (uint32_t)md;
+  return __float_as_uint(__fmaf_ru(__uint2float_ru(hi), 4294967296.0f, __uint2float_ru(lo)));
+}
 
 struct KnnStats {
   unsigned long long *c;  // [0] internal nodes expanded, [1] leaves scanned, [2] points scanned, [3] queries
 };
 
-constexpr int MAXLVL = 33;  // tree depth bound (P-Orth: 31 levels below the root)
+// Per-warp depth-first stack of the k-NN search: an expanded node pushes at
+// most F - 1 more entries than it pops, so depth x 31 + 32 entries suffice
+// (SPaC: 7 levels at 1e9 points; P-Orth: at most 2^D children per level).
+constexpr int KSTACK = 256;
+constexpr uint32_t KLEAF = 0x80000000u;  // stack entry names a leaf
 
-// Last leaf j in [0, L) whose first key (>> shift) is <= key, or 0: a 32-ary
-// search by the warp, one ballot over 32 evenly spaced leaves per round.
+// Last position p in [0, n) whose first key (>> shift) is <= key, or 0 when
+// the key precedes every position (binary search by one thread).
 template <typename FirstKey>
-__device__ __forceinline__ int64_t seed_leaf(FirstKey first_key, int64_t L, uint64_t key, int shift) {
-  const int lane = threadIdx.x & 31;
-  int64_t lo = 0, hi = L;  // the answer lies in [lo, hi)
-  while (hi - lo > 1) {
-    const int64_t step = (hi - lo + 31) >> 5;
-    const int64_t p = lo + (int64_t)lane * step;
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, p < hi && (first_key(p) >> shift) <= key);
-    if (m == 0) return lo;  // only when lo == 0: the key precedes every leaf
-    lo += (int64_t)(31 - __clz(m)) * step;
-    hi = min(hi, lo + step);
+__device__ __forceinline__ int64_t seed_search(FirstKey first_key, int64_t n, uint64_t key, int shift) {
+  int64_t lo = 0, hi = n;  // first position whose first key is greater
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((first_key(mid) >> shift) <= key)
+      lo = mid + 1;
+    else
+      hi = mid;
   }
-  return lo;
+  return lo > 0 ? lo - 1 : 0;
 }
 
-// One warp per query: depth-first search that always enters the nearest
-// not-yet-visited child (Appendix "Implementation Details": children in
-// increasing box distance).  Each level of the current path keeps, in shared
-// memory, its children's distance keys and a bitmask of children still to
-// visit; one ballot prunes every remaining child farther than the current
-// k-th distance, one reduce picks the nearest.
+// Seed position of every query (queries in curve order), one thread each:
+// SPaC, the node of the last leaf of the query's index whose first key is at
+// most the query's key; P-Orth, the last pool slot with that property.  Many
+// independent searches in flight hide the dependent loads that one warp-wide
+// search per query would wait on.
+__global__ void k_knn_seed(const KnnSeed sd, const uint32_t *ref, const uint32_t *order, int64_t nq, uint32_t *pos) {
+  for (int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < nq; qi += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = sd.qkey[qi] & sd.qkey_mask;
+    int64_t p = 0;
+    if (sd.pkey && sd.n_slots > 0) {
+      p = seed_search([&](int64_t x) { return sd.pkey[x]; }, sd.n_slots, key, sd.key_shift);
+    } else if (sd.qseg) {
+      const int64_t q = order ? (int64_t)order[qi] : qi;
+      const int sg = sd.qseg[q];
+      const int64_t lb = sd.node_off[sg];
+      const int64_t L = (sd.off[sg + 1] - sd.off[sg] + sd.phi - 1) / sd.phi;
+      if (L > 0) p = lb + seed_search([&](int64_t x) { return sd.pkey[ref[lb + x]]; }, L, key, sd.key_shift);
+    } else if (sd.L > 0) {
+      p = seed_search([&](int64_t x) { return sd.sep_key[x]; }, sd.L, key, sd.key_shift);
+    }
+    pos[qi] = (uint32_t)p;
+  }
+}
+
+// One warp per query: depth-first search over a per-warp stack in shared
+// memory.  Expanding a node evaluates its children one per lane and pushes
+// those not farther than the current k-th distance, the nearest one on top, so
+// the search enters the nearest child first (Appendix "Implementation
+// Details": children in increasing box distance) and takes its siblings later,
+// each re-checked against the k-th distance of that moment when it is popped.
 // Seed (SPaC): the leaf that holds the query's own curve position is scanned
 // first.  SPaC leaves are consecutive runs of the curve and their boxes
 // overlap, so the nearest box is often not the leaf around the query; the
 // curve neighbours make the k-th distance nearly final before the search
-// starts, and the search then skips the seed leaf.
+// starts (so the order of the later pops matters little), and the search then
+// skips the seed leaves.
 template <int D, int KPL, bool STATS>
 __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
-  __shared__ uint32_t s_key[QW][MAXLVL][32];
-  __shared__ uint32_t s_c0[QW][MAXLVL];
-  __shared__ uint32_t s_mask[QW][MAXLVL];
-  __shared__ uint32_t s_leaf[QW][MAXLVL];
+  // (node | KLEAF, child key, node's ref, leaf: its count / internal: its children)
+  __shared__ uint4 s_stk[QW][KSTACK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nw = (int64_t)gridDim.x * QW;
   const TreeView &t = a.t;
@@ -195,26 +233,28 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     const bool by_slots = sd.pkey && sd.n_slots > 0;
     uint32_t sk_lo = 1, sk_hi = 0;
     if (sd.qkey && root >= 0) {
-      const uint64_t key = sd.qkey[qi] & sd.qkey_mask;
+      const int64_t pos = sd.pos[qi];  // k_knn_seed
       if (by_slots) {
-        const int64_t pos = seed_leaf([&](int64_t p) { return sd.pkey[p]; }, sd.n_slots, key, sd.key_shift);
         const int64_t want = min((int64_t)32 * KPL, sd.n_slots);
         const int64_t lo = max((int64_t)0, min(pos - want / 2, sd.n_slots - want));
         sk_lo = (uint32_t)lo;
         sk_hi = (uint32_t)(lo + want);
-        knn_scan_slots<D, KPL>(t, sk_lo, (int)want, qc, kl, a.k);
+        knn_scan_slots<D, KPL, true>(t, sk_lo, (int)want, qc, kl, a.k);
         if (STATS) n_pts += want;
       } else if (L > 0) {
-        const int64_t j = lb + (sd.sep_key ? seed_leaf([&](int64_t p) { return sd.sep_key[p]; }, L, key, sd.key_shift)
-                                           : seed_leaf([&](int64_t p) { return sd.pkey[t.ref[lb + p]]; }, L, key,
-                                                       sd.key_shift));
+        const int64_t j = pos;
         const int64_t le = lb + L;
-        int64_t got = 0;
+        knn_scan_leaf<D, KPL, true>(t, (uint32_t)j, qc, kl, a.k);
+        int64_t got = t.cnt[j];
+        if (STATS) {
+          ++n_leaf;
+          n_pts += got;
+        }
         s_lo = j;
-        s_hi = j - 1;
+        s_hi = j;
         while (got < a.k && (s_lo > lb || s_hi + 1 < le)) {
           int64_t nx;
-          if (s_hi < s_lo || (s_hi + 1 < le && (s_lo == lb || s_hi - j <= j - s_lo)))
+          if (s_hi + 1 < le && (s_lo == lb || s_hi - j <= j - s_lo))
             nx = ++s_hi;
           else
             nx = --s_lo;
@@ -229,61 +269,69 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     }
     auto seeded = [&](uint32_t leaf) { return !by_slots && (int64_t)leaf >= s_lo && (int64_t)leaf <= s_hi; };
     uint32_t kdk = order_key(kl.kd);
-    auto expand = [&](uint32_t node, int lvl) {
-      const int nk = t.kids[node];
-      const uint32_t c0 = t.ref[node];
+    int sp = 0;
+    // Pushes the children [c0, c0 + nk) that may hold a neighbour.  Each lane
+    // loads its child's reference and count with its box, so that a popped
+    // entry needs no further load before its own children or points are read.
+    auto expand = [&](uint32_t c0, int nk) {
       const uint32_t c = c0 + (uint32_t)lane;
-      uint32_t key = 0xFFFFFFFFu;
+      uint32_t key = 0xFFFFFFFFu;  // above any k-th distance key
       bool leafc = false;
+      uint32_t cref = 0;
+      int ccnt = 0;
       if (lane < nk) {  // every node of every layout holds a point
+        cref = t.ref[c];
+        if (a.leaf_limit >= 0) {
+          leafc = (int64_t)c < a.leaf_limit;
+          ccnt = leafc ? t.cnt[c] : t.kids[c];
+        } else {
+          const int ck = t.kids[c], cn = t.cnt[c];
+          leafc = ck == 0;
+          ccnt = leafc ? cn : ck;
+        }
         key = box_key<D>(t, c, qc);
-        leafc = a.leaf_limit >= 0 ? (int64_t)c < a.leaf_limit : t.kids[c] == 0;
       }
-      s_key[w][lvl][lane] = key;
-      const uint32_t mk = __ballot_sync(0xFFFFFFFFu, key <= kdk);
-      const uint32_t lf = __ballot_sync(0xFFFFFFFFu, leafc);
-      if (lane == 0) {
-        s_c0[w][lvl] = c0;
-        s_mask[w][lvl] = mk;
-        s_leaf[w][lvl] = lf;
-      }
+      const bool in = key <= kdk;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, in);
       if (STATS) ++n_int;
+      if (m == 0) return;
+      const int n = __popc(m);
+      if (sp + n > KSTACK) {  // cannot happen within the depth bound above
+        if (lane == 0) atomicOr(a.status, ST_STACK);
+        return;
+      }
+      // the nearest survivor (lowest lane on ties) takes the top slot, the
+      // survivor that held the top slot takes its place
+      const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, in ? key : 0xFFFFFFFFu);
+      const int win = __ffs(__ballot_sync(0xFFFFFFFFu, in && key == mn)) - 1;
+      int pos = __popc(m & lanemask_lt());
+      if (lane == win)
+        pos = n - 1;
+      else if (pos == n - 1)
+        pos = __popc(m & ((1u << win) - 1u));
+      __syncwarp();
+      if (in) s_stk[w][sp + pos] = make_uint4(c | (leafc ? KLEAF : 0u), key, cref, (uint32_t)ccnt);
+      sp += n;
       __syncwarp();
     };
     if (root >= 0) {
       if (t.kids[root] == 0) {
         if (!seeded((uint32_t)root)) knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k, sk_lo, sk_hi);
       } else {
-        int lvl = 0;
-        expand((uint32_t)root, 0);
-        while (lvl >= 0) {
-          const uint32_t key = s_key[w][lvl][lane];
-          const uint32_t m = s_mask[w][lvl] & __ballot_sync(0xFFFFFFFFu, key <= kdk);
-          if (m == 0) {
-            --lvl;
-            continue;
-          }
-          const bool in = (m >> lane) & 1u;
-          const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, in ? key : 0xFFFFFFFFu);
-          const int src = __ffs(__ballot_sync(0xFFFFFFFFu, in && key == mn)) - 1;
-          const uint32_t child = s_c0[w][lvl] + (uint32_t)src;
-          const bool is_leaf = (s_leaf[w][lvl] >> src) & 1u;
-          __syncwarp();
-          if (lane == 0) s_mask[w][lvl] = m & ~(1u << src);
-          __syncwarp();
-          if (is_leaf) {
-            if (seeded(child)) continue;  // scanned as a seed
-            knn_scan_leaf<D, KPL>(t, child, qc, kl, a.k, sk_lo, sk_hi);
+        expand(t.ref[root], t.kids[root]);
+        while (sp > 0) {
+          const uint4 e = s_stk[w][--sp];
+          if (e.y > kdk) continue;  // farther than the k-th distance found since the push
+          if (e.x & KLEAF) {
+            if (seeded(e.x & ~KLEAF)) continue;  // scanned as a seed
+            knn_scan_slots<D, KPL>(t, e.z, (int)e.w, qc, kl, a.k, sk_lo, sk_hi);
             kdk = order_key(kl.kd);
             if (STATS) {
               ++n_leaf;
-              n_pts += t.cnt[child];
+              n_pts += e.w;
             }
-          } else if (lvl + 1 < MAXLVL) {
-            ++lvl;
-            expand(child, lvl);
-          } else if (lane == 0) {
-            atomicOr(a.status, ST_STACK);
+          } else {
+            expand(e.z, (int)e.w);
           }
         }
       }
@@ -435,8 +483,16 @@ __global__ __launch_bounds__(1024) void k_sort_segments(const int64_t *offsets, 
   }
 }
 
-int query_grid(int64_t nq) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nq, QW), (int64_t)num_sms() * 16));
+// Grid of a grid-stride query kernel: the blocks that are resident at once
+// (a larger grid would run as a second, partly idle wave).
+template <typename Kern>
+int resident_query_grid(Kern kern, int64_t nq) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, QW * 32, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nq, QW), (int64_t)num_sms() * per_sm));
 }
 
 }  // namespace
@@ -463,6 +519,7 @@ psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, QueryO
   qo.order = r.vals;
   qo.keys = r.keys;
   qo.key_shift = e.key_shift;
+  qo.spare = reinterpret_cast<uint32_t *>(r.keys == qo.k0.p ? qo.k1.p : qo.k0.p);
   return PSI_OK;
 }
 
@@ -472,14 +529,23 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
   if (nq == 0) return PSI_OK;
   KnnArgs a{tv, q, nq, k, order, qroot, seed, leaf_limit, out_id, out_d2, status};
   KnnStats stats{d_stats};
-  const int g = query_grid(nq);
+  if (seed.qkey) {
+    if (!seed.pos) {
+      set_error("k-NN seed without its scratch");
+      return PSI_ERR_INVALID;
+    }
+    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nq, 256), (int64_t)num_sms() * 16));
+    PSI_LAUNCH(k_knn_seed, gs, 256, 0, s, seed, tv.ref, order, nq, seed.pos);
+  }
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
-#define KNN_CASE(DD, KK)                                                                     \
-  do {                                                                                       \
-    if (d_stats)                                                                             \
-      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn<DD, KK, true>), g, QW * 32, 0, s, a, stats);   \
-    else                                                                                     \
-      PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK, false>), g, QW * 32, 0, s, a, stats);        \
+#define KNN_CASE(DD, KK)                                                                           \
+  do {                                                                                             \
+    if (d_stats)                                                                                   \
+      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn<DD, KK, true>), resident_query_grid(k_knn<DD, KK, true>, nq), \
+                       QW * 32, 0, s, a, stats);                                                   \
+    else                                                                                           \
+      PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK, false>), resident_query_grid(k_knn<DD, KK, false>, nq),     \
+                       QW * 32, 0, s, a, stats);                                                   \
   } while (0)
   if (D == 2) {
     if (kpl == 1) KNN_CASE(2, 1);
@@ -508,6 +574,7 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
     seed.qkey = qo.keys;
     seed.L = ix->L;
     seed.key_shift = qo.key_shift;
+    seed.pos = qo.spare;
     if (ix->cfg.kind == PSI_PORTH) {
       // P-Orth leaves do not overlap and the search is near its floor; the
       // seed pays off only in cutting single insertions into long lists
@@ -525,11 +592,12 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
 psi_status run_range_count(const psi_index *ix, const int32_t *boxes, int64_t nq, int64_t *counts, cudaStream_t s) {
   if (nq == 0) return PSI_OK;
   RangeArgs a{ix->view(), boxes, nq, counts, nullptr, nullptr, ix->d_status};
-  const int g = query_grid(nq);
   if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_range_count", (k_range<2, false>), g, QW * 32, 0, s, a);
+    PSI_LAUNCH_NAMED("k_range_count", (k_range<2, false>), resident_query_grid(k_range<2, false>, nq), QW * 32, 0, s,
+                     a);
   else
-    PSI_LAUNCH_NAMED("k_range_count", (k_range<3, false>), g, QW * 32, 0, s, a);
+    PSI_LAUNCH_NAMED("k_range_count", (k_range<3, false>), resident_query_grid(k_range<3, false>, nq), QW * 32, 0, s,
+                     a);
   PSI_CK(cudaGetLastError());
   return PSI_OK;
 }
@@ -538,11 +606,10 @@ psi_status run_range_emit(const psi_index *ix, const int32_t *boxes, int64_t nq,
                           uint32_t *ids, bool sorted, cudaStream_t s) {
   if (nq == 0) return PSI_OK;
   RangeArgs a{ix->view(), boxes, nq, nullptr, offsets, ids, ix->d_status};
-  const int g = query_grid(nq);
   if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_range_emit", (k_range<2, true>), g, QW * 32, 0, s, a);
+    PSI_LAUNCH_NAMED("k_range_emit", (k_range<2, true>), resident_query_grid(k_range<2, true>, nq), QW * 32, 0, s, a);
   else
-    PSI_LAUNCH_NAMED("k_range_emit", (k_range<3, true>), g, QW * 32, 0, s, a);
+    PSI_LAUNCH_NAMED("k_range_emit", (k_range<3, true>), resident_query_grid(k_range<3, true>, nq), QW * 32, 0, s, a);
   if (sorted)
     PSI_LAUNCH(k_sort_segments, (int)std::min<int64_t>(nq, (int64_t)num_sms() * 2), 1024, 0, s, offsets, nq, ids);
   PSI_CK(cudaGetLastError());
