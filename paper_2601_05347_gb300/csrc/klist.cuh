@@ -163,6 +163,46 @@ __device__ __forceinline__ void klist_fill(KList<KPL, T> &kl, bool in, T d2, uin
   kl.refresh_kth(k);
 }
 
+// Ascending warp bitonic sort of one 64-bit key per lane.
+__device__ __forceinline__ void warp_sort_u64(uint64_t &x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+      if (keep_min == (o < x)) x = o;
+    }
+  }
+}
+
+// Integer distances: when every candidate's distance is below 2^32 - 1 (the
+// common case for a query's first leaf), (d2 << 32 | id) orders the pairs
+// exactly as (d2, id) does, and one 64-bit key per lane sorts faster than a
+// (distance, id) pair.
+template <int KPL>
+__device__ __forceinline__ void klist_fill(KList<KPL, int64_t> &kl, bool in, int64_t d2, uint32_t id, int k) {
+  const int lane = threadIdx.x & 31;
+  if (__all_sync(0xFFFFFFFFu, !in || (uint64_t)d2 < 0xFFFFFFFFull)) {
+    uint64_t x = in ? ((uint64_t)d2 << 32 | id) : ~0ull;
+    warp_sort_u64(x);
+    if (lane < k) {
+      kl.d[0] = x == ~0ull ? DistInf<int64_t>::v() : (int64_t)(x >> 32);
+      kl.i[0] = x == ~0ull ? 0xFFFFFFFFu : (uint32_t)x;
+    }
+  } else {
+    int64_t cd = in ? d2 : DistInf<int64_t>::v();
+    uint32_t ci = in ? id : 0xFFFFFFFFu;
+    warp_sort_pairs(cd, ci);
+    if (lane < k) {
+      kl.d[0] = cd;
+      kl.i[0] = ci;
+    }
+  }
+  kl.refresh_kth(k);
+}
+
 // Offers one candidate per lane (`in`: it beats the current k-th).  With more
 // than six entrants they are sorted across the warp and merged into the list
 // row by row: the row against the reversed carry gives, lane-wise, the 32

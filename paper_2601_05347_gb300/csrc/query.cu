@@ -148,7 +148,6 @@ struct KnnStats {
 // most F - 1 more entries than it pops, so depth x 31 + 32 entries suffice
 // (SPaC: 7 levels at 1e9 points; P-Orth: at most 2^D children per level).
 constexpr int KSTACK = 256;
-constexpr uint32_t KLEAF = 0x80000000u;  // stack entry names a leaf
 
 // Last position p in [0, n) whose first key (>> shift) is <= key, or 0 when
 // the key precedes every position (binary search by one thread).
@@ -203,7 +202,7 @@ __global__ void k_knn_seed(const KnnSeed sd, const uint32_t *ref, const uint32_t
 // skips the seed leaves.
 template <int D, int KPL, bool STATS>
 __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
-  // (node | KLEAF, child key, node's ref, leaf: its count / internal: its children)
+  // internal nodes still to visit: (node, key, first child, children)
   __shared__ uint4 s_stk[QW][KSTACK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nw = (int64_t)gridDim.x * QW;
@@ -267,12 +266,17 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
         }
       }
     }
-    auto seeded = [&](uint32_t leaf) { return !by_slots && (int64_t)leaf >= s_lo && (int64_t)leaf <= s_hi; };
+    // seed leaves as a node range [slo, shi] (empty: slo > shi)
+    const uint32_t slo = by_slots || s_hi < s_lo ? 1u : (uint32_t)s_lo;
+    const uint32_t shi = by_slots || s_hi < s_lo ? 0u : (uint32_t)s_hi;
     uint32_t kdk = order_key(kl.kd);
     int sp = 0;
-    // Pushes the children [c0, c0 + nk) that may hold a neighbour.  Each lane
-    // loads its child's reference and count with its box, so that a popped
-    // entry needs no further load before its own children or points are read.
+    // Children [c0, c0 + nk) of an expanded node: the internal ones that may
+    // hold a neighbour are pushed (the nearest on top); the leaves that may
+    // are scanned at once, nearest first, each re-checked against the k-th
+    // distance left by the ones before it.  Each lane loads its child's
+    // reference and count with its box, so a popped entry needs no further
+    // load before its own children are read.
     auto expand = [&](uint32_t c0, int nk) {
       const uint32_t c = c0 + (uint32_t)lane;
       uint32_t key = 0xFFFFFFFFu;  // above any k-th distance key
@@ -290,49 +294,70 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
           ccnt = leafc ? cn : ck;
         }
         key = box_key<D>(t, c, qc);
+        if (leafc && c >= slo && c <= shi) key = 0xFFFFFFFFu;  // scanned as a seed
       }
       const bool in = key <= kdk;
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, in);
       if (STATS) ++n_int;
-      if (m == 0) return;
-      const int n = __popc(m);
-      if (sp + n > KSTACK) {  // cannot happen within the depth bound above
-        if (lane == 0) atomicOr(a.status, ST_STACK);
-        return;
+      const uint32_t mi = __ballot_sync(0xFFFFFFFFu, in && !leafc);
+      uint32_t ml = __ballot_sync(0xFFFFFFFFu, in && leafc);
+      if (mi) {
+        const int n = __popc(mi);
+        if (sp + n > KSTACK) {  // cannot happen within the depth bound above
+          if (lane == 0) atomicOr(a.status, ST_STACK);
+        } else {
+          // the nearest internal survivor (lowest lane on ties) takes the top
+          // slot, the one that held the top slot takes its place
+          const bool ii = (mi >> lane) & 1u;
+          const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, ii ? key : 0xFFFFFFFFu);
+          const int win = __ffs(__ballot_sync(0xFFFFFFFFu, ii && key == mn)) - 1;
+          int pos = __popc(mi & lanemask_lt());
+          if (lane == win)
+            pos = n - 1;
+          else if (pos == n - 1)
+            pos = __popc(mi & ((1u << win) - 1u));
+          __syncwarp();
+          if (ii) s_stk[w][sp + pos] = make_uint4(c, key, cref, (uint32_t)ccnt);
+          sp += n;
+          __syncwarp();
+        }
       }
-      // the nearest survivor (lowest lane on ties) takes the top slot, the
-      // survivor that held the top slot takes its place
-      const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, in ? key : 0xFFFFFFFFu);
-      const int win = __ffs(__ballot_sync(0xFFFFFFFFu, in && key == mn)) - 1;
-      int pos = __popc(m & lanemask_lt());
-      if (lane == win)
-        pos = n - 1;
-      else if (pos == n - 1)
-        pos = __popc(m & ((1u << win) - 1u));
-      __syncwarp();
-      if (in) s_stk[w][sp + pos] = make_uint4(c | (leafc ? KLEAF : 0u), key, cref, (uint32_t)ccnt);
-      sp += n;
-      __syncwarp();
+      while (ml) {
+        const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, (ml >> lane) & 1u ? key : 0xFFFFFFFFu);
+        if (mn > kdk) break;  // every remaining leaf is farther than the k-th distance
+        const int src = __ffs(__ballot_sync(0xFFFFFFFFu, ((ml >> lane) & 1u) && key == mn)) - 1;
+        ml &= ~(1u << src);
+        const uint32_t lref = __shfl_sync(0xFFFFFFFFu, cref, src);
+        const int lcnt = __shfl_sync(0xFFFFFFFFu, ccnt, src);
+        knn_scan_slots<D, KPL>(t, lref, lcnt, qc, kl, a.k, sk_lo, sk_hi);
+        kdk = order_key(kl.kd);
+        if (STATS) {
+          ++n_leaf;
+          n_pts += lcnt;
+        }
+      }
     };
     if (root >= 0) {
       if (t.kids[root] == 0) {
-        if (!seeded((uint32_t)root)) knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k, sk_lo, sk_hi);
+        if (!((uint32_t)root >= slo && (uint32_t)root <= shi))
+          knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k, sk_lo, sk_hi);
       } else {
-        expand(t.ref[root], t.kids[root]);
-        while (sp > 0) {
-          const uint4 e = s_stk[w][--sp];
-          if (e.y > kdk) continue;  // farther than the k-th distance found since the push
-          if (e.x & KLEAF) {
-            if (seeded(e.x & ~KLEAF)) continue;  // scanned as a seed
-            knn_scan_slots<D, KPL>(t, e.z, (int)e.w, qc, kl, a.k, sk_lo, sk_hi);
-            kdk = order_key(kl.kd);
-            if (STATS) {
-              ++n_leaf;
-              n_pts += e.w;
+        // the root as the first entry: one call site keeps `expand` inlined
+        uint32_t c0 = t.ref[root];
+        int nk = t.kids[root];
+        for (;;) {
+          expand(c0, nk);
+          uint4 e = make_uint4(0, 0, 0, 0);
+          bool more = false;
+          while (sp > 0) {
+            e = s_stk[w][--sp];
+            if (e.y <= kdk) {  // else farther than the k-th distance found since the push
+              more = true;
+              break;
             }
-          } else {
-            expand(e.z, (int)e.w);
           }
+          if (!more) break;
+          c0 = e.z;
+          nk = (int)e.w;
         }
       }
     }
