@@ -227,13 +227,15 @@ psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n,
 
 /* ---- Instrumentation ---------------------------------------------------- */
 
-/* psi_knn with traversal counters: d_stats (device, 4 x uint64) receives the
- * number of internal nodes expanded, leaves scanned, points scanned and
- * queries answered.  Same results as psi_knn; slower (atomic counters). */
+/* psi_knn with traversal counters: d_stats (device, 5 x uint64) receives the
+ * number of internal nodes expanded, leaves scanned, points scanned, queries
+ * answered and child descriptors read (children evaluated by the expanded
+ * nodes).  Same results as psi_knn; slower (atomic counters). */
 psi_status psi_knn_instrumented(const psi_index *ix, const int32_t *d_q, int64_t q, int32_t k, uint32_t *d_ids,
                                 int64_t *d_d2, uint64_t *d_stats, void *stream);
 
-/* psi_batch_knn with the same traversal counters (summed over all indexes). */
+/* psi_batch_knn with the same five traversal counters (summed over all
+ * indexes); d_stats must be zeroed by the caller. */
 psi_status psi_batch_knn_instrumented(psi_batch *b, const int32_t *d_q, const int64_t *d_qoffsets, int64_t nq,
                                       int32_t k, uint32_t *d_ids, int64_t *d_d2, uint64_t *d_stats, void *stream);
 

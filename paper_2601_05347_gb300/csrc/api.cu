@@ -304,7 +304,7 @@ psi_status psi_knn_instrumented(const psi_index *ix, const int32_t *d_q, int64_t
     return PSI_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  PSI_CK(cudaMemsetAsync(d_stats, 0, 4 * sizeof(uint64_t), s));
+  PSI_CK(cudaMemsetAsync(d_stats, 0, 5 * sizeof(uint64_t), s));
   return run_knn(ix, d_q, q, k, d_ids, d_d2, (unsigned long long *)d_stats, s);
 }
 

@@ -49,16 +49,27 @@ constexpr uint32_t INSIDE = 0x80000000u;
 // that distance rounded to nearest, so comparing float bits never prunes a box
 // that holds a neighbour.
 template <int D>
-__device__ __forceinline__ uint32_t box_key(const TreeView &t, uint32_t node, const int32_t *qc) {
+__device__ __forceinline__ uint32_t box_key_of(const int32_t *lo, const int32_t *hi, const int32_t *qc) {
   float s = 0.0f;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    const int32_t lo = t.lo[d][node], hi = t.hi[d][node], q = qc[d];
-    const int32_t g = q < lo ? lo - q : (q > hi ? q - hi : 0);
+    const int32_t q = qc[d];
+    const int32_t g = q < lo[d] ? lo[d] - q : (q > hi[d] ? q - hi[d] : 0);
     const float gf = __int2float_rd(g);
     s = __fadd_rd(s, __fmul_rd(gf, gf));
   }
   return __float_as_uint(s);
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t box_key(const TreeView &t, uint32_t node, const int32_t *qc) {
+  int32_t lo[D], hi[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    lo[d] = t.lo[d][node];
+    hi[d] = t.hi[d][node];
+  }
+  return box_key_of<D>(lo, hi, qc);
 }
 
 // 0: disjoint, 1: straddles, 2: node box inside the query box.
@@ -141,13 +152,17 @@ __device__ __forceinline__ uint32_t order_key(int64_t md) {
 }
 
 struct KnnStats {
-  unsigned long long *c;  // [0] internal nodes expanded, [1] leaves scanned, [2] points scanned, [3] queries
+  // [0] internal nodes expanded, [1] leaves scanned, [2] points scanned, [3] queries,
+  // [4] child descriptors read (children evaluated by the expansions)
+  unsigned long long *c;
 };
 
 // Per-warp depth-first stack of the k-NN search: an expanded node pushes at
 // most F - 1 more entries than it pops, so depth x 31 + 32 entries suffice
 // (SPaC: 7 levels at 1e9 points; P-Orth: at most 2^D children per level).
 constexpr int KSTACK = 256;
+// Queries per warp of the grouped k-NN kernel (k <= 32, queries in curve order).
+constexpr int kGroup = 2;
 
 // Last position p in [0, n) whose first key (>> shift) is <= key, or 0 when
 // the key precedes every position (binary search by one thread).
@@ -207,7 +222,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nw = (int64_t)gridDim.x * QW;
   const TreeView &t = a.t;
-  unsigned long long n_int = 0, n_leaf = 0, n_pts = 0;
+  unsigned long long n_int = 0, n_leaf = 0, n_pts = 0, n_kids = 0;
   for (int64_t qi = (int64_t)blockIdx.x * QW + w; qi < a.nq; qi += nw) {
     const int64_t q = a.order ? (int64_t)a.order[qi] : qi;
     int32_t qc[D];
@@ -297,7 +312,10 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
         if (leafc && c >= slo && c <= shi) key = 0xFFFFFFFFu;  // scanned as a seed
       }
       const bool in = key <= kdk;
-      if (STATS) ++n_int;
+      if (STATS) {
+        ++n_int;
+        n_kids += nk;
+      }
       const uint32_t mi = __ballot_sync(0xFFFFFFFFu, in && !leafc);
       uint32_t ml = __ballot_sync(0xFFFFFFFFu, in && leafc);
       if (mi) {
@@ -375,6 +393,231 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     atomicAdd(&stats.c[0], n_int);
     atomicAdd(&stats.c[1], n_leaf);
     atomicAdd(&stats.c[2], n_pts);
+    atomicAdd(&stats.c[4], n_kids);
+  }
+}
+
+// Scan one leaf for the queries of a group whose bit is set in qmask (warp-
+// uniform): every lane loads one point once and offers it to each of those
+// queries' lists.  FILL: the lists are known to be empty (the group's first
+// leaf).
+template <int D, int G, bool FILL>
+__device__ __forceinline__ void knn_scan_group(const TreeView &t, uint32_t s0, int cnt, const int32_t (&qc)[G][D],
+                                               KList<1> (&kl)[G], int k, uint32_t qmask) {
+  const int lane = threadIdx.x & 31;
+  for (int b = 0; b < cnt; b += 32) {
+    const int s = b + lane;
+    const bool valid = s < cnt;
+    int32_t p[D];
+    uint32_t id = 0xFFFFFFFFu;
+    if (valid) {
+      const uint32_t slot = s0 + (uint32_t)s;
+      id = t.pid[slot];
+#pragma unroll
+      for (int d = 0; d < D; ++d) p[d] = t.px[d][slot];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (!((qmask >> g) & 1u)) continue;
+      int64_t d2 = INT64_MAX;
+      if (valid) {
+        d2 = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int32_t dd = p[d] - qc[g][d];  // exact: both in [0, 2^31)
+          d2 += (int64_t)dd * dd;
+        }
+      }
+      if (FILL && b == 0)
+        klist_fill(kl[g], valid, d2, id, k);
+      else
+        klist_offer(kl[g], valid && kl[g].admits(d2, id), d2, id, k);
+    }
+  }
+}
+
+// k-NN for k <= 32 with G consecutive queries (in curve order) per warp.
+// Neighbouring queries visit nearly the same nodes and leaves, so the group
+// shares one depth-first traversal: each child box is loaded once and tested
+// against every query of the group (a child is needed if some query's k-th
+// distance admits it), and each leaf's points are loaded once and offered to
+// the lists of the queries that need the leaf.  Per query the result is the
+// same as k_knn's: exact (distance, id) order, each query pruned by its own
+// k-th distance.  Seeds (SPaC): the distinct seed leaves of the group's
+// queries are scanned first, for all of them.
+template <int D, int G, bool STATS>
+__global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats) {
+  __shared__ uint2 s_stk[QW][KSTACK];  // internal nodes still to visit: (first child, children)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const TreeView &t = a.t;
+  const KnnSeed &sd = a.seed;
+  const int64_t ngroups = (a.nq + G - 1) / G;
+  unsigned long long n_int = 0, n_leaf = 0, n_pts = 0, n_kids = 0;
+  for (int64_t gi = (int64_t)blockIdx.x * QW + w; gi < ngroups; gi += (int64_t)gridDim.x * QW) {
+    const int64_t qi0 = gi * G;
+    const int ng = (int)min((int64_t)G, a.nq - qi0);
+    int32_t qc[G][D];
+    uint32_t seed[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t qi = qi0 + min(g, ng - 1);  // a short last group repeats its last query
+      const int64_t q = a.order ? (int64_t)a.order[qi] : qi;
+#pragma unroll
+      for (int d = 0; d < D; ++d) qc[g][d] = a.q[q * D + d];
+      seed[g] = sd.qkey ? sd.pos[qi] : 0xFFFFFFFFu;
+    }
+    KList<1> kl[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) kl[g].init();
+    const uint32_t all = (1u << G) - 1u;
+    const int32_t root = t.root;
+    if (sd.qkey && root >= 0) {
+      // the distinct seed leaves (positions are non-decreasing in curve order)
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if (g > 0 && seed[g] == seed[g - 1]) continue;
+        const uint32_t j = seed[g];
+        if (g == 0)
+          knn_scan_group<D, G, true>(t, t.ref[j], t.cnt[j], qc, kl, a.k, all);
+        else
+          knn_scan_group<D, G, false>(t, t.ref[j], t.cnt[j], qc, kl, a.k, all);
+        if (STATS) {
+          ++n_leaf;
+          n_pts += t.cnt[j];
+        }
+      }
+    }
+    uint32_t kdk[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) kdk[g] = order_key(kl[g].kd);
+    int sp = 0;
+    // Children [c0, c0 + nk): the internal ones some query may need are pushed
+    // (the one nearest to some query on top); the leaves some query may need
+    // are scanned at once, nearest first, for the queries that still need them.
+    auto expand = [&](uint32_t c0, int nk) {
+      const uint32_t c = c0 + (uint32_t)lane;
+      uint32_t key[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) key[g] = 0xFFFFFFFFu;
+      uint32_t need = 0, mkey = 0xFFFFFFFFu;  // queries that may need the child; its smallest key
+      bool leafc = false;
+      uint32_t cref = 0;
+      int ccnt = 0;
+      if (lane < nk) {
+        cref = t.ref[c];
+        if (a.leaf_limit >= 0) {
+          leafc = (int64_t)c < a.leaf_limit;
+          ccnt = leafc ? t.cnt[c] : t.kids[c];
+        } else {
+          const int ck = t.kids[c], cn = t.cnt[c];
+          leafc = ck == 0;
+          ccnt = leafc ? cn : ck;
+        }
+        int32_t lo[D], hi[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          lo[d] = t.lo[d][c];
+          hi[d] = t.hi[d][c];
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          key[g] = box_key_of<D>(lo, hi, qc[g]);
+          if (key[g] <= kdk[g]) {
+            need |= 1u << g;
+            mkey = min(mkey, key[g]);
+          }
+        }
+        if (leafc) {
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (c == seed[g]) need = 0;  // scanned as a seed
+        }
+      }
+      if (STATS) {
+        ++n_int;
+        n_kids += nk;
+      }
+      const uint32_t mi = __ballot_sync(0xFFFFFFFFu, need && !leafc);
+      uint32_t ml = __ballot_sync(0xFFFFFFFFu, need && leafc);
+      if (mi) {
+        const int n = __popc(mi);
+        if (sp + n > KSTACK) {  // cannot happen within the depth bound
+          if (lane == 0) atomicOr(a.status, ST_STACK);
+        } else {
+          const bool ii = (mi >> lane) & 1u;
+          const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, ii ? mkey : 0xFFFFFFFFu);
+          const int win = __ffs(__ballot_sync(0xFFFFFFFFu, ii && mkey == mn)) - 1;
+          int pos = __popc(mi & lanemask_lt());
+          if (lane == win)
+            pos = n - 1;
+          else if (pos == n - 1)
+            pos = __popc(mi & ((1u << win) - 1u));
+          __syncwarp();
+          if (ii) s_stk[w][sp + pos] = make_uint2(cref, (uint32_t)ccnt);
+          sp += n;
+          __syncwarp();
+        }
+      }
+      while (ml) {
+        // queries that still need each remaining leaf under the current bounds
+        uint32_t now = 0, nkey = 0xFFFFFFFFu;
+        if ((ml >> lane) & 1u) {
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (((need >> g) & 1u) && key[g] <= kdk[g]) {
+              now |= 1u << g;
+              nkey = min(nkey, key[g]);
+            }
+        }
+        const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, nkey);
+        if (mn == 0xFFFFFFFFu) break;  // no query needs any remaining leaf
+        const int src = __ffs(__ballot_sync(0xFFFFFFFFu, now && nkey == mn)) - 1;
+        ml &= ~(1u << src);
+        const uint32_t qm = __shfl_sync(0xFFFFFFFFu, now, src);
+        const uint32_t lref = __shfl_sync(0xFFFFFFFFu, cref, src);
+        const int lcnt = __shfl_sync(0xFFFFFFFFu, ccnt, src);
+        knn_scan_group<D, G, false>(t, lref, lcnt, qc, kl, a.k, qm);
+#pragma unroll
+        for (int g = 0; g < G; ++g) kdk[g] = order_key(kl[g].kd);
+        if (STATS) {
+          ++n_leaf;
+          n_pts += lcnt;
+        }
+      }
+    };
+    if (root >= 0) {
+      if (t.kids[root] == 0) {
+        bool sd_root = false;
+#pragma unroll
+        for (int g = 0; g < G; ++g) sd_root |= seed[g] == (uint32_t)root;
+        if (!sd_root) knn_scan_group<D, G, false>(t, t.ref[root], t.cnt[root], qc, kl, a.k, all);
+      } else {
+        uint32_t c0 = t.ref[root];
+        int nk = t.kids[root];
+        for (;;) {  // one call site keeps `expand` inlined
+          expand(c0, nk);
+          if (sp == 0) break;
+          const uint2 e = s_stk[w][--sp];
+          c0 = e.x;
+          nk = (int)e.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (g < ng && lane < a.k) {
+        const int64_t q = a.order ? (int64_t)a.order[qi0 + g] : qi0 + g;
+        a.out_id[q * a.k + lane] = kl[g].i[0];
+        a.out_d2[q * a.k + lane] = kl[g].d[0];
+      }
+    }
+    if (STATS && lane == 0) atomicAdd(&stats.c[3], (unsigned long long)ng);
+  }
+  if (STATS && lane == 0) {
+    atomicAdd(&stats.c[0], n_int);
+    atomicAdd(&stats.c[1], n_leaf);
+    atomicAdd(&stats.c[2], n_pts);
+    atomicAdd(&stats.c[4], n_kids);
   }
 }
 
@@ -563,6 +806,27 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
     PSI_LAUNCH(k_knn_seed, gs, 256, 0, s, seed, tv.ref, order, nq, seed.pos);
   }
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
+  // k <= 32 over one tree with queries in curve order: kGroup queries per warp
+  if (kpl == 1 && !qroot && order && kGroup > 1) {
+#define KNN_GROUP(DD)                                                                                       \
+  do {                                                                                                      \
+    if (d_stats)                                                                                            \
+      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn_group<DD, kGroup, true>),                                      \
+                       resident_query_grid(k_knn_group<DD, kGroup, true>, ceil_div(nq, kGroup)), QW * 32, 0, s, \
+                       a, stats);                                                                           \
+    else                                                                                                    \
+      PSI_LAUNCH_NAMED("k_knn", (k_knn_group<DD, kGroup, false>),                                           \
+                       resident_query_grid(k_knn_group<DD, kGroup, false>, ceil_div(nq, kGroup)), QW * 32, 0, \
+                       s, a, stats);                                                                        \
+  } while (0)
+    if (D == 2)
+      KNN_GROUP(2);
+    else
+      KNN_GROUP(3);
+#undef KNN_GROUP
+    PSI_CK(cudaGetLastError());
+    return PSI_OK;
+  }
 #define KNN_CASE(DD, KK)                                                                           \
   do {                                                                                             \
     if (d_stats)                                                                                   \

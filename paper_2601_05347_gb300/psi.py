@@ -197,16 +197,16 @@ class Index:
         return out_ids, out_d2
 
     def knn_stats(self, q: torch.Tensor, k: int, stream=None):
-        """k-NN with traversal counters: (ids, d2, {nodes, leaves, points, queries})."""
+        """k-NN with traversal counters: (ids, d2, {nodes, leaves, points, queries, children})."""
         q = q.contiguous()
         nq = int(q.shape[0])
         out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
         out_d2 = torch.empty((nq, k), dtype=torch.int64, device=q.device)
-        st = torch.zeros(4, dtype=torch.int64, device=q.device)
+        st = torch.zeros(5, dtype=torch.int64, device=q.device)
         _check(lib().psi_knn_instrumented(self._h, _ptr(q), nq, k, _ptr(out_ids), _ptr(out_d2), _ptr(st),
                                           _stream(stream)))
         c = st.cpu().tolist()
-        return out_ids, out_d2, {"nodes": c[0], "leaves": c[1], "points": c[2], "queries": c[3]}
+        return out_ids, out_d2, {"nodes": c[0], "leaves": c[1], "points": c[2], "queries": c[3], "children": c[4]}
 
     def range_count(self, boxes: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         boxes = boxes.contiguous()
@@ -316,17 +316,17 @@ class Batch:
         return out_ids, out_d2
 
     def knn_stats(self, q: torch.Tensor, qoffsets: torch.Tensor, k: int, stream=None):
-        """Batched k-NN with traversal counters: (ids, d2, {nodes, leaves, points, queries})."""
+        """Batched k-NN with traversal counters: (ids, d2, {nodes, leaves, points, queries, children})."""
         nq = int(q.shape[0])
         if nq > self._qcap:
             self.reserve(nq, stream)
         out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
         out_d2 = torch.empty((nq, k), dtype=torch.int64, device=q.device)
-        st = torch.zeros(4, dtype=torch.int64, device=q.device)
+        st = torch.zeros(5, dtype=torch.int64, device=q.device)
         _check(lib().psi_batch_knn_instrumented(self._h, _ptr(q.contiguous()), _ptr(qoffsets.contiguous()), nq, k,
                                                 _ptr(out_ids), _ptr(out_d2), _ptr(st), _stream(stream)))
         c = st.cpu().tolist()
-        return out_ids, out_d2, {"nodes": c[0], "leaves": c[1], "points": c[2], "queries": c[3]}
+        return out_ids, out_d2, {"nodes": c[0], "leaves": c[1], "points": c[2], "queries": c[3], "children": c[4]}
 
     def sync(self, stream=None):
         _check(lib().psi_batch_sync(self._h, _stream(stream)))

@@ -234,6 +234,26 @@ def test_knn_matches_oracle(kind, dim, bits, k):
     assert (gd.cpu().numpy() == od).all()
 
 
+@pytest.mark.parametrize("kind,dim,bits,n,phi,k,nq,dup", [("spac_h", 2, 30, 30000, 64, 10, 4097, False),
+                                                         ("porth", 2, 30, 20000, 8, 5, 4099, True),
+                                                         ("spac_z", 3, 21, 7, 32, 10, 4098, False),
+                                                         ("spac_h", 2, 30, 50000, 32, 32, 4101, True),
+                                                         ("spac_h", 3, 21, 40000, 16, 1, 4103, False)])
+def test_knn_grouped_queries_ragged(kind, dim, bits, n, phi, k, nq, dup):
+    # >= 4096 queries with k <= 32 run several curve-ordered queries per warp;
+    # query counts not a multiple of the group size leave a short last group
+    p, ids = points(n, dim, bits, 61 + nq, dup=dup, clustered=not dup)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=phi, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=phi, bits=bits)
+    q = query_points(nq, dim, bits, 7 + k, p)
+    gi, gd = ix.knn(T(q), k)
+    oi, od = o.knn(q, k)
+    assert (U32(gi) == oi).all()
+    assert (gd.cpu().numpy() == od).all()
+    si, sd, st = ix.knn_stats(T(q), k)
+    assert torch.equal(si, gi) and torch.equal(sd, gd) and st["queries"] == nq
+
+
 @pytest.mark.parametrize("n", [0, 1, 7, 40])
 def test_knn_small_and_k_beyond_size(n):
     p, ids = points(n, 2, 30, 3)
