@@ -221,9 +221,26 @@ psi_status psi_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int32_t
  *     race on it and must be serialised by the caller.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
- *   - Synchronises `stream` at the end (like psi_sort_pairs). */
+ *     before any stream capture.  The address is looked up again when the
+ *     device's context has changed since (e.g. after cudaDeviceReset).
+ *   - Synchronises `stream` at the end (like psi_sort_pairs).
+ *   - PSI_ERR_DEVICE_TIMEOUT (a bounded device-side wait ran out): the
+ *     arrays' contents are then unspecified. */
 psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bits, void *stream);
+
+/* ---- Test hook of the bounded device-side waits ----------------------------
+ * Failure detection (every wait of a digit pass on a predecessor tile's
+ * look-back word gives up after a bounded number of polls and reports
+ * PSI_ERR_DEVICE_TIMEOUT) made testable without a GPU fault or hang.  Sorts
+ * n (key, value) pairs like psi_sort_pairs (8-bit digits, all 64 key bits),
+ * but tile `withheld_tile` (0-based, 4096 pairs per tile; -1: none) of the
+ * first digit pass never publishes its look-back words, and a waiting tile
+ * gives up after `spin_limit` (>= 1) polls.  Returns PSI_ERR_DEVICE_TIMEOUT
+ * when a wait ran out: the arrays' contents are then unspecified (every
+ * write stays inside them); PSI_OK and the sorted arrays when no wait did.  The context stays usable either way.
+ * Synchronises `stream`.  No counterpart in the paper: a test facility. */
+psi_status psi_test_sort_withheld_tile(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int64_t withheld_tile,
+                                       uint32_t spin_limit, void *stream);
 
 /* ---- Instrumentation ---------------------------------------------------- */
 

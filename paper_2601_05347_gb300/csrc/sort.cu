@@ -27,6 +27,7 @@
 // Equal keys (duplicate points) are then put in id order by k_tie_runs /
 // k_tie_long (a later canonical leaf layout depends on it).
 #include "common.cuh"
+#include <cuda.h>
 #include <mutex>
 #include <type_traits>
 
@@ -105,6 +106,11 @@ struct PassArgs {
   uint64_t kmask = ~0ull;  // (1 << kr) - 1: the key bits of a packed word
   int kr = 0;
   int drop = 0;
+  // Bounded look-back wait: polls of a predecessor's word before giving up
+  // with ST_TIMEOUT.  withheld_tile >= 0 (a test of that path only): this
+  // tile never publishes its words, so its successors' waits run out.
+  uint32_t spin_limit = kSpinLimit;
+  int64_t withheld_tile = -1;
 };
 
 // What a digit pass reads and writes.  An encoding sort whose positions
@@ -362,7 +368,8 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
       }
       cnt[q] = run;
       tsum += run;
-      st_relaxed_u32(a.lookback + (size_t)tile * RADIX + d, (tile == 0 ? LB_PRE : LB_AGG) | run);
+      if ((int64_t)tile != a.withheld_tile)
+        st_relaxed_u32(a.lookback + (size_t)tile * RADIX + d, (tile == 0 ? LB_PRE : LB_AGG) | run);
     }
     uint32_t x = tsum;
 #pragma unroll
@@ -403,7 +410,7 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
           if (done) break;
           if (u < LB_W && t - u >= 0) {
             t -= u;
-            if (++spins > kSpinLimit) {
+            if (++spins > a.spin_limit) {
               atomicOr(a.status, ST_TIMEOUT);
               break;
             }
@@ -412,7 +419,8 @@ __global__ __launch_bounds__(ST, RB == 11 ? 2 : 3) void k_onesweep(PassArgs a) {
             t -= LB_W;
           }
         }
-        st_relaxed_u32(a.lookback + (size_t)tile * RADIX + d, LB_PRE | ((prev + cnt[q]) & LB_VAL));
+        if ((int64_t)tile != a.withheld_tile)
+          st_relaxed_u32(a.lookback + (size_t)tile * RADIX + d, LB_PRE | ((prev + cnt[q]) & LB_VAL));
       }
       sm.glob[d] = sm.gb[d] + prev - excl;
       excl += cnt[q];
@@ -972,9 +980,36 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Host code may not use g_noalloc_scratch as a pointer: on the host that name
 // is only a stand-in for the device symbol.  Its device address is looked up
-// once per device, with that device current, and cached here.
+// with the device current, once per device and context (a context torn down
+// and created again, e.g. after cudaDeviceReset, may load the module at
+// another address), and cached here.
 std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_addr[64] = {};
+struct NoallocAddr {
+  void *ctx = nullptr;
+  unsigned char *addr = nullptr;
+};
+NoallocAddr g_noalloc_addr[64];
+
+// The current driver context (null if the driver's entry point is not
+// reachable), through the runtime's driver entry-point query.
+void *current_context() {
+  using CtxGet = CUresult (*)(CUcontext *);
+  static CtxGet fn = nullptr;
+  static bool tried = false;
+  if (!tried) {  // under g_noalloc_mu
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGet>(p);
+    else
+      cudaGetLastError();
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 psi_status noalloc_scratch(unsigned char **out) {
   int dev = 0;
@@ -984,13 +1019,17 @@ psi_status noalloc_scratch(unsigned char **out) {
     return PSI_ERR_INVALID;
   }
   std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  void *ctx = current_context();
+  NoallocAddr &e = g_noalloc_addr[dev];
+  // without a context handle to compare, look the address up on every call
+  if (!e.addr || !ctx || e.ctx != ctx) {
     void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
-    g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+    cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess || !p) return cuda_fail(err != cudaSuccess ? err : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+    e.addr = static_cast<unsigned char *>(p);
+    e.ctx = ctx;
   }
-  *out = g_noalloc_addr[dev];
+  *out = e.addr;
   return PSI_OK;
 }
 
@@ -1062,6 +1101,76 @@ extern "C" psi_status psi_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals,
   PSI_CK(cudaGetLastError());
   int h = 0;
   PSI_CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  if (h & ST_TIMEOUT) {
+    set_error("a bounded device-side wait timed out");
+    return PSI_ERR_DEVICE_TIMEOUT;
+  }
+  return PSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Test hook of the bounded look-back wait (failure detection without a GPU
+// fault): the sort of psi_sort_pairs_noalloc's plan (8-bit digits, global
+// digit offsets scanned up front) on library-allocated scratch, with one tile
+// of the first digit pass withholding its look-back words.
+// ---------------------------------------------------------------------------
+extern "C" psi_status psi_test_sort_withheld_tile(uint64_t *d_keys, uint32_t *d_vals, int64_t n,
+                                                  int64_t withheld_tile, uint32_t spin_limit, void *stream) {
+  using namespace psi;
+  set_error("");
+  if (n < 0 || (n > 0 && (!d_keys || !d_vals)) || n >= (int64_t)LB_VAL || spin_limit < 1) {
+    set_error("invalid test sort arguments");
+    return PSI_ERR_INVALID;
+  }
+  if (n == 0) return PSI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  constexpr int RADIX = Radix<8>::RADIX;
+  const int passes = 8;
+  const int64_t tiles = ceil_div(n, TILE);
+  Buf<uint64_t> k2;
+  Buf<uint32_t> v2, hist, gbase, look, ctr;
+  Buf<int> status;
+  psi_status st;
+  if ((st = k2.alloc(n, s)) || (st = v2.alloc(n, s)) || (st = hist.alloc(passes * RADIX, s)) ||
+      (st = gbase.alloc(passes * RADIX, s)) || (st = look.alloc((size_t)passes * tiles * RADIX, s)) ||
+      (st = ctr.alloc(passes, s)) || (st = status.alloc(1, s)))
+    return st;
+  PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * passes * RADIX, s));
+  PSI_CK(cudaMemsetAsync(look.p, 0, sizeof(uint32_t) * passes * tiles * RADIX, s));
+  PSI_CK(cudaMemsetAsync(ctr.p, 0, sizeof(uint32_t) * passes, s));
+  PSI_CK(cudaMemsetAsync(status.p, 0, sizeof(int), s));
+  EncodeSpec none;
+  if ((st = launch_hist<0, 2, 0, 8>(d_keys, none, n, passes, hist.p, status.p, s))) return st;
+  PSI_LAUNCH_NAMED("k_hist_scan", k_hist_scan<8>, passes, RADIX, 0, s, hist.p, gbase.p);
+  uint64_t *kb[2] = {k2.p, d_keys};
+  uint32_t *vb[2] = {v2.p, d_vals};
+  for (int p = 0; p < passes; ++p) {
+    PassArgs a;
+    a.kin = p == 0 ? d_keys : kb[(p - 1) & 1];
+    a.vin = p == 0 ? d_vals : vb[(p - 1) & 1];
+    a.kout = kb[p & 1];
+    a.vout = vb[p & 1];
+    a.pts = nullptr;
+    a.bits = 0;
+    a.key_shift = 0;
+    a.n = n;
+    a.shift = p * 8;
+    a.gbase = gbase.p + p * RADIX;
+    a.hist_cur = nullptr;
+    a.hist_next = nullptr;
+    a.shift_next = 0;
+    a.lookback = look.p + (size_t)p * tiles * RADIX;
+    a.lookback_next = nullptr;
+    a.tile_ctr = ctr.p + p;
+    a.status = status.p;
+    a.spin_limit = spin_limit;
+    a.withheld_tile = p == 0 ? withheld_tile : -1;
+    if ((st = launch_pass<0, 2, 0, 8>(a, tiles, s))) return st;
+  }
+  PSI_CK(cudaGetLastError());
+  int h = 0;
+  PSI_CK(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   PSI_CK(cudaStreamSynchronize(s));
   if (h & ST_TIMEOUT) {
     set_error("a bounded device-side wait timed out");

@@ -70,6 +70,7 @@ def lib():
             "psi_sort_pairs": (st, [P, P, i64, i32, P]),
             "psi_knn_instrumented": (st, [P, P, i64, i32, P, P, P, P]),
             "psi_sort_pairs_noalloc": (st, [P, P, i64, i32, P]),
+            "psi_test_sort_withheld_tile": (st, [P, P, i64, i64, ctypes.c_uint32, P]),
             "psi_batch_create": (st, [P, P, i32, i32, P, P]),
             "psi_batch_build": (st, [P, P, P, P]),
             "psi_batch_knn_reserve": (st, [P, i64, P]),
@@ -452,6 +453,14 @@ def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 64, strea
     """In-place stable sort of (uint64 key, uint32 value) pairs by key."""
     _check(lib().psi_sort_pairs(_ptr(keys), _ptr(vals), int(keys.shape[0]), key_bits, _stream(stream)))
     return keys, vals
+
+
+def test_sort_withheld_tile(keys: torch.Tensor, vals: torch.Tensor, withheld_tile: int, spin_limit: int,
+                            stream=None) -> int:
+    """Test hook of the bounded look-back waits: returns the library status
+    (OK, or ERR_DEVICE_TIMEOUT when the withheld tile made a wait run out)."""
+    return int(lib().psi_test_sort_withheld_tile(_ptr(keys), _ptr(vals), int(keys.shape[0]), int(withheld_tile),
+                                                 int(spin_limit), _stream(stream)))
 
 
 def launch_count() -> int:

@@ -36,7 +36,8 @@ KINDS = ("insert", "delete", "knn", "count", "report")
 
 
 class Request:
-    __slots__ = ("kind", "a", "b", "k", "arrival", "seq", "future", "done", "est_bytes", "t_admit", "t_launch")
+    __slots__ = ("kind", "a", "b", "k", "arrival", "seq", "future", "done", "est_bytes", "t_admit", "t_launch",
+                 "held")
 
     def __init__(self, kind: str, a: np.ndarray, b: np.ndarray | None = None, k: int = 0):
         assert kind in KINDS
@@ -46,6 +47,7 @@ class Request:
         self.t_admit = 0.0   # trace: taken by the worker
         self.t_launch = 0.0  # trace: its work enqueued on the device
         self.seq = -1
+        self.held = False  # its est_bytes count against the server's budget
         self.future = Future()
         n = len(a)
         self.est_bytes = {"insert": 160 * n, "delete": 120 * n, "knn": n * (8 + 12 * k + 64),
@@ -109,6 +111,7 @@ class Server:
         _warm_pinned(warm_pinned_bytes)
         self.pending = collections.deque()
         self.lock = threading.Condition()
+        self.inflight = 0  # est_bytes of admitted requests whose device memory is not yet released
         self.seq = 0
         self.stop_flag = False
         self.rounds = []  # (admitted, epochs) per round, for inspection
@@ -144,17 +147,37 @@ class Server:
 
     # -- worker --------------------------------------------------------------
     def _admit(self):
+        """Takes the pending requests, in arrival order, that fit the budget
+        next to the device memory still held by earlier rounds (query results
+        not yet copied back); waits while none fits."""
         with self.lock:
-            while not self.pending and not self.stop_flag:
-                self.lock.wait()
-            out, used = [], 0
-            now = time.perf_counter()
-            while self.pending and used + self.pending[0].est_bytes <= self.budget:
-                r = self.pending.popleft()
-                used += r.est_bytes
-                r.t_admit = now
-                out.append(r)
-            return out
+            while True:
+                while not self.pending and not self.stop_flag:
+                    self.lock.wait()
+                out, used = [], 0
+                now = time.perf_counter()
+                while self.pending and self.inflight + used + self.pending[0].est_bytes <= self.budget:
+                    r = self.pending.popleft()
+                    used += r.est_bytes
+                    r.t_admit = now
+                    r.held = True
+                    out.append(r)
+                if out or not self.pending or self.stop_flag and not self.inflight:
+                    self.inflight += used
+                    return out
+                self.lock.wait()  # the finisher releases memory and notifies
+
+    def _release(self, rs):
+        """Returns the budget share of requests whose device memory is freed."""
+        freed = 0
+        for r in rs:
+            if r.held:
+                r.held = False
+                freed += r.est_bytes
+        if freed:
+            with self.lock:
+                self.inflight -= freed
+                self.lock.notify_all()
 
     def _loop(self):
         while True:
@@ -170,10 +193,12 @@ class Server:
                     self._run_queries(queries)
                     if updates:
                         self._run_update(updates)
+                        self._release(updates)  # done synchronously: its inputs are freed
             except Exception as e:  # fail every request of the round, keep serving
                 for r in batch:
                     if not r.future.done():
                         r.future.set_exception(e)
+                self._release([r for r in batch if r.future.done() and r.future.exception() is not None])
 
     def _to_dev(self, a: np.ndarray, s) -> torch.Tensor:
         """Host array -> device: a pinned copy (host caching allocator), sent
@@ -281,6 +306,7 @@ class Server:
                     res = (off[a:b + 1] - off[a], out[1][off[a]:off[b]].view(np.uint32))
                 r.done = now
                 r.future.set_result(res)
+            self._release(rs)  # the group's results are on the host
 
 
 def serve_plain(index: "psi.Index", req: Request):

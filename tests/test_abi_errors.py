@@ -83,3 +83,12 @@ def test_float_porth_rejects_bad_configs(L, dim, leaf, depth, lo, hi):
     assert L.psi_forth_build(ctypes.byref(c), P, P, 10, NULL, ctypes.byref(h)) == INVALID
     assert h.value is None
     assert "forth" in L.psi_last_error().decode()
+
+
+def test_withheld_tile_hook_rejects_bad_arguments():
+    lib = ctypes.CDLL(_build.build())
+    f = lib.psi_test_sort_withheld_tile
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p]
+    assert f(None, None, -1, 0, 16, None) == 1          # n < 0
+    assert f(None, None, 10, 0, 16, None) == 1          # null arrays
+    assert f(None, None, 0, 0, 16, None) == 0           # nothing to sort
