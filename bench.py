@@ -487,7 +487,8 @@ def run_ours(args):
     if not args.no_batched:
         line["batched"] = run_batched(args.batched_indexes, max(1, args.steps), args.warmup, rank)
     if not args.no_served:
-        line["served"] = run_served(args.served_points, args.served_requests, rank)
+        # the served configuration: updates of 1e3..1e7 points, query batches of 1e2..1e6
+        line["served"] = run_served(args.served_points, args.served_requests, rank, upd=(1e3, 1e7), qry=(1e2, 1e6))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, host, budget_s=args.cpu_budget)
     if rank == 0:
@@ -1080,8 +1081,36 @@ def run_forth(scale: float = 1.0):
 # ---------------------------------------------------------------------------
 # oracle timings (the CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample_step(w, host, frac: float):
-    """Times the oracle on a bounded sample of the step's workload."""
+def host_cores():
+    """(nproc, the CPUs this process may run on) of the host."""
+    try:
+        aff = sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        aff = list(range(os.cpu_count() or 1))
+    runs, start = [], None
+    for i, c in enumerate(aff):
+        if start is None:
+            start = c
+        if i + 1 == len(aff) or aff[i + 1] != c + 1:
+            runs.append(f"{start}-{c}" if c > start else f"{c}")
+            start = None
+    return os.cpu_count() or 1, len(aff), ",".join(runs)
+
+
+def _split_call(fn, arr, threads):
+    """fn over `threads` contiguous chunks of arr on as many host threads (the
+    oracle's C calls release the interpreter lock); results in chunk order."""
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = np.array_split(arr, threads)
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(fn, chunks))
+
+
+def oracle_sample_step(w, host, frac: float, threads: int = 1):
+    """Times the oracle on a bounded sample of the step's workload.  Build and
+    updates run single-threaded; with threads > 1 the queries are also timed
+    split across that many host threads (same per-query code, results checked
+    identical to the single-threaded ones)."""
     from oracle import oracle as O
     n = max(1000, int(w["n"] * frac))
     pts = host["pts"][:n]
@@ -1091,7 +1120,7 @@ def oracle_sample_step(w, host, frac: float):
     nq = max(100, int(w["n_knn"] * frac))
     nb = max(50, int(w["n_box"] * frac))
     dsel = gen.sample_without_replacement(n, md, 17)
-    t = {}
+    t, tp = {}, {}
     a = time.perf_counter()
     ix = O.Index(pts, ids, kind=O.SPAC_H, phi=32)
     t["build"] = time.perf_counter() - a
@@ -1103,31 +1132,51 @@ def oracle_sample_step(w, host, frac: float):
     t["delete"] = time.perf_counter() - a
     q = pts[gen.sample_with_replacement(n, nq, 18)]
     a = time.perf_counter()
-    ix.knn(q, w["k"])
+    ki, kd = ix.knn(q, w["k"])
     t["knn"] = time.perf_counter() - a
     # boxes sized for ~box_target points in the sample (same shape, scaled)
     side = int(host["half_side"] * np.sqrt(w["n"] / n))
     boxes = gen.centred_boxes(pts[gen.sample_with_replacement(n, nb, 19)], side, BITS)
     a = time.perf_counter()
-    ix.range_report(boxes)
+    roff, rids = ix.range_report(boxes)
     t["range_report"] = time.perf_counter() - a
     a = time.perf_counter()
-    ix.range_count(boxes)
+    rc = ix.range_count(boxes)
     t["range_count"] = time.perf_counter() - a
+    same = True
+    if threads > 1:
+        a = time.perf_counter()
+        parts = _split_call(lambda c: ix.knn(c, w["k"]), q, threads)
+        tp["knn"] = time.perf_counter() - a
+        same &= bool((np.concatenate([p[0] for p in parts]) == ki).all()
+                     and (np.concatenate([p[1] for p in parts]) == kd).all())
+        a = time.perf_counter()
+        parts = _split_call(ix.range_report, boxes, threads)
+        tp["range_report"] = time.perf_counter() - a
+        same &= bool((np.concatenate([p[1] for p in parts]) == rids).all())
+        a = time.perf_counter()
+        parts = _split_call(ix.range_count, boxes, threads)
+        tp["range_count"] = time.perf_counter() - a
+        same &= bool((np.concatenate(parts) == rc).all())
     sizes = dict(build=n, insert=mi, delete=md, knn=nq, range_report=nb, range_count=nb)
-    return t, sizes
+    return t, sizes, tp, same
 
 
 def cpu_baseline(w, host, budget_s: float = 20.0):
     frac = 0.02 if w["n"] >= 10_000_000 else 1.0
-    t, sizes = oracle_sample_step(w, host, frac)
-    phases = {p: {"value": round(sizes[p] / t[p] / (1e6 if p in ("build", "insert", "delete") else 1), 2),
-                  "unit": "Mpts/s" if p in ("build", "insert", "delete") else "queries/s", "sample": sizes[p]}
-              for p in t}
+    nproc, ncpu, aff = host_cores()
+    t, sizes, tp, same = oracle_sample_step(w, host, frac, threads=ncpu)
+    unit = lambda p: "Mpts/s" if p in ("build", "insert", "delete") else "queries/s"
+    rate = lambda p, sec: round(sizes[p] / sec / (1e6 if p in ("build", "insert", "delete") else 1), 2)
+    phases = {p: {"value": rate(p, t[p]), "unit": unit(p), "sample": sizes[p]} for p in t}
+    multi = {p: {"value": rate(p, tp[p]), "unit": unit(p), "sample": sizes[p]} for p in tp}
     return {"value": phases["build"]["value"], "unit": "Mpts/s (build)", "cores": 1, "kind": "oracle",
             "sample": f"{frac:.0%} of every phase of the step (build of the first {sizes['build']} points), "
-                      f"single-threaded sequential C oracle", "seconds": round(sum(t.values()), 1),
-            "phases": phases}
+                      f"single-threaded sequential C oracle", "seconds": round(sum(t.values()) + sum(tp.values()), 1),
+            "phases": phases,
+            "queries_all_cores": {"threads": ncpu, "nproc": nproc, "affinity": aff, "results_identical": same,
+                                  "how": "the same per-query oracle code on contiguous chunks of the sample's "
+                                         "queries, one host thread per allowed CPU", "phases": multi}}
 
 
 def run_reference(args):
@@ -1143,7 +1192,7 @@ def run_reference(args):
     times = []
     sizes = None
     for _ in range(args.steps):
-        t, sizes = oracle_sample_step(w, host, frac)
+        t, sizes, _, _ = oracle_sample_step(w, host, frac)
         times.append(t)
     build_s = statistics.mean(t["build"] for t in times)
     value = sizes["build"] / build_s / 1e6
@@ -1155,7 +1204,8 @@ def run_reference(args):
         "data": "synthetic (seeded Varden-style random walks, SplitMix64)",
         "config": {"workload": w["name"], "sample_fraction": frac},
         "cpu_baseline": {"value": round(value, 3), "unit": "Mpts/s (build)", "cores": 1, "kind": "oracle",
-                         "sample": f"{frac:.0%} of every phase of the step, single-threaded sequential C oracle"},
+                         "sample": f"{frac:.0%} of every phase of the step, single-threaded sequential C oracle",
+                         "nproc": host_cores()[0], "affinity": host_cores()[2]},
         "e2e": {"value": round(value, 3), "unit": "Mpts/s (build)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -1172,12 +1222,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batched-indexes", type=int, default=512,
+    ap.add_argument("--batched-indexes", type=int, default=4096,
                     help="indexes in the batched-form comparison of the default line")
     ap.add_argument("--batched", action="store_true", help="only the 4096-index batched configuration")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--served-points", type=int, default=20_000_000)
-    ap.add_argument("--served-requests", type=int, default=300)
+    ap.add_argument("--served-points", type=int, default=500_000_000)
+    ap.add_argument("--served-requests", type=int, default=1000)
     ap.add_argument("--serve", action="store_true", help="only the served configuration at 5e8 resident points")
     ap.add_argument("--configs", action="store_true",
                     help="the 2D uniform 1e6, 2D clustered update-batch and 3D 1e8 configurations")
