@@ -13,14 +13,15 @@
 //           rebuild when the leaf would exceed the wrap).
 //   delete: every leaf point whose (key, id) occurs in the slice (and whose
 //           coordinates match) is removed; survivors are compacted in place
-//           and the box recomputed; empty leaves are dropped.
+//           and the box recomputed; then the leaf wrap is restored (Sec 4.2):
+//           each run of leaves left below phi / 2 points (emptied ones
+//           included) joins the leaf after it and their points are re-wrapped
+//           into balanced leaves of at least phi / 2 points.
 // Only touched leaves move data; they read the sorted batch as records (id
 // and point per entry, gathered once by k_batch_records).  The leaf list is
 // then rewritten from a scan of per-leaf output counts and the summary tree
 // rebuilt over it -- the paper's join-based rebalancing is replaced by this
-// relayout of the (small) leaf directory.  Leaves that deletes leave under
-// phi / 2 are not merged with their neighbours (no query depends on leaf
-// shape).
+// relayout of the (small) leaf directory.
 #include "index.cuh"
 
 namespace psi {
@@ -97,58 +98,68 @@ __global__ void k_insert_plan(const int32_t *cnt, const int32_t *sbeg, const int
 
 constexpr int MAXPL = 4;  // points per lane in one block (C <= 128)
 
+// Sorts, in place by (key, id), the cnt (<= MAXPL * 32) points of one leaf
+// block starting at slot s0: the whole warp ranks every point against all
+// others and writes it to its rank.
+template <int D>
+__device__ __forceinline__ void sort_leaf_block(Pool &pool, uint32_t s0, int cnt) {
+  const int lane = threadIdx.x & 31;
+  uint64_t k[MAXPL];
+  uint32_t id[MAXPL];
+  int32_t c[MAXPL][D];
+#pragma unroll
+  for (int r = 0; r < MAXPL; ++r) {
+    const int e = r * 32 + lane;
+    k[r] = ~0ull;
+    id[r] = 0xFFFFFFFFu;
+    if (e < cnt) {
+      k[r] = pool.pkey[s0 + e];
+      id[r] = pool.pid[s0 + e];
+#pragma unroll
+      for (int d = 0; d < D; ++d) c[r][d] = pool.px[d][s0 + e];
+    }
+  }
+  int rank[MAXPL] = {0, 0, 0, 0};
+  for (int r2 = 0; r2 < MAXPL; ++r2) {
+    if (r2 * 32 >= cnt) break;
+    for (int sl = 0; sl < 32; ++sl) {
+      const uint64_t kf = __shfl_sync(0xFFFFFFFFu, k[r2], sl);
+      const uint32_t idf = __shfl_sync(0xFFFFFFFFu, id[r2], sl);
+      if (r2 * 32 + sl >= cnt) break;
+#pragma unroll
+      for (int r = 0; r < MAXPL; ++r) rank[r] += kid_less(kf, idf, k[r], id[r]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < MAXPL; ++r) {
+    const int e = r * 32 + lane;
+    if (e < cnt) {
+      pool.pkey[s0 + rank[r]] = k[r];
+      pool.pid[s0 + rank[r]] = id[r];
+#pragma unroll
+      for (int d = 0; d < D; ++d) pool.px[d][s0 + rank[r]] = c[r][d];
+    }
+  }
+  __syncwarp();
+}
+
 // Sorts, in place, the block of every leaf that will be re-wrapped.  A warp
 // takes 32 leaves: one lane per leaf finds the few that overflow, then the
 // warp sorts each of those.
+template <int D>
 __global__ void k_sort_overflow_leaves(const int32_t *ncnt, const uint32_t *nref, const int32_t *sbeg,
-                                       const int32_t *send, int64_t L, int C, int D, Pool pool) {
+                                       const int32_t *send, int64_t L, int C, Pool pool) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < L; j0 += warps * 32) {
     const int64_t jl = j0 + lane;
     uint32_t todo = __ballot_sync(0xFFFFFFFFu, jl < L && send[jl] > sbeg[jl] && ncnt[jl] + (send[jl] - sbeg[jl]) > C);
-   while (todo) {
-    const int64_t j = j0 + __ffs(todo) - 1;
-    todo &= todo - 1;
-    const int cnt = ncnt[j];
-    const uint32_t s0 = nref[j];
-    uint64_t k[MAXPL];
-    uint32_t id[MAXPL];
-    int32_t c[MAXPL][3];
-#pragma unroll
-    for (int r = 0; r < MAXPL; ++r) {
-      const int e = r * 32 + lane;
-      k[r] = ~0ull;
-      id[r] = 0xFFFFFFFFu;
-      if (e < cnt) {
-        k[r] = pool.pkey[s0 + e];
-        id[r] = pool.pid[s0 + e];
-        for (int d = 0; d < D; ++d) c[r][d] = pool.px[d][s0 + e];
-      }
+    while (todo) {
+      const int64_t j = j0 + __ffs(todo) - 1;
+      todo &= todo - 1;
+      sort_leaf_block<D>(pool, nref[j], ncnt[j]);
     }
-    int rank[MAXPL] = {0, 0, 0, 0};
-    for (int r2 = 0; r2 < MAXPL; ++r2) {
-      if (r2 * 32 >= cnt) break;
-      for (int sl = 0; sl < 32; ++sl) {
-        const uint64_t kf = __shfl_sync(0xFFFFFFFFu, k[r2], sl);
-        const uint32_t idf = __shfl_sync(0xFFFFFFFFu, id[r2], sl);
-        if (r2 * 32 + sl >= cnt) break;
-#pragma unroll
-        for (int r = 0; r < MAXPL; ++r) rank[r] += kid_less(kf, idf, k[r], id[r]);
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < MAXPL; ++r) {
-      const int e = r * 32 + lane;
-      if (e < cnt) {
-        pool.pkey[s0 + rank[r]] = k[r];
-        pool.pid[s0 + rank[r]] = id[r];
-        for (int d = 0; d < D; ++d) pool.px[d][s0 + rank[r]] = c[r][d];
-      }
-    }
-    __syncwarp();
-   }
   }
 }
 
@@ -364,9 +375,11 @@ __global__ void k_insert_apply(InsertArgs a) {
       a.nw.ref[o] = d0;
       a.nw.kids[o] = 0;
       a.nw.depth[o] = 0;
-      // the first part keeps the old lower end (leaf 0 stays open below);
-      // later parts start at their first element
-      if (t == 0) {
+      // the first part keeps the old lower end; later parts start at their
+      // first element, and so does the first part of leaf 0, which is open
+      // below and may hold points under its separator (appended ones), so
+      // that the separators stay increasing
+      if (t == 0 && j != 0) {
         a.nw.sk[o] = a.old.sk[j];
         a.nw.si[o] = a.old.si[j];
       } else {
@@ -570,28 +583,179 @@ __global__ void k_delete_leaves(Leaves lv, Pool pool, const int32_t *sbeg, const
   block_count_add(deleted, removed);
 }
 
-__global__ void k_nonempty(const int32_t *cnt, int64_t L, int32_t *keep) {
+// ---- Restoring the leaf wrap after a delete (Sec 4.2) ----------------------
+// A leaf left with fewer than h = max(1, phi / 2) points (an emptied leaf
+// included) is underfull.  Each maximal run of consecutive underfull leaves
+// forms a group with the leaf after it, when there is one; the group's points
+// -- its leaves' points one after another, which in leaf order are
+// consecutive (key, id) ranges -- are re-wrapped into ceil(total / phi)
+// leaves of balanced size in fresh blocks.  Afterwards every leaf but the last
+// of the index holds at least h points.
+
+// start[j]: leaf j begins a run of underfull leaves.
+__global__ void k_wrap_flags(const int32_t *cnt, int64_t L, int h, int32_t *start) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x)
-    keep[j] = cnt[j] > 0;
+    start[j] = cnt[j] < h && (j == 0 || cnt[j - 1] >= h);
 }
 
-template <int D>
-__global__ void k_compact_leaves(Leaves old, Leaves nw, const int32_t *keep, const int64_t *pos, int64_t L) {
+// Group g (numbered by the exclusive scan gx of start): its first leaf gs[g]
+// and its last leaf ge[g] (the leaf after the run, or the run's own last leaf
+// at the end of the index).
+__global__ void k_wrap_bounds(const int32_t *cnt, const int32_t *start, const int64_t *gx, int64_t L, int h,
+                              int32_t *gs, int32_t *ge) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
-    if (!keep[j]) continue;
-    const int64_t o = pos[j];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      nw.lo[d][o] = old.lo[d][j];
-      nw.hi[d][o] = old.hi[d][j];
+    if (start[j]) gs[gx[j]] = (int32_t)j;
+    if (cnt[j] < h && (j + 1 == L || cnt[j + 1] >= h)) ge[gx[j] + start[j] - 1] = (int32_t)(j + 1 < L ? j + 1 : j);
+  }
+}
+
+// Output leaves of each old leaf (a group's re-wrapped leaves are counted at
+// its first leaf, its other leaves give none, a leaf outside every group is
+// kept as it is), the fresh blocks each needs, and whether it is in a group.
+__global__ void k_wrap_plan(const int32_t *cnt, const int32_t *start, const int64_t *gx, const int32_t *ge,
+                            const int64_t *E, int64_t L, int h, int phi, int32_t *outl, int32_t *nblk,
+                            int32_t *ingroup) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+    const bool ig = cnt[j] < h || (j > 0 && cnt[j - 1] < h);
+    ingroup[j] = ig;
+    if (start[j]) {
+      const int64_t e = ge[gx[j]];
+      const int64_t total = E[e] + cnt[e] - E[j];
+      const int r = (int)((total + phi - 1) / phi);
+      outl[j] = r;
+      nblk[j] = r;
+    } else {
+      outl[j] = ig ? 0 : 1;
+      nblk[j] = 0;
     }
-    nw.cnt[o] = old.cnt[j];
-    nw.ref[o] = old.ref[j];
-    nw.kids[o] = 0;
-    nw.depth[o] = 0;
-    // a leaf that becomes the first keeps its own lower end; leaf 0 is open below anyway
-    nw.sk[o] = old.sk[j];
-    nw.si[o] = old.si[j];
+  }
+}
+
+// Sorts, in place, the block of every leaf of a group (a group's points in
+// leaf order are then sorted by (key, id) as a whole).
+template <int D>
+__global__ void k_sort_flagged_leaves(const int32_t *cnt, const uint32_t *ref, const int32_t *flag, int64_t L,
+                                      Pool pool) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < L; j0 += warps * 32) {
+    const int64_t jl = j0 + lane;
+    uint32_t todo = __ballot_sync(0xFFFFFFFFu, jl < L && flag[jl] && cnt[jl] > 1);
+    while (todo) {
+      const int64_t j = j0 + __ffs(todo) - 1;
+      todo &= todo - 1;
+      sort_leaf_block<D>(pool, ref[j], cnt[j]);
+    }
+  }
+}
+
+struct WrapArgs {
+  Leaves old, nw;
+  Pool pool;
+  const int32_t *owner, *start, *ge, *outl;
+  const int64_t *gx, *pos, *boff, *E;
+  int64_t Lnew, base_block;
+  int C;
+};
+
+// A warp takes 32 new leaf positions: a lane copies the descriptor of a kept
+// leaf, then the warp builds each re-wrapped one (part t of its group).
+template <int D>
+__global__ void k_wrap_apply(WrapArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t o0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; o0 < a.Lnew; o0 += warps * 32) {
+    bool part = false;
+    {
+      const int64_t ol = o0 + lane;
+      if (ol < a.Lnew) {
+        const int64_t j = a.owner[ol];
+        if (!a.start[j]) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            a.nw.lo[d][ol] = a.old.lo[d][j];
+            a.nw.hi[d][ol] = a.old.hi[d][j];
+          }
+          a.nw.cnt[ol] = a.old.cnt[j];
+          a.nw.ref[ol] = a.old.ref[j];
+          a.nw.kids[ol] = 0;
+          a.nw.depth[ol] = 0;
+          a.nw.sk[ol] = a.old.sk[j];
+          a.nw.si[ol] = a.old.si[j];
+        } else {
+          part = true;
+        }
+      }
+    }
+    uint32_t todo = __ballot_sync(0xFFFFFFFFu, part);
+    while (todo) {
+      const int64_t o = o0 + __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t j = a.owner[o];
+      const int64_t e = a.ge[a.gx[j]];
+      const int64_t t = o - a.pos[j];
+      const int64_t total = a.E[e] + a.old.cnt[e] - a.E[j];
+      const int r = a.outl[j];
+      const int64_t pa = t * total / r, pb = (t + 1) * total / r;
+      const uint32_t d0 = (uint32_t)((a.base_block + a.boff[j] + t) * a.C);
+      int32_t blo[D], bhi[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        blo[d] = INT32_MAX;
+        bhi[d] = INT32_MIN;
+      }
+      for (int64_t p = pa + lane; p < pb; p += 32) {
+        // the group's leaf holding position p: the last leaf x in [j, e] with E[x] <= E[j] + p
+        const int64_t v = a.E[j] + p;
+        int64_t lo = j, hi = e + 1;
+        while (hi - lo > 1) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (a.E[mid] <= v)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        const uint32_t src = a.old.ref[lo] + (uint32_t)(v - a.E[lo]);
+        const uint32_t dst = d0 + (uint32_t)(p - pa);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int32_t c = a.pool.px[d][src];
+          a.pool.px[d][dst] = c;
+          blo[d] = min(blo[d], c);
+          bhi[d] = max(bhi[d], c);
+        }
+        a.pool.pid[dst] = a.pool.pid[src];
+        a.pool.pkey[dst] = a.pool.pkey[src];
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        blo[d] = __reduce_min_sync(0xFFFFFFFFu, blo[d]);
+        bhi[d] = __reduce_max_sync(0xFFFFFFFFu, bhi[d]);
+      }
+      __syncwarp();
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          a.nw.lo[d][o] = blo[d];
+          a.nw.hi[d][o] = bhi[d];
+        }
+        a.nw.cnt[o] = (int32_t)(pb - pa);
+        a.nw.ref[o] = d0;
+        a.nw.kids[o] = 0;
+        a.nw.depth[o] = 0;
+        // the first part keeps the group's lower end; later parts start at
+        // their first point, and so does the first part of a group at leaf 0
+        // (open below: it may hold points under its separator)
+        if (t == 0 && j != 0) {
+          a.nw.sk[o] = a.old.sk[j];
+          a.nw.si[o] = a.old.si[j];
+        } else {
+          a.nw.sk[o] = a.pool.pkey[d0];
+          a.nw.si[o] = a.pool.pid[d0];
+        }
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -680,8 +844,12 @@ psi_status spac_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
 
   const int64_t base_block = ix->pool_used;
   if ((st = grow_pool(ix, (base_block + NB) * ix->C, base_block * ix->C, s))) return st;
-  PSI_LAUNCH(k_sort_overflow_leaves, warp_grid(ceil_div(L, 32)), 256, 0, s, ix->nodes.cnt, ix->nodes.ref, sbeg.p,
-             send.p, L, ix->C, ix->D, ix->pool);
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_sort_overflow_leaves", k_sort_overflow_leaves<2>, warp_grid(ceil_div(L, 32)), 256, 0, s,
+                     ix->nodes.cnt, ix->nodes.ref, sbeg.p, send.p, L, ix->C, ix->pool);
+  else
+    PSI_LAUNCH_NAMED("k_sort_overflow_leaves", k_sort_overflow_leaves<3>, warp_grid(ceil_div(L, 32)), 256, 0, s,
+                     ix->nodes.cnt, ix->nodes.ref, sbeg.p, send.p, L, ix->C, ix->pool);
 
   NodeArrays na;
   uint64_t *nsk = nullptr;
@@ -745,11 +913,11 @@ psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   Batch b;
   if ((st = sort_batch(ix, pts, ids, m, s, b))) return st;
   const int64_t L = ix->L;
-  Buf<int32_t> bleaf, sbeg, send, keep;
-  Buf<int64_t> pos, tot;
+  Buf<int32_t> bleaf, sbeg, send;
+  Buf<int64_t> tot;
   Buf<unsigned long long> del;
-  if ((st = bleaf.alloc(m, s)) || (st = sbeg.alloc(L, s)) || (st = send.alloc(L, s)) || (st = keep.alloc(L, s)) ||
-      (st = pos.alloc(L, s)) || (st = tot.alloc(2, s)) || (st = del.alloc(1, s)))
+  if ((st = bleaf.alloc(m, s)) || (st = sbeg.alloc(L, s)) || (st = send.alloc(L, s)) || (st = tot.alloc(2, s)) ||
+      (st = del.alloc(1, s)))
     return st;
   PSI_CK(cudaMemsetAsync(sbeg.p, 0, sizeof(int32_t) * L, s));
   PSI_CK(cudaMemsetAsync(send.p, 0, sizeof(int32_t) * L, s));
@@ -776,20 +944,49 @@ psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
       PSI_LAUNCH_NAMED("k_delete_leaves", (k_delete_leaves<3, MAXPL>), g, 256, 0, s, lv, ix->pool, sbeg.p, send.p, L,
                        b.keys, rid.p, rpt.p, del.p);
   }
-  PSI_LAUNCH(k_nonempty, grid_for(L), 256, 0, s, ix->nodes.cnt, L, keep.p);
-  if ((st = scan_i32_to_i64(keep.p, pos.p, L, tot.p, s))) return st;
+  // the leaf wrap (Sec 4.2): runs of leaves left below h points join the leaf
+  // after them and are re-wrapped
+  const int h = std::max(1, ix->phi / 2);
+  Buf<int32_t> start;
+  Buf<int64_t> gx, E;
+  if ((st = start.alloc(L, s)) || (st = gx.alloc(L, s)) || (st = E.alloc(L, s))) return st;
+  PSI_LAUNCH(k_wrap_flags, grid_for(L), 256, 0, s, ix->nodes.cnt, L, h, start.p);
+  if ((st = scan_i32_to_i64(start.p, gx.p, L, tot.p, s))) return st;
   PSI_LAUNCH(k_copy_i64, 1, 1, 0, s, del.p, tot.p + 1);
   if (d_deleted) PSI_CK(cudaMemcpyAsync(d_deleted, tot.p + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-  int64_t h[2];
-  PSI_CK(cudaMemcpyAsync(h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  int64_t h2[2];
+  PSI_CK(cudaMemcpyAsync(h2, tot.p, sizeof(h2), cudaMemcpyDeviceToHost, s));
   PSI_CK(cudaStreamSynchronize(s));
-  const int64_t Lnew = h[0];
-  if (Lnew == L) {  // no leaf emptied: the in-place edits above are the new leaves
-    ix->n -= h[1];
+  const int64_t G = h2[0];
+  ix->n -= h2[1];
+  if (G == 0) {  // no leaf fell below h: the in-place edits above are the new leaves
     if ((st = build_spac_summary(ix, s))) return st;
     PSI_CK(cudaGetLastError());
     return PSI_OK;
   }
+  Buf<int32_t> gs, ge, outl, nblk, ingroup;
+  Buf<int64_t> pos, boff, tot2;
+  if ((st = gs.alloc(G, s)) || (st = ge.alloc(G, s)) || (st = outl.alloc(L, s)) || (st = nblk.alloc(L, s)) ||
+      (st = ingroup.alloc(L, s)) || (st = pos.alloc(L, s)) || (st = boff.alloc(L, s)) || (st = tot2.alloc(3, s)))
+    return st;
+  if ((st = scan_i32_to_i64(ix->nodes.cnt, E.p, L, tot2.p + 2, s))) return st;
+  PSI_LAUNCH(k_wrap_bounds, grid_for(L), 256, 0, s, ix->nodes.cnt, start.p, gx.p, L, h, gs.p, ge.p);
+  PSI_LAUNCH(k_wrap_plan, grid_for(L), 256, 0, s, ix->nodes.cnt, start.p, gx.p, ge.p, E.p, L, h, ix->phi, outl.p,
+             nblk.p, ingroup.p);
+  if ((st = scan_i32_to_i64(outl.p, pos.p, L, tot2.p, s))) return st;
+  if ((st = scan_i32_to_i64(nblk.p, boff.p, L, tot2.p + 1, s))) return st;
+  int64_t h3[2];
+  PSI_CK(cudaMemcpyAsync(h3, tot2.p, sizeof(h3), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  const int64_t Lnew = h3[0], NB = h3[1];
+  const int64_t base_block = ix->pool_used;
+  if ((st = grow_pool(ix, (base_block + NB) * ix->C, base_block * ix->C, s))) return st;
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_sort_flagged_leaves", k_sort_flagged_leaves<2>, warp_grid(ceil_div(L, 32)), 256, 0, s,
+                     ix->nodes.cnt, ix->nodes.ref, ingroup.p, L, ix->pool);
+  else
+    PSI_LAUNCH_NAMED("k_sort_flagged_leaves", k_sort_flagged_leaves<3>, warp_grid(ceil_div(L, 32)), 256, 0, s,
+                     ix->nodes.cnt, ix->nodes.ref, ingroup.p, L, ix->pool);
   NodeArrays na;
   uint64_t *nsk = nullptr;
   uint32_t *nsi = nullptr;
@@ -801,11 +998,36 @@ psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
     DevMem::free(nsi, s);
     return st;
   }
-  Leaves nl = leaves_of(na, nsk, nsi);
-  if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_compact_leaves", k_compact_leaves<2>, grid_for(L), 256, 0, s, lv, nl, keep.p, pos.p, L);
-  else
-    PSI_LAUNCH_NAMED("k_compact_leaves", k_compact_leaves<3>, grid_for(L), 256, 0, s, lv, nl, keep.p, pos.p, L);
+  if (Lnew > 0) {
+    // a group re-wrapped into more than kOwnerInline leaves holds more than
+    // (kOwnerInline - 1) * phi points
+    const int64_t cap_big = ix->n / ((kOwnerInline - 1) * (int64_t)ix->phi) + 1;
+    Buf<int32_t> owner, big;
+    Buf<uint32_t> n_big;
+    if ((st = owner.alloc(Lnew, s)) || (st = big.alloc(cap_big, s)) || (st = n_big.alloc(1, s))) return st;
+    PSI_CK(cudaMemsetAsync(n_big.p, 0, sizeof(uint32_t), s));
+    PSI_LAUNCH(k_owner_scatter, grid_for(L), 256, 0, s, outl.p, pos.p, L, owner.p, big.p, n_big.p, cap_big);
+    PSI_LAUNCH(k_owner_fill_big, num_sms() * 4, 256, 0, s, outl.p, pos.p, big.p, n_big.p, cap_big, owner.p);
+    WrapArgs a;
+    a.old = lv;
+    a.nw = leaves_of(na, nsk, nsi);
+    a.pool = ix->pool;
+    a.owner = owner.p;
+    a.start = start.p;
+    a.ge = ge.p;
+    a.outl = outl.p;
+    a.gx = gx.p;
+    a.pos = pos.p;
+    a.boff = boff.p;
+    a.E = E.p;
+    a.Lnew = Lnew;
+    a.base_block = base_block;
+    a.C = ix->C;
+    if (ix->D == 2)
+      PSI_LAUNCH_NAMED("k_wrap_apply", k_wrap_apply<2>, warp_grid(ceil_div(Lnew, 32)), 256, 0, s, a);
+    else
+      PSI_LAUNCH_NAMED("k_wrap_apply", k_wrap_apply<3>, warp_grid(ceil_div(Lnew, 32)), 256, 0, s, a);
+  }
   free_nodes(ix->nodes, s);
   DevMem::free(ix->sep_key, s);
   DevMem::free(ix->sep_id, s);
@@ -813,7 +1035,7 @@ psi_status spac_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   ix->sep_key = nsk;
   ix->sep_id = nsi;
   ix->L = Lnew;
-  ix->n -= h[1];
+  ix->pool_used = base_block + NB;
   if ((st = build_spac_summary(ix, s))) return st;
   PSI_CK(cudaGetLastError());
   return PSI_OK;

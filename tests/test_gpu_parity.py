@@ -328,6 +328,8 @@ def spac_invariants(ix):
     nxt = np.append(sep[1:], np.array([1 << 100], dtype=object))
     assert all(sep[1:] > sep[:-1])
     assert all((pair < nxt[leaf]) & ((pair >= sep[leaf]) | (leaf == 0)))
+    # the leaf wrap (Sec 4.2): every leaf but the index's last holds at least phi / 2 points
+    assert (cnt[:-1] >= max(1, ix.leaf_size // 2)).all()
 
 
 @pytest.mark.parametrize("kind,dim,bits,phi", [("spac_z", 2, 30, 32), ("spac_h", 2, 30, 32), ("porth", 2, 30, 32),
@@ -383,6 +385,81 @@ def test_updates_match_oracle(kind, dim, bits, phi):
         assert (ix.range_count(T(boxes)).cpu().numpy() == o.range_count(boxes)).all()
         if kind == "porth":
             check_porth_nodes(ix, o)
+
+
+@pytest.mark.parametrize("kind,dim,bits,phi", [("spac_h", 2, 30, 8), ("spac_z", 3, 21, 32), ("spac_h", 2, 30, 2),
+                                               ("spac_z", 2, 30, 64), ("spac_h", 3, 21, 4)])
+def test_delete_restores_the_leaf_wrap(kind, dim, bits, phi):
+    # deletes that leave long runs of underfull and empty leaves, in the middle
+    # and at the end of the key order, then a delete of almost everything
+    n = 200_000
+    p, ids = points(n, dim, bits, 71 + phi, clustered=True)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=phi, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=phi, bits=bits)
+    order = np.lexsort((ids, O.keys(p, dim, KIND[kind], bits)))  # (key, id) order
+    live = np.ones(n, bool)
+    rng = np.random.default_rng(phi)
+    steps = [order[20_000:120_000][rng.random(100_000) < 0.93],   # a long run of underfull leaves
+             order[130_000:131_000],                               # a run of emptied leaves
+             order[190_000:][rng.random(10_000) < 0.99],           # the tail of the key order
+             order[rng.random(n) < 0.999]]                         # almost everything
+    for sel in steps:
+        sel = sel[live[sel]]
+        nd = torch.zeros(1, dtype=torch.int64, device=DEV)
+        ix.delete(T(p[sel]), T(ids[sel]), nd)
+        assert int(nd.item()) == o.delete(p[sel], ids[sel]) == len(sel)
+        live[sel] = False
+        ix.sync()
+        assert len(ix) == len(o) == int(live.sum())
+        gp = ix.points()
+        gi = np.sort(U32(gp["ids"]))
+        assert (gi == np.sort(ids[live])).all()
+        if len(ix):
+            spac_invariants(ix)
+        q = query_points(2000, dim, bits, 5 + phi, p[live] if live.any() else p)
+        gi, gd = ix.knn(T(q), 10)
+        oi, od = o.knn(q, 10)
+        assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
+    # inserts after the re-wraps land in the new leaves
+    newp = gen.varden(30_000, dim, bits, 99)
+    newi = (np.arange(30_000) + 50_000_000).astype(np.uint32)
+    ix.insert(T(newp), T(newi))
+    o.insert(newp, newi)
+    ix.sync()
+    spac_invariants(ix)
+    q = query_points(2000, dim, bits, 6, newp)
+    gi, gd = ix.knn(T(q), 10)
+    oi, od = o.knn(q, 10)
+    assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+@pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
+def test_inserts_below_the_first_key_keep_separators_increasing(kind):
+    # leaf 0 is open below: points under its separator are appended to it, and
+    # when it overflows its re-wrapped parts must keep the separators
+    # increasing, or later batches would be routed to the wrong leaves
+    bits = 30
+    p, ids = points(5000, 2, bits, 81)
+    p = p | (1 << 20)  # every base point away from the curve's start at (0, 0)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=8, coord_bits=bits)
+    o = O.Index(p, ids, kind=KIND[kind], phi=8, bits=bits)
+    for step in range(3):
+        lowp = (gen.uniform(40, 2, bits, 7 + step) >> 12).astype(np.int32)  # keys below every base key
+        lowi = (np.arange(40) + 1_000_000 * (step + 1)).astype(np.uint32)
+        ix.insert(T(lowp), T(lowi))
+        o.insert(lowp, lowi)
+        ix.sync()
+        spac_invariants(ix)
+    # every low point can be deleted again (it is routed to the leaf holding it)
+    lo_all = np.concatenate([(gen.uniform(40, 2, bits, 7 + st) >> 12).astype(np.int32) for st in range(3)])
+    lo_ids = np.concatenate([(np.arange(40) + 1_000_000 * (st + 1)).astype(np.uint32) for st in range(3)])
+    nd = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ix.delete(T(lo_all), T(lo_ids), nd)
+    assert int(nd.item()) == o.delete(lo_all, lo_ids) == 120
+    ix.sync()
+    spac_invariants(ix)
+    gi = np.sort(U32(ix.points()["ids"]))
+    assert (gi == np.sort(ids)).all()
 
 
 def test_insert_into_empty_and_delete_everything():
