@@ -148,6 +148,7 @@ struct EncodeSpec {
 struct SortResult {
   uint64_t *keys;
   uint32_t *vals;
+  int prefix_low = 0;  // > 0: sorted by key bits [prefix_low, key_bits) only (then runs fixed up)
 };
 
 // Sorts n pairs.  If enc.pts is non-null the keys are computed from the points

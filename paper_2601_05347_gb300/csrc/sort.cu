@@ -56,6 +56,9 @@ struct EventGuard {
   }
 };
 constexpr int64_t kPackMin = int64_t(1) << 22;  // smallest encoding sort that may pack
+constexpr int kPrefixBits = 48;                   // key bits sorted by a prefix sort
+constexpr int kPrefixShort = 8;                   // longest run fixed in registers
+constexpr int64_t kPrefixMin = int64_t(1) << 20;  // smallest encoding sort that may sort a prefix only
 
 // Digit width RB in {8, 10, 11}: RADIX digits, DPT digits per thread in the
 // tile epilogue; per-warp counters fit 16 bits (a warp ranks 512 keys).
@@ -124,6 +127,16 @@ enum : int {
   IO_UNPACK = 3,  // packed word in, (key from the point, value) out
 };
 
+// Optional extras of the histogram pass: the histogram of an alternative
+// first digit ((key >> alt_shift) & mask, into hist_alt) and a second count of
+// input neighbours agreeing above near2_shift.
+struct HistExtra {
+  uint32_t *hist_alt = nullptr;
+  int alt_shift = 0;
+  unsigned long long *near2 = nullptr;
+  int near2_shift = 0;
+};
+
 // Digit histograms of all passes in one read; when encoding with kst set, the
 // keys are also written out (in input order) for the digit passes to read.  With 8-bit digits the counts go
 // to 4 shared copies (lane % 4 picks one) so that lanes of a warp hitting the
@@ -131,17 +144,22 @@ enum : int {
 template <int MODE, int D, int CURVE, int RB>
 __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const int32_t *pts, int bits, int key_shift,
                                                    int64_t n, int passes, uint32_t *hist, int *status,
-                                                   uint64_t *kst, unsigned long long *near, int near_shift) {
+                                                   uint64_t *kst, unsigned long long *near, int near_shift,
+                                                   HistExtra ex) {
   using R = Radix<RB>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][passes][RADIX]
-  uint8_t *htab = smem_raw + sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX;
-  for (int i = threadIdx.x; i < R::HIST_PARTS * passes * R::RADIX; i += blockDim.x) shp[i] = 0;
+  // one counter section per counted digit: the passes' digits, then the
+  // alternative first digit (ex.hist_alt)
+  const int secs = passes + (ex.hist_alt ? 1 : 0);
+  uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][secs][RADIX]
+  uint8_t *htab = smem_raw + sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX;
+  for (int i = threadIdx.x; i < R::HIST_PARTS * secs * R::RADIX; i += blockDim.x) shp[i] = 0;
   if (MODE == 1) curve_table_init<D, CURVE>(htab);
   __syncthreads();
   bool bad_any = false;
-  uint32_t n_near = 0;  // input neighbours (i, i + 1) whose keys agree above near_shift
-  uint32_t *mine = shp + (threadIdx.x % R::HIST_PARTS) * passes * R::RADIX;
+  uint32_t n_near = 0;   // input neighbours (i, i + 1) whose keys agree above near_shift
+  uint32_t n_near2 = 0;  // ... above ex.near2_shift
+  uint32_t *mine = shp + (threadIdx.x % R::HIST_PARTS) * secs * R::RADIX;
   // HIST_U items per thread per round, their loads issued together
   const int64_t chunk = (int64_t)blockDim.x * HIST_U;
   const int64_t stride = (int64_t)gridDim.x * chunk;
@@ -174,20 +192,23 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
         }
       }
     }
-    if (near) {
+    if (near || ex.near2) {
 #pragma unroll
       for (int u = 0; u < HIST_U; ++u) {
         const uint64_t kn = __shfl_down_sync(0xFFFFFFFFu, k[u], 1);
         const bool okn = __shfl_down_sync(0xFFFFFFFFu, ok[u], 1);
-        n_near += (threadIdx.x & 31) < 31 && ok[u] && okn && ((k[u] ^ kn) >> near_shift) == 0;
+        const bool pair = (threadIdx.x & 31) < 31 && ok[u] && okn;
+        n_near += pair && ((k[u] ^ kn) >> near_shift) == 0;
+        n_near2 += pair && ((k[u] ^ kn) >> ex.near2_shift) == 0;
       }
     }
 #pragma unroll
     for (int u = 0; u < HIST_U; ++u) {
       const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok[u]);
       if (ok[u]) {
-        for (int p = 0; p < passes; ++p) {
-          uint32_t dg = (uint32_t)(k[u] >> (p * RB)) & (R::RADIX - 1);
+        for (int p = 0; p < secs; ++p) {
+          const int sh = p < passes ? p * RB : ex.alt_shift;
+          uint32_t dg = (uint32_t)(k[u] >> sh) & (R::RADIX - 1);
           int all_same;
           __match_all_sync(act, dg, &all_same);
           if (all_same) {
@@ -201,12 +222,13 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   }
   if (bad_any) atomicOr(status, ST_RANGE);
   if (near) block_count_add(near, n_near);
+  if (ex.near2) block_count_add(ex.near2, n_near2);
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * R::RADIX; i += blockDim.x) {
+  for (int i = threadIdx.x; i < secs * R::RADIX; i += blockDim.x) {
     uint32_t v = 0;
 #pragma unroll
-    for (int q = 0; q < R::HIST_PARTS; ++q) v += shp[q * passes * R::RADIX + i];
-    if (v) atomicAdd(&hist[i], v);
+    for (int q = 0; q < R::HIST_PARTS; ++q) v += shp[q * secs * R::RADIX + i];
+    if (v) atomicAdd(i < passes * R::RADIX ? &hist[i] : &ex.hist_alt[i - passes * R::RADIX], v);
   }
 }
 
@@ -615,6 +637,178 @@ __global__ __launch_bounds__(1024) void k_tie_long(const uint64_t *keys, uint32_
   }
 }
 
+// ---- Runs of a sort on the top key bits only ----------------------------
+// A sort on key bits [low, key_bits) leaves each run of keys equal in those
+// bits in input order; the run is then put in (key, id) order.  A run of up to
+// kPrefixShort is sorted by one thread with a register sorting network (ids
+// are read only to order equal keys); longer runs are listed for
+// k_prefix_long.
+
+__device__ __forceinline__ bool key_id_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb, const uint32_t *ids) {
+  return ka < kb || (ka == kb && ids[va] < ids[vb]);
+}
+
+// Compare-exchange of two (key, value) slots of a register sorting network by
+// (key, id): ids are read only when the keys are equal (duplicate points).
+__device__ __forceinline__ void prefix_cx(uint64_t &ka, uint32_t &va, uint64_t &kb, uint32_t &vb,
+                                          const uint32_t *ids) {
+  if (key_id_less(kb, vb, ka, va, ids)) {
+    const uint64_t k = ka;
+    ka = kb;
+    kb = k;
+    const uint32_t v = va;
+    va = vb;
+    vb = v;
+  }
+}
+
+// Odd-even transposition network over the first `rounds` slots (rounds =
+// the run's length, at most N): sorts them by (key, id).
+template <int N>
+__device__ __forceinline__ void prefix_network(uint64_t (&k)[kPrefixShort], uint32_t (&v)[kPrefixShort], int len,
+                                               const uint32_t *ids) {
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int j = r & 1; j + 1 < N; j += 2)
+      if (j + 1 < len) prefix_cx(k[j], v[j], k[j + 1], v[j + 1], ids);
+}
+
+// kPrefixU elements per thread (a block takes kPrefixU * blockDim consecutive
+// elements, coalesced): the keys of all of a thread's elements and their
+// neighbours are requested before any is compared, so that many loads are in
+// flight; a thread whose element starts a run (rare: most elements differ from
+// both neighbours in their top bits) reads the rest of it and sorts it in
+// registers with a network sized to the run.
+constexpr int kPrefixU = 4;
+
+__global__ __launch_bounds__(256) void k_prefix_runs(uint64_t *keys, uint32_t *vals, const uint32_t *ids, int64_t n,
+                                                     int low, int64_t *long_runs, uint32_t *n_long,
+                                                     int64_t cap_long) {
+  const int64_t chunk = (int64_t)blockDim.x * kPrefixU;
+  for (int64_t b0 = (int64_t)blockIdx.x * chunk; b0 < n; b0 += (int64_t)gridDim.x * chunk) {
+    uint64_t kp[kPrefixU], kc[kPrefixU], kn[kPrefixU];
+#pragma unroll
+    for (int u = 0; u < kPrefixU; ++u) {
+      const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      kc[u] = i < n ? keys[i] : ~0ull;
+      kp[u] = i > 0 && i < n ? keys[i - 1] : ~0ull;
+      kn[u] = i + 1 < n ? keys[i + 1] : ~0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kPrefixU; ++u) {
+      const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+      const uint64_t p = kc[u] >> low;
+      const bool with_prev = i > 0 && i < n && (kp[u] >> low) == p;
+      const bool with_next = i + 1 < n && (kn[u] >> low) == p;
+      if (!with_next || with_prev) continue;  // not the start of a run of two or more
+      uint64_t k[kPrefixShort];
+      uint32_t v[kPrefixShort];
+      k[0] = kc[u];
+      k[1] = kn[u];
+      v[0] = vals[i];
+      v[1] = vals[i + 1];
+      uint64_t k2 = i + 2 < n ? keys[i + 2] : ~0ull;
+      int len = 2;
+#pragma unroll
+      for (int j = 2; j < kPrefixShort; ++j) {
+        k[j] = ~0ull;  // past the run: above every key, never moved before a member
+        v[j] = 0;
+        if (len == j) {
+          const uint64_t kj = j == 2 ? k2 : (i + j < n ? keys[i + j] : ~0ull);
+          if (i + j < n && (kj >> low) == p) {
+            k[j] = kj;
+            v[j] = vals[i + j];
+            ++len;
+          }
+        }
+      }
+      if (len == kPrefixShort && i + kPrefixShort < n && (keys[i + kPrefixShort] >> low) == p) {
+        const uint32_t slot = atomicAdd(n_long, 1u);
+        if (slot < cap_long) long_runs[slot] = i;
+        continue;
+      }
+      if (len == 2)
+        prefix_network<2>(k, v, len, ids);
+      else if (len <= 4)
+        prefix_network<4>(k, v, len, ids);
+      else
+        prefix_network<kPrefixShort>(k, v, len, ids);
+#pragma unroll
+      for (int j = 0; j < kPrefixShort; ++j)
+        if (j < len) {
+          keys[i + j] = k[j];
+          vals[i + j] = v[j];
+        }
+    }
+  }
+}
+
+// One block per long run: bitonic sort by (key, id) (ids are unique, so no
+// stability is needed).  Runs up to kSmemRun sort in shared memory, longer
+// ones in place in global memory.
+__global__ __launch_bounds__(1024) void k_prefix_long(uint64_t *keys, uint32_t *vals, const uint32_t *ids, int64_t n,
+                                                      int low, const int64_t *long_runs, const uint32_t *n_long,
+                                                      int64_t cap_long) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);
+  uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kSmemRun);
+  uint32_t *si = sv + kSmemRun;
+  const int64_t runs = min((int64_t)*n_long, cap_long);
+  for (int64_t r = blockIdx.x; r < runs; r += gridDim.x) {
+    const int64_t s = long_runs[r];
+    const uint64_t p = keys[s] >> low;
+    int64_t lo = s, hi = n;  // first index past the run
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if ((keys[mid] >> low) == p)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int64_t len = lo - s;
+    if (len <= kSmemRun) {
+      for (int64_t j = threadIdx.x; j < len; j += blockDim.x) {
+        sk[j] = keys[s + j];
+        sv[j] = vals[s + j];
+        si[j] = ids[sv[j]];
+      }
+      __syncthreads();
+      bitonic_ascending(
+          len, [&](int64_t a, int64_t b) { return sk[a] < sk[b] || (sk[a] == sk[b] && si[a] < si[b]); },
+          [&](int64_t a, int64_t b) {
+            const uint64_t x = sk[a];
+            sk[a] = sk[b];
+            sk[b] = x;
+            uint32_t y = sv[a];
+            sv[a] = sv[b];
+            sv[b] = y;
+            y = si[a];
+            si[a] = si[b];
+            si[b] = y;
+          });
+      for (int64_t j = threadIdx.x; j < len; j += blockDim.x) {
+        keys[s + j] = sk[j];
+        vals[s + j] = sv[j];
+      }
+      __syncthreads();
+    } else {
+      uint64_t *kk = keys + s;
+      uint32_t *vv = vals + s;
+      bitonic_ascending(
+          len, [&](int64_t a, int64_t b) { return key_id_less(kk[a], vv[a], kk[b], vv[b], ids); },
+          [&](int64_t a, int64_t b) {
+            const uint64_t x = kk[a];
+            kk[a] = kk[b];
+            kk[b] = x;
+            const uint32_t y = vv[a];
+            vv[a] = vv[b];
+            vv[b] = y;
+          });
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -622,17 +816,17 @@ __global__ __launch_bounds__(1024) void k_tie_long(const uint64_t *keys, uint32_
 template <int MODE, int D, int CURVE, int RB>
 static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_t n, int passes, uint32_t *hist,
                               int *status, cudaStream_t s, uint64_t *kst = nullptr,
-                              unsigned long long *near = nullptr, int near_shift = 0) {
+                              unsigned long long *near = nullptr, int near_shift = 0, HistExtra ex = HistExtra()) {
   using R = Radix<RB>;
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
-  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * passes * R::RADIX + kCurveTabBytes;
+  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX + kCurveTabBytes;
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // all blocks resident at once (the grid-stride rounds stay balanced)
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) per_sm = 0;
   const int grid = (int)std::min<int64_t>(ceil_div(n, 256 * HIST_U), (int64_t)num_sms() * std::max(per_sm, 1));
   PSI_LAUNCH_NAMED("k_sort_hist", kern, std::max(grid, 1), 256, smem, s, kin, enc.pts, enc.bits, enc.key_shift, n,
-                   passes, hist, status, kst, near, near_shift);
+                   passes, hist, status, kst, near, near_shift, ex);
   return PSI_OK;
 }
 
@@ -670,20 +864,38 @@ static int pick_radix(int /*key_bits*/, int requested) {
 template <int RB>
 static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, const uint32_t *vals_in, int64_t n,
                                 int key_bits, uint64_t *kbuf0, uint32_t *vbuf0, uint64_t *kbuf1, uint32_t *vbuf1,
-                                int *d_status, cudaStream_t s, SortResult *out) {
+                                int *d_status, cudaStream_t s, SortResult *out, bool may_prefix) {
   using R = Radix<RB>;
   const bool encode = enc.pts != nullptr;
-  const int passes = (key_bits + RB - 1) / RB;
+  const int passes_full = (key_bits + RB - 1) / RB;
   const int64_t tiles = ceil_div(n, TILE);
+  // Decisions taken on the host from counts of the histogram pass are not
+  // possible while the stream is being captured.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();  // a refused query: take no host decision, leave no error behind
+    cs = cudaStreamCaptureStatusActive;
+  }
+  const bool capturing = cs != cudaStreamCaptureStatusNone;
+  // Prefix sort: an encoding sort whose equal keys are put in id order
+  // afterwards anyway (may_prefix) sorts only the top kPrefixBits key bits
+  // when the keys are unlikely to share them much: the histogram pass counts
+  // input neighbours whose keys agree in those bits, and fewer than half
+  // must.  Each run of equal top bits is then sorted by (key, id).
+  const int low_c = key_bits - kPrefixBits;
+  const bool pref_cand = may_prefix && encode && RB == 8 && n >= kPrefixMin && low_c > 0 &&
+                         (key_bits - low_c + RB - 1) / RB < passes_full && !capturing;
+  const bool pack_cand = encode && RB == 8 && n >= kPackMin && !capturing;
   Buf<uint32_t> hist, lookback, ctr;
   psi_status st;
+  // digit counts: a section per pass, then the prefix sort's first digit;
   // two look-back tables used alternately: pass p clears the table of pass p+1
-  if ((st = hist.alloc((size_t)passes * R::RADIX, s)) ||
-      (st = lookback.alloc((size_t)2 * tiles * R::RADIX, s)) || (st = ctr.alloc(passes, s)))
+  if ((st = hist.alloc((size_t)(passes_full + 1) * R::RADIX, s)) ||
+      (st = lookback.alloc((size_t)2 * tiles * R::RADIX, s)) || (st = ctr.alloc(passes_full, s)))
     return st;
-  PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * passes * R::RADIX, s));
+  PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * (passes_full + 1) * R::RADIX, s));
   PSI_CK(cudaMemsetAsync(lookback.p, 0, sizeof(uint32_t) * tiles * R::RADIX, s));
-  PSI_CK(cudaMemsetAsync(ctr.p, 0, sizeof(uint32_t) * passes, s));
+  PSI_CK(cudaMemsetAsync(ctr.p, 0, sizeof(uint32_t) * passes_full, s));
 
   // Hilbert keys cost more arithmetic than their 8-byte write and read: the
   // histogram pass computes them once and writes them out; the first digit
@@ -699,72 +911,83 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   // passes-2 move those words alone; the last pass writes the pairs again,
   // reading each key (or point) at its position.  Those reads are local only
   // when the input is: the histogram pass counts input neighbours whose keys
-  // share their top 24 bits, and the sort packs when at least half do.  Not
-  // during stream capture (the count is read on the host).
-  int pk = passes, p_pack = passes;
-  int kr = 0, drop = 0;
-  if (encode && RB == 8 && n >= kPackMin) {
-    const int vbits = 64 - __builtin_clzll((uint64_t)(n - 1));
-    int p = 1;
-    while (p < passes && vbits + key_bits - RB * (p + 1) > 64) ++p;
-    if (p + 2 <= passes - 1) p_pack = p;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (p_pack < passes && cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
-      cudaGetLastError();  // a refused query: sort unpacked, leave no error behind
-      p_pack = passes;
-    }
-    if (cs != cudaStreamCaptureStatusNone) p_pack = passes;
-  }
-  // the count reaches the host through a pinned word behind an event, read
-  // only when pass p_pack is about to be launched (the passes before it are
-  // queued meanwhile).  One word per host thread, allocated on its first
-  // packing sort and kept for the thread's lifetime (a sort on that thread
-  // finishes with the word before the next one starts).
+  // share their top 24 bits, and the sort packs when at least half do.
+  // The counts reach the host through pinned words behind an event, read when
+  // the first decision needs them (the prefix decision before pass 0; else
+  // the packing decision just before the pack pass, the passes before it
+  // queued meanwhile).  Two words per host thread, allocated on its first
+  // such sort and kept for the thread's lifetime.
   static thread_local unsigned long long *h_near = nullptr;
-  if (p_pack < passes && !h_near &&
-      cudaHostAlloc((void **)&h_near, sizeof(unsigned long long), cudaHostAllocPortable) != cudaSuccess) {
+  bool counts = pref_cand || pack_cand;
+  if (counts && !h_near &&
+      cudaHostAlloc((void **)&h_near, 2 * sizeof(unsigned long long), cudaHostAllocPortable) != cudaSuccess) {
     cudaGetLastError();
     h_near = nullptr;
-    p_pack = passes;
+    counts = false;
   }
   Buf<unsigned long long> nearc;
   EventGuard near_ev;
-  if (p_pack < passes && cudaEventCreateWithFlags(&near_ev.e, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();  // e.g. another thread capturing in global mode: sort unpacked
+  if (counts && cudaEventCreateWithFlags(&near_ev.e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();  // e.g. another thread capturing in global mode: no host decisions
     near_ev.e = nullptr;
-    p_pack = passes;
+    counts = false;
   }
-  if (p_pack < passes) {
-    if ((st = nearc.alloc(1, s))) return st;
-    PSI_CK(cudaMemsetAsync(nearc.p, 0, sizeof(unsigned long long), s));
+  if (counts) {
+    if ((st = nearc.alloc(2, s))) return st;
+    PSI_CK(cudaMemsetAsync(nearc.p, 0, 2 * sizeof(unsigned long long), s));
   }
   const int near_shift = std::max(0, key_bits - 24);
+  HistExtra ex;
+  if (counts && pref_cand) {
+    ex.hist_alt = hist.p + (size_t)passes_full * R::RADIX;
+    ex.alt_shift = low_c;
+    ex.near2 = nearc.p + 1;
+    ex.near2_shift = low_c;
+  }
+  unsigned long long *nearp = counts ? nearc.p : nullptr;
 
-  // digit 0 is counted up front; every pass counts the next digit of its keys
+  // the first digit is counted up front; every pass counts the next digit of its keys
   if (!encode)
     st = launch_hist<0, 2, 0, RB>(keys_in, enc, n, 1, hist.p, d_status, s);
   else if (enc.dim == 2 && enc.curve == CURVE_MORTON)
-    st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s, nullptr, nearc.p, near_shift);
+    st = launch_hist<1, 2, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s, nullptr, nearp, near_shift, ex);
   else if (enc.dim == 2)
-    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p, nearc.p, near_shift);
+    st = launch_hist<1, 2, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p, nearp, near_shift, ex);
   else if (enc.curve == CURVE_MORTON)
-    st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s, nullptr, nearc.p, near_shift);
+    st = launch_hist<1, 3, 0, RB>(nullptr, enc, n, 1, hist.p, d_status, s, nullptr, nearp, near_shift, ex);
   else
-    st = launch_hist<1, 3, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p, nearc.p, near_shift);
+    st = launch_hist<1, 3, 1, RB>(nullptr, enc, n, 1, hist.p, d_status, s, kst.p, nearp, near_shift, ex);
   if (st) return st;
-  if (p_pack < passes) {
-    PSI_CK(cudaMemcpyAsync(h_near, nearc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  bool synced = false;
+  if (counts) {
+    PSI_CK(cudaMemcpyAsync(h_near, nearc.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     PSI_CK(cudaEventRecord(near_ev.e, s));
+  }
+  int low = 0;
+  if (counts && pref_cand) {
+    PSI_CK(cudaEventSynchronize(near_ev.e));
+    synced = true;
+    if (2 * h_near[1] < (unsigned long long)n) low = low_c;
+  }
+  const int passes = (key_bits - low + RB - 1) / RB;
+  int pk = passes, p_pack = passes;
+  int kr = 0, drop = 0;
+  if (counts && pack_cand) {
+    const int vbits = 64 - __builtin_clzll((uint64_t)(n - 1));
+    int p = 1;
+    while (p < passes && vbits + (key_bits - low) - RB * (p + 1) > 64) ++p;
+    if (p + 2 <= passes - 1) p_pack = p;
   }
 
   uint64_t *kb[2] = {kbuf0, kbuf1};
   uint32_t *vb[2] = {vbuf0, vbuf1};
   for (int p = 0; p < passes; ++p) {
     if (p == p_pack) {
-      PSI_CK(cudaEventSynchronize(near_ev.e));
-      if (2 * *h_near >= (unsigned long long)n) {
+      if (!synced) PSI_CK(cudaEventSynchronize(near_ev.e));
+      synced = true;
+      if (2 * h_near[0] >= (unsigned long long)n) {
         pk = p_pack;
-        drop = RB * (pk + 1);
+        drop = low + RB * (pk + 1);
         kr = key_bits - drop;
       }
     }
@@ -778,18 +1001,18 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     a.bits = enc.bits;
     a.key_shift = enc.key_shift;
     a.n = n;
-    a.shift = p * RB;
+    a.shift = low + p * RB;
     a.gbase = nullptr;
-    a.hist_cur = hist.p + p * R::RADIX;
+    a.hist_cur = (p == 0 && low) ? hist.p + (size_t)passes_full * R::RADIX : hist.p + p * R::RADIX;
     a.hist_next = p + 1 < passes ? hist.p + (p + 1) * R::RADIX : nullptr;
-    a.shift_next = (p + 1) * RB;
+    a.shift_next = low + (p + 1) * RB;
     a.lookback = lookback.p + (size_t)(p & 1) * tiles * R::RADIX;
     a.lookback_next = p + 1 < passes ? lookback.p + (size_t)((p + 1) & 1) * tiles * R::RADIX : nullptr;
     a.tile_ctr = ctr.p + p;
     a.status = d_status;
     if (p > pk) {
-      a.shift = p * RB - drop;
-      a.shift_next = (p + 1) * RB - drop;
+      a.shift = low + p * RB - drop;
+      a.shift_next = low + (p + 1) * RB - drop;
       a.kmask = (1ull << kr) - 1;
     }
     a.kr = kr;
@@ -808,6 +1031,7 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   }
   out->keys = kb[(passes - 1) & 1];
   out->vals = vb[(passes - 1) & 1];
+  out->prefix_low = low;
   return PSI_OK;
 }
 
@@ -827,13 +1051,14 @@ psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint
   psi_status st;
   switch (pick_radix(key_bits, radix_bits)) {
     case 10:
-      st = sort_pairs_rb<10>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out);
+      st = sort_pairs_rb<10>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out, false);
       break;
     case 11:
-      st = sort_pairs_rb<11>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out);
+      st = sort_pairs_rb<11>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out, false);
       break;
     default:
-      st = sort_pairs_rb<8>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out);
+      st = sort_pairs_rb<8>(enc, keys_in, vals_in, n, key_bits, kbuf0, vbuf0, kbuf1, vbuf1, d_status, s, out,
+                            tie_ids != nullptr);
   }
   if (st) return st;
 
@@ -844,9 +1069,21 @@ psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint
     if ((st = runs.alloc(cap_long, s))) return st;
     if ((st = nlong.alloc(1, s))) return st;
     PSI_CK(cudaMemsetAsync(nlong.p, 0, sizeof(uint32_t), s));
-    PSI_LAUNCH(k_tie_runs, (unsigned)ceil_div(n, 256), 256, 0, s, out->keys, out->vals, tie_ids, n, runs.p, nlong.p,
-               cap_long);
-    PSI_LAUNCH(k_tie_long, num_sms(), 1024, 0, s, out->keys, out->vals, tie_ids, n, runs.p, nlong.p, cap_long);
+    if (out->prefix_low > 0) {  // runs of equal top bits in (key, id) order (equal keys included)
+      const int64_t cap_plong = n / (kPrefixShort + 1) + 1;
+      if ((st = runs.alloc(cap_plong, s))) return st;
+      const size_t smem = (size_t)kSmemRun * (sizeof(uint64_t) + 2 * sizeof(uint32_t));
+      PSI_CK(cudaFuncSetAttribute(k_prefix_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int gr = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256 * kPrefixU), (int64_t)num_sms() * 8));
+      PSI_LAUNCH(k_prefix_runs, gr, 256, 0, s, out->keys, out->vals, tie_ids, n, out->prefix_low, runs.p, nlong.p,
+                 cap_plong);
+      PSI_LAUNCH(k_prefix_long, num_sms(), 1024, smem, s, out->keys, out->vals, tie_ids, n, out->prefix_low, runs.p,
+                 nlong.p, cap_plong);
+    } else {
+      PSI_LAUNCH(k_tie_runs, (unsigned)ceil_div(n, 256), 256, 0, s, out->keys, out->vals, tie_ids, n, runs.p,
+                 nlong.p, cap_long);
+      PSI_LAUNCH(k_tie_long, num_sms(), 1024, 0, s, out->keys, out->vals, tie_ids, n, runs.p, nlong.p, cap_long);
+    }
   }
   PSI_CK(cudaGetLastError());
   return PSI_OK;

@@ -168,6 +168,32 @@ def test_build_across_the_packed_sort_threshold(kind, dim, bits, n, clustered):
         check_spac_layout(ix, o)
 
 
+@pytest.mark.parametrize("kind,dim,bits,n,region", [("spac_z", 2, 30, (1 << 20) + 17, 15),
+                                                    ("spac_h", 2, 30, (1 << 20) + 3, 12),
+                                                    ("spac_z", 2, 30, (1 << 20) + 13, 9),
+                                                    ("porth", 2, 30, (1 << 20) + 9, 15),
+                                                    ("spac_z", 3, 21, (1 << 20) + 1, 21),
+                                                    ("spac_h", 3, 21, (1 << 20) + 11, 11),
+                                                    ("spac_h", 2, 30, (1 << 20) + 5, 30)])
+def test_build_prefix_sort_runs(kind, dim, bits, n, region):
+    # an encoding sort of at least 2^20 pairs whose input neighbours rarely
+    # share their top 48 key bits (points in random order) sorts those bits
+    # only, then puts each run of equal top bits in (key, id) order: points in
+    # [0, 2^region)^dim give runs of up to a few points (fixed in registers),
+    # about 250 (fixed in shared memory) and 1.6e4 (fixed in global memory),
+    # with duplicate points among them
+    p = gen.uniform(n, dim, region, 500 + n % 1000).astype(np.int32)
+    perm = np.argsort(gen.splitmix64(n, np.arange(n, dtype=np.uint64)), kind="stable").astype(np.uint64)
+    with np.errstate(over="ignore"):
+        ids = ((perm * np.uint64(2654435761) + np.uint64(7)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
+    if kind == "porth":
+        check_porth_nodes(ix, o)
+    else:
+        check_spac_layout(ix, o)
+
+
 @pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
 @pytest.mark.parametrize("dup", [False, True])
 def test_spac_build_layout_3d_and_duplicates(kind, dup):
