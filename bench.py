@@ -971,7 +971,8 @@ def run_config2(n=100_000_000):
     return out
 
 
-def run_incremental(n=100_000_000, ratios=(0.1, 0.01, 0.001, 0.0001), nq=10_000_000):
+def run_incremental(n=100_000_000, ratios=(0.1, 0.01, 0.001, 0.0001), nq=10_000_000,
+                    dists=("uniform", "sweepline", "varden"), kinds=("spac_h", "spac_z", "porth")):
     """Incremental construction and destruction (Sec 5.1): the index is built by n/b batch inserts of
     consecutive slices of the point array (b = ratio * n) starting from an empty index, then emptied by
     n/b batch deletes in the same order; 10-NN queries at data points are timed after half of the batches.
@@ -982,17 +983,14 @@ def run_incremental(n=100_000_000, ratios=(0.1, 0.01, 0.001, 0.0001), nq=10_000_
     out = {}
     empty_p = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
     empty_i = torch.zeros(0, dtype=torch.int32, device="cuda")
-    for dist in ("uniform", "sweepline", "varden"):
+    for dist in dists:
         seed = gen.config_seed(5, {"uniform": 0, "sweepline": 1, "varden": 2}[dist])
         pts = {"uniform": gen.uniform, "sweepline": gen.sweepline, "varden": gen.varden}[dist](n, 2, BITS, seed)
         dp, di = T(pts), T(np.arange(n, dtype=np.uint32))
         dq = T(pts[gen.sample_with_replacement(n, nq, seed + 1)])
-        for kind in ("spac_h", "spac_z", "porth"):
+        for kind in kinds:
             for ratio in ratios:
                 key = f"{dist}/{kind}/{ratio * 100:g}pct"
-                if kind == "porth" and ratio < 0.001:
-                    out[key] = {"skipped": "P-Orth batch updates re-derive the whole tree (O(n) per batch)"}
-                    continue
                 b = max(1, int(n * ratio))
                 nb = (n + b - 1) // b
                 r = {"batches": nb}
@@ -1231,6 +1229,9 @@ def main():
     ap.add_argument("--serve", action="store_true", help="only the served configuration at 5e8 resident points")
     ap.add_argument("--configs", action="store_true",
                     help="the 2D uniform 1e6, 2D clustered update-batch and 3D 1e8 configurations")
+    ap.add_argument("--inc-dists", default="uniform,sweepline,varden", help="workloads of --incremental")
+    ap.add_argument("--inc-kinds", default="spac_h,spac_z,porth", help="indexes of --incremental")
+    ap.add_argument("--inc-ratios", default="0.1,0.01,0.001,0.0001", help="batch sizes of --incremental")
     ap.add_argument("--incremental", action="store_true",
                     help="incremental construction/destruction by 10%%..0.01%% batches (Uniform, Sweepline, Varden)")
     args = ap.parse_args()
@@ -1251,7 +1252,10 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         print(json.dumps({"metric": "incremental construction / destruction, 1e8 2D points",
-                          "incremental": run_incremental(args.n or 100_000_000)}), flush=True)
+                          "incremental": run_incremental(
+                              args.n or 100_000_000, tuple(float(x) for x in args.inc_ratios.split(",")),
+                              dists=tuple(args.inc_dists.split(",")), kinds=tuple(args.inc_kinds.split(",")))}),
+              flush=True)
     elif args.serve:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

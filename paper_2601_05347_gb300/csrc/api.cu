@@ -192,6 +192,7 @@ static void destroy_index(psi_index *ix) {
   DevMem::free(ix->sep_key, s);
   DevMem::free(ix->sep_id, s);
   DevMem::free(ix->leaf_node, s);
+  free_pleaves(ix->pl, s);
   DevMem::free(ix->d_status, s);
   delete ix;
 }

@@ -49,6 +49,19 @@ struct Pool {
   int64_t cap_slots = 0;
 };
 
+// P-Orth leaf list in key order (leaf i is node leaf_node[i]): the slot range
+// [ref, ref + cnt) of its points in the pool (sorted by (key, id)), its cell
+// depth, the first key of its cell and its tight box.
+struct PLeaves {
+  uint32_t *ref = nullptr;
+  int32_t *cnt = nullptr;
+  int32_t *depth = nullptr;
+  uint64_t *key = nullptr;
+  int32_t *lo[3] = {nullptr, nullptr, nullptr};
+  int32_t *hi[3] = {nullptr, nullptr, nullptr};
+  int64_t cap = 0;
+};
+
 }  // namespace psi
 
 struct psi_index {
@@ -68,9 +81,11 @@ struct psi_index {
   // SPaC leaves (= nodes [0, L)): lower end of each leaf's (key, id) range.
   uint64_t *sep_key = nullptr;
   uint32_t *sep_id = nullptr;
-  // P-Orth: leaf list in key order (node ids), used by updates.
+  // P-Orth: leaf list in key order (node ids, and the leaves' records), used
+  // by updates.
   int32_t *leaf_node = nullptr;
   int64_t leaf_cap = 0;
+  psi::PLeaves pl;
 
   int *d_status = nullptr;
   std::vector<int64_t> level_off, level_size;  // SPaC summary levels
@@ -101,6 +116,8 @@ psi_status build_spac_summary(psi_index *ix, cudaStream_t s);
 // SPaC build from sorted (key, position) pairs.
 psi_status spac_from_sorted(psi_index *ix, const uint64_t *skeys, const uint32_t *svals, const int32_t *pts,
                             const uint32_t *ids, int64_t n, cudaStream_t s);
+psi_status alloc_pleaves(PLeaves &a, int D, int64_t cap, cudaStream_t s);
+void free_pleaves(PLeaves &a, cudaStream_t s);
 psi_status porth_build(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t n, cudaStream_t s);
 psi_status porth_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, cudaStream_t s);
 psi_status porth_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, int64_t *d_deleted,
@@ -127,9 +144,6 @@ struct KnnSeed {
   const int64_t *node_off = nullptr;
   int phi = 0;
   const uint64_t *pkey = nullptr;
-  // P-Orth: the pool is key-sorted and contiguous, slots [0, n_slots); the seed
-  // is a slot range around the query's key
-  int64_t n_slots = 0;
   // scratch of nq entries (required with qkey): the seed leaf node (or slot)
   // of each query in curve order, written by the k-NN call before its search
   uint32_t *pos = nullptr;

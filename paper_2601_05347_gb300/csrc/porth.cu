@@ -3,8 +3,7 @@
 // The paper notes (Sec 3.1) that its sieve-based construction is equivalent
 // to an integer sort on Morton codes, lambda*D most significant bits per
 // round.  Here the points are sorted once on their full Morton keys (the
-// library's onesweep sort) and kept contiguously in key order; the tree is a
-// function of that order:
+// library's onesweep sort); the tree is a function of that order:
 //
 //   Leaf cells.  The cell of depth l containing key k_i holds more than phi
 //   points iff some phi+1 consecutive sorted keys around i share their top l
@@ -22,17 +21,61 @@
 //   children of a node (the next depth's nodes whose first leaf lies inside
 //   its cell) are contiguous.  Boxes are unions of the children, bottom up.
 //
-// Updates (Algorithm 2) rely on history independence (Sec 5.1.3 "Impact of
-// Updates to Queries"): the tree after a batch is the tree of the new point
-// set.  An insert merges the sorted batch into the sorted points; a delete
-// removes matching (point, id) pairs; both then re-derive leaves and nodes.
+// Storage: the leaf list (PLeaves) is kept in key order; each leaf owns a
+// slot range of the pool holding its points sorted by (key, id).  The node
+// arrays are derived from the leaf list (O(leaves), not O(points)).
+//
+// Updates (Algorithm 2: sieve the batch to the leaves it reaches and rebuild
+// only those).  A leaf's depth depends only on the phi+1 keys around each of
+// its points, so a batch changes only the leaves within phi+1 points of an
+// inserted or deleted point.  Each batch point is routed to the leaf whose
+// key range holds it; the leaves within phi+1 points of a routed leaf are
+// marked dirty; each maximal run of dirty leaves (a segment) is rebuilt from
+// its own points merged with (or stripped of) the batch points, with phi+1
+// keys of the clean neighbours on each side as context for the depth windows,
+// into fresh slots; the other leaves keep their records and slots.  The
+// result equals a fresh build of the new point set (history independence,
+// Sec 5.1.3), which the parity tests check node by node.
 #include "index.cuh"
 
 namespace psi {
+
+psi_status alloc_pleaves(PLeaves &a, int D, int64_t cap, cudaStream_t s) {
+  a.cap = cap;
+  const size_t c = (size_t)std::max<int64_t>(cap, 1);
+  psi_status st;
+  if ((st = DevMem::alloc((void **)&a.ref, sizeof(uint32_t) * c, s)) ||
+      (st = DevMem::alloc((void **)&a.cnt, sizeof(int32_t) * c, s)) ||
+      (st = DevMem::alloc((void **)&a.depth, sizeof(int32_t) * c, s)) ||
+      (st = DevMem::alloc((void **)&a.key, sizeof(uint64_t) * c, s)))
+    return st;
+  for (int d = 0; d < D; ++d)
+    if ((st = DevMem::alloc((void **)&a.lo[d], sizeof(int32_t) * c, s)) ||
+        (st = DevMem::alloc((void **)&a.hi[d], sizeof(int32_t) * c, s)))
+      return st;
+  return PSI_OK;
+}
+
+void free_pleaves(PLeaves &a, cudaStream_t s) {
+  DevMem::free(a.ref, s);
+  DevMem::free(a.cnt, s);
+  DevMem::free(a.depth, s);
+  DevMem::free(a.key, s);
+  for (int d = 0; d < 3; ++d) {
+    DevMem::free(a.lo[d], s);
+    DevMem::free(a.hi[d], s);
+  }
+  a = PLeaves();
+}
+
 namespace {
 
 int grid_for(int64_t n, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 32));
+}
+
+int warp_grid(int64_t warps) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps, 8), (int64_t)num_sms() * 32));
 }
 
 __device__ __forceinline__ int common_digits(uint64_t a, uint64_t b, int K, int D, int bits) {
@@ -88,7 +131,8 @@ __global__ void k_porth_gather(const uint64_t *skeys, const uint32_t *svals, con
 
 constexpr int LT = 256;  // positions per block in the leaf-depth kernel (8 blocks per SM overlap their loads)
 
-// Leaf depth of every point and leaf-start flags.
+// Leaf depth of every position of a key array (positions outside [0, n)
+// contribute no window).
 __global__ __launch_bounds__(LT) void k_leaf_depth(const uint64_t *keys, int64_t n, int phi, int K, int D, int bits,
                                                    int32_t *ldepth) {
   __shared__ uint64_t sk[LT + 2 * 64 + 1];
@@ -138,31 +182,102 @@ __global__ __launch_bounds__(LT) void k_leaf_depth(const uint64_t *keys, int64_t
   }
 }
 
-__global__ void k_leaf_starts(const uint64_t *keys, const int32_t *ldepth, int64_t n, int D, int bits,
-                              int32_t *is_start) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int s = 1;
-    if (i > 0) {
-      const int d = ldepth[i];
-      s = d != ldepth[i - 1] || cell_of(keys[i], d, D, bits) != cell_of(keys[i - 1], d, D, bits);
+// ---- leaves from a key array -------------------------------------------------
+// A work array lists keys in sorted order: the points of the leaves being
+// (re)built (mask 1, each with its pool slot; a leaf's points occupy
+// consecutive slots) and, between runs of them, context keys of unchanged
+// neighbours (mask 0) that only feed the depth windows.  A null mask means
+// every position is a point and its slot is slot0 + position.
+
+struct WorkArray {
+  const uint64_t *key;
+  const int32_t *mask;  // or null
+  const uint32_t *slot;  // or null (slot0 + position)
+  uint32_t slot0;
+  int64_t n;
+};
+
+__device__ __forceinline__ bool work_point(const WorkArray &w, int64_t i) { return !w.mask || w.mask[i]; }
+__device__ __forceinline__ uint32_t work_slot(const WorkArray &w, int64_t i) {
+  return w.slot ? w.slot[i] : w.slot0 + (uint32_t)i;
+}
+
+// start[i]: point i begins a leaf (a run's first point, or its (depth, cell)
+// differs from the previous point's).
+__global__ void k_work_starts(WorkArray w, const int32_t *ldepth, int D, int bits, int32_t *start) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += (int64_t)gridDim.x * blockDim.x) {
+    int s = 0;
+    if (work_point(w, i)) {
+      s = 1;
+      if (i > 0 && work_point(w, i - 1)) {
+        const int d = ldepth[i];
+        s = d != ldepth[i - 1] || cell_of(w.key[i], d, D, bits) != cell_of(w.key[i - 1], d, D, bits);
+      }
     }
-    is_start[i] = s;
+    start[i] = s;
   }
 }
 
-// Leaf list: begin, depth, cell start key.
-__global__ void k_leaf_list(const uint64_t *keys, const int32_t *ldepth, const int32_t *is_start, const int64_t *rank,
-                            int64_t n, int D, int bits, int64_t *lb, int32_t *ld, uint64_t *lkey) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (!is_start[i]) continue;
-    const int64_t r = rank[i];
-    const int d = ldepth[i];
-    const int sh = D * (bits - d);
-    lb[r] = i;
-    ld[r] = d;
-    lkey[r] = sh >= 64 ? 0 : ((keys[i] >> sh) << sh);
+// Leaf records: leaf rank[i] for every start i (first slot, depth, cell key),
+// and its count at its last point.
+__global__ void k_work_leaves(WorkArray w, const int32_t *ldepth, const int32_t *start, const int64_t *rank, int D,
+                              int bits, PLeaves out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!work_point(w, i)) continue;
+    const int64_t r = rank[i] + start[i] - 1;  // the leaf of point i
+    if (start[i]) {
+      const int d = ldepth[i];
+      const int sh = D * (bits - d);
+      out.ref[r] = work_slot(w, i);
+      out.depth[r] = d;
+      out.key[r] = sh >= 64 ? 0 : ((w.key[i] >> sh) << sh);
+    }
+    const bool last = i + 1 == w.n || !work_point(w, i + 1) || start[i + 1];
+    if (last) {
+      // the leaf's first slot, read back through its first point
+      int64_t f = i;
+      while (!start[f]) --f;  // at most the leaf's size back (phi, or a pile of duplicates)
+      out.cnt[r] = (int32_t)(work_slot(w, i) - work_slot(w, f) + 1);
+    }
   }
 }
+
+// Tight box of leaves [0, L) of a leaf list: a warp per leaf.
+template <int D>
+__global__ void k_pleaf_boxes(PLeaves pl, Pool pool, int64_t L) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < L; i += warps) {
+    const uint32_t s0 = pl.ref[i];
+    const int c = pl.cnt[i];
+    int32_t lo[D], hi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      lo[d] = INT32_MAX;
+      hi[d] = INT32_MIN;
+    }
+    for (int s = lane; s < c; s += 32)
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int32_t v = pool.px[d][s0 + s];
+        lo[d] = min(lo[d], v);
+        hi[d] = max(hi[d], v);
+      }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      lo[d] = __reduce_min_sync(0xFFFFFFFFu, lo[d]);
+      hi[d] = __reduce_max_sync(0xFFFFFFFFu, hi[d]);
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        pl.lo[d][i] = lo[d];
+        pl.hi[d][i] = hi[d];
+      }
+  }
+}
+
+// ---- nodes from the leaf list ---------------------------------------------
 
 // Nodes headed by each leaf: depths c_i + 1 .. d_i.
 __global__ void k_heads(const int32_t *ld, const uint64_t *lkey, int64_t L, int K, int D, int bits, int32_t *c,
@@ -199,29 +314,33 @@ __global__ void k_emit_nodes(const int32_t *ld, const int32_t *c, const int64_t 
 struct LinkArgs {
   const uint64_t *ndepth;  // node depth, depth-major order
   const uint32_t *nleaf;   // node's first leaf, ascending within a depth
-  const int64_t *doff;   // [bits + 2] depth offsets
-  const int64_t *lb;     // leaf begin slot
-  const int32_t *ld;
-  const uint64_t *lkey;
-  int64_t L, N, n;
+  const int64_t *doff;     // [bits + 2] depth offsets
+  const int64_t *E;        // exclusive prefix sums of the leaf counts (L + 1)
+  PLeaves pl;
+  int64_t L, N;
   int D, bits;
   NodeArrays nodes;
   int32_t *leaf_node;
 };
 
+template <int D>
 __global__ void k_link(LinkArgs a) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.N; x += (int64_t)gridDim.x * blockDim.x) {
     const int l = (int)a.ndepth[x];
     const int64_t i = (int64_t)a.nleaf[x];
     const int sh = a.D * (a.bits - l);
-    const uint64_t prefix = sh >= 64 ? 0 : (a.lkey[i] >> sh);
+    const uint64_t prefix = sh >= 64 ? 0 : (a.pl.key[i] >> sh);
     a.nodes.depth[x] = l;
     a.nodes.prefix[x] = prefix;
-    if (l == a.ld[i]) {
-      const int64_t e = i + 1 < a.L ? a.lb[i + 1] : a.n;
-      a.nodes.ref[x] = (uint32_t)a.lb[i];
+    if (l == a.pl.depth[i]) {
+      a.nodes.ref[x] = a.pl.ref[i];
       a.nodes.kids[x] = 0;
-      a.nodes.cnt[x] = (int32_t)(e - a.lb[i]);
+      a.nodes.cnt[x] = a.pl.cnt[i];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        a.nodes.lo[d][x] = a.pl.lo[d][i];
+        a.nodes.hi[d][x] = a.pl.hi[d][i];
+      }
       a.leaf_node[i] = (int32_t)x;
       continue;
     }
@@ -230,7 +349,7 @@ __global__ void k_link(LinkArgs a) {
     int64_t lo = i + 1, hi = a.L;
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      if (a.lkey[mid] < lim)
+      if (a.pl.key[mid] < lim)
         lo = mid + 1;
       else
         hi = mid;
@@ -238,40 +357,34 @@ __global__ void k_link(LinkArgs a) {
     const int64_t e = lo;
     // children: depth l+1 nodes whose first leaf lies in [i, e)
     const int64_t s0 = a.doff[l + 1], s1 = a.doff[l + 2];
-    int64_t c0 = s0, c1 = s1;
-    {
-      int64_t p = s0, q = s1;
-      while (p < q) {
-        const int64_t mid = (p + q) >> 1;
-        if ((int64_t)a.nleaf[mid] < i)
-          p = mid + 1;
-        else
-          q = mid;
-      }
-      c0 = p;
-      q = s1;
-      while (p < q) {
-        const int64_t mid = (p + q) >> 1;
-        if ((int64_t)a.nleaf[mid] < e)
-          p = mid + 1;
-        else
-          q = mid;
-      }
-      c1 = p;
+    int64_t p = s0, q = s1;
+    while (p < q) {
+      const int64_t mid = (p + q) >> 1;
+      if ((int64_t)a.nleaf[mid] < i)
+        p = mid + 1;
+      else
+        q = mid;
+    }
+    const int64_t c0 = p;
+    q = s1;
+    while (p < q) {
+      const int64_t mid = (p + q) >> 1;
+      if ((int64_t)a.nleaf[mid] < e)
+        p = mid + 1;
+      else
+        q = mid;
     }
     a.nodes.ref[x] = (uint32_t)c0;
-    a.nodes.kids[x] = (int32_t)(c1 - c0);
-    const int64_t pe = e < a.L ? a.lb[e] : a.n;
-    a.nodes.cnt[x] = (int32_t)(pe - a.lb[i]);
+    a.nodes.kids[x] = (int32_t)(p - c0);
+    a.nodes.cnt[x] = (int32_t)(a.E[e] - a.E[i]);
   }
 }
 
-// Boxes of the nodes of one depth: leaves from their points, internal nodes
-// from their children.
+// Boxes of the internal nodes of one depth from their children (leaf boxes
+// come with the leaf records): an 8-lane group per node (at most 2^D <= 8
+// children), four nodes per warp.
 template <int D>
-__global__ void k_boxes(NodeArrays nodes, Pool pool, int64_t off, int64_t cnt) {
-  // an 8-lane group per node (at most 2^D <= 8 children; leaf points 8 at a
-  // time), four nodes per warp
+__global__ void k_boxes(NodeArrays nodes, int64_t off, int64_t cnt) {
   const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
   const unsigned gmask = 0xFFu << (g * 8);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -279,30 +392,19 @@ __global__ void k_boxes(NodeArrays nodes, Pool pool, int64_t off, int64_t cnt) {
        x0 += warps * 4) {
     const int64_t x = x0 + g;
     const bool valid = x < off + cnt;
+    const int nk = valid ? nodes.kids[x] : 0;
     int32_t lo[D], hi[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       lo[d] = INT32_MAX;
       hi[d] = INT32_MIN;
     }
-    if (valid) {
-      const int nk = nodes.kids[x];
+    if (gl < nk) {
       const uint32_t r = nodes.ref[x];
-      if (nk == 0) {
-        const int c = nodes.cnt[x];
-        for (int s = gl; s < c; s += 8)
 #pragma unroll
-          for (int d = 0; d < D; ++d) {
-            const int32_t v = pool.px[d][r + s];
-            lo[d] = min(lo[d], v);
-            hi[d] = max(hi[d], v);
-          }
-      } else if (gl < nk) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          lo[d] = nodes.lo[d][r + gl];
-          hi[d] = nodes.hi[d][r + gl];
-        }
+      for (int d = 0; d < D; ++d) {
+        lo[d] = nodes.lo[d][r + gl];
+        hi[d] = nodes.hi[d][r + gl];
       }
     }
 #pragma unroll
@@ -310,7 +412,7 @@ __global__ void k_boxes(NodeArrays nodes, Pool pool, int64_t off, int64_t cnt) {
       lo[d] = __reduce_min_sync(gmask, lo[d]);
       hi[d] = __reduce_max_sync(gmask, hi[d]);
     }
-    if (valid && gl == 0)
+    if (nk > 0 && gl == 0)
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         nodes.lo[d][x] = lo[d];
@@ -321,138 +423,395 @@ __global__ void k_boxes(NodeArrays nodes, Pool pool, int64_t off, int64_t cnt) {
 
 // ---- updates ----------------------------------------------------------------
 
-// Rank of each batch item among the pool's (key, id) order; count of batch
-// items before each pool position.
-__global__ void k_merge_ranks(const uint64_t *pkey, const uint32_t *pid, int64_t n, const uint64_t *bkeys,
-                              const uint32_t *bvals, const uint32_t *ids, int64_t m, int64_t *brank,
-                              int32_t *delta) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = bkeys[j];
-    const uint32_t id = ids[bvals[j]];
-    int64_t lo = 0, hi = n;
+// The sorted batch as records: the id and the point of each sorted entry.
+template <int D>
+__global__ void k_prec(const uint32_t *bvals, const int32_t *pts, const uint32_t *ids, int64_t m, uint32_t *rid,
+                       int32_t *rpt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = bvals[i];
+    rid[i] = ids[v];
+#pragma unroll
+    for (int d = 0; d < D; ++d) rpt[i * D + d] = pts[(int64_t)v * D + d];
+  }
+}
+
+// Leaf of each sorted batch key: the last leaf whose cell starts at or below
+// it (leaf 0 when none does).  Cells are disjoint and in key order, so a
+// stored point equal to the key can only be in that leaf, and a new point
+// goes between that leaf's points and the next leaf's.
+__global__ void k_route(const uint64_t *bkeys, int64_t m, const uint64_t *lkey, int64_t L, int32_t *bleaf) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = bkeys[i];
+    int64_t lo = 0, hi = L;  // first leaf whose cell starts above k
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      if (kid_less(pkey[mid], pid[mid], k, id))
+      if (lkey[mid] <= k)
         lo = mid + 1;
       else
         hi = mid;
     }
-    brank[j] = lo;
-    atomicAdd(&delta[lo], 1);
+    bleaf[i] = (int32_t)max((int64_t)0, lo - 1);
   }
 }
 
-template <int D>
-__global__ void k_merge_scatter(Pool oldp, int64_t n, const int64_t *shift, const uint64_t *bkeys,
-                                const uint32_t *bvals, const int32_t *pts, const uint32_t *ids, int64_t m,
-                                const int64_t *brank, Pool np) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int64_t o = i + shift[i];
-#pragma unroll
-    for (int d = 0; d < D; ++d) np.px[d][o] = oldp.px[d][i];
-    np.pid[o] = oldp.pid[i];
-    np.pkey[o] = oldp.pkey[i];
-  }
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-    const int64_t o = brank[j] + j;
-    const uint32_t v = bvals[j];
-#pragma unroll
-    for (int d = 0; d < D; ++d) np.px[d][o] = pts[(int64_t)v * D + d];
-    np.pid[o] = ids[v];
-    np.pkey[o] = bkeys[j];
+// Slice [sbeg[x], send[x]) of the sorted batch routed to leaf x.
+__global__ void k_pslices(const int32_t *bleaf, int64_t m, int32_t *sbeg, int32_t *send) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t j = bleaf[i];
+    if (i == 0 || bleaf[i - 1] != j) sbeg[j] = (int32_t)i;
+    if (i == m - 1 || bleaf[i + 1] != j) send[j] = (int32_t)(i + 1);
   }
 }
 
+// The leaf holding old position p: the last leaf y with E[y] <= p (leaves
+// hold at least one point, so E is strictly increasing).
+__device__ __forceinline__ int64_t leaf_at(const int64_t *E, int64_t L, int64_t p) {
+  int64_t lo = 0, hi = L;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (E[mid] <= p)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// A leaf with a slice makes dirty every leaf holding a point within phi + 1
+// positions of its own points (the depth windows that can change).
+__global__ void k_dirty_marks(const int32_t *sbeg, const int32_t *send, const int64_t *E, int64_t L, int64_t n,
+                              int phi, int32_t *diff) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += (int64_t)gridDim.x * blockDim.x) {
+    if (send[x] <= sbeg[x]) continue;
+    const int64_t p0 = max((int64_t)0, E[x] - (phi + 1));
+    const int64_t p1 = min(n - 1, E[x + 1] + phi);
+    atomicAdd(&diff[leaf_at(E, L, p0)], 1);
+    atomicAdd(&diff[leaf_at(E, L, p1) + 1], -1);
+  }
+}
+
+// dirty[x] from the exclusive scan ex of diff (its inclusive sum is ex[x + 1]);
+// segment starts and ends.
+__global__ void k_dirty_flags(const int64_t *ex, int64_t L, int32_t *dirty, int32_t *sstart) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += (int64_t)gridDim.x * blockDim.x) {
+    const bool dx = ex[x + 1] > 0;
+    dirty[x] = dx;
+    sstart[x] = dx && (x == 0 || ex[x] <= 0);
+  }
+}
+
+// Delete: every stored point of a leaf with a slice whose (key, id) occurs in
+// the slice with the same coordinates is removed (keep[E[x] + s] = 0); rem[x]
+// counts them.  A warp per leaf with a slice.
 template <int D>
-__global__ void k_mark_deleted(const uint64_t *pkey, const uint32_t *pid, Pool pool, int64_t n, const uint64_t *bkeys,
-                               const uint32_t *bvals, const int32_t *pts, const uint32_t *ids, int64_t m,
-                               int32_t *keep, unsigned long long *deleted) {
+__global__ void k_pdel_marks(PLeaves pl, Pool pool, const int64_t *E, const int32_t *sbeg, const int32_t *send,
+                             int64_t L, const uint64_t *bkeys, const uint32_t *rid, const int32_t *rpt,
+                             int32_t *keep, int32_t *rem, unsigned long long *deleted) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   uint32_t removed = 0;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = bkeys[j];
-    const uint32_t v = bvals[j];
-    const uint32_t id = ids[v];
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (kid_less(pkey[mid], pid[mid], k, id))
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    if (lo < n && pkey[lo] == k && pid[lo] == id) {
-      bool same = true;
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < L; x += warps) {
+    const int32_t b = sbeg[x], e = send[x];
+    if (e <= b) continue;
+    const uint32_t s0 = pl.ref[x];
+    const int c = pl.cnt[x];
+    int r = 0;
+    for (int s = lane; s < c; s += 32) {
+      const uint64_t k = pool.pkey[s0 + s];
+      const uint32_t id = pool.pid[s0 + s];
+      int32_t lo = b, hi = e;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (kid_less(bkeys[mid], rid[mid], k, id))
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      bool hit = lo < e && bkeys[lo] == k && rid[lo] == id;
+      if (hit) {
 #pragma unroll
-      for (int d = 0; d < D; ++d) same &= pool.px[d][lo] == pts[(int64_t)v * D + d];
-      if (same && atomicExch(&keep[lo], 0) == 1) ++removed;
+        for (int d = 0; d < D; ++d) hit &= rpt[(int64_t)lo * D + d] == pool.px[d][s0 + s];
+      }
+      keep[E[x] + s] = !hit;
+      r += hit;
+    }
+    r = __reduce_add_sync(0xFFFFFFFFu, r);
+    if (lane == 0) {
+      rem[x] = r;
+      removed += (uint32_t)r;
     }
   }
   block_count_add(deleted, removed);
 }
 
-template <int D>
-__global__ void k_compact_points(Pool oldp, int64_t n, const int32_t *keep, const int64_t *pos, Pool np) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (!keep[i]) continue;
-    const int64_t o = pos[i];
-#pragma unroll
-    for (int d = 0; d < D; ++d) np.px[d][o] = oldp.px[d][i];
-    np.pid[o] = oldp.pid[i];
-    np.pkey[o] = oldp.pkey[i];
+// New point count of every dirty leaf (0 for clean leaves).
+__global__ void k_newcount(const int32_t *dirty, const int32_t *cnt, const int32_t *sbeg, const int32_t *send,
+                           const int32_t *rem, int64_t L, bool insert, int32_t *nc) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += (int64_t)gridDim.x * blockDim.x) {
+    int c = 0;
+    if (dirty[x]) c = cnt[x] + (insert ? max(0, send[x] - sbeg[x]) : -(send[x] > sbeg[x] ? rem[x] : 0));
+    nc[x] = c;
   }
 }
 
-__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+// Segment g: its first and last leaf, and its context sizes (old points
+// before and after it, at most phi + 1 each).
+__global__ void k_seg_bounds(const int32_t *dirty, const int32_t *sstart, const int64_t *gx, int64_t L,
+                             int32_t *xs, int32_t *xe) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += (int64_t)gridDim.x * blockDim.x) {
+    if (sstart[x]) xs[gx[x]] = (int32_t)x;
+    if (dirty[x] && (x + 1 == L || !dirty[x + 1])) xe[gx[x] + sstart[x] - 1] = (int32_t)x;
+  }
+}
+
+__global__ void k_seg_ctx(const int32_t *xs, const int32_t *xe, const int64_t *E, int64_t G, int64_t n, int phi,
+                          int32_t *ctxl, int32_t *ctxr, int32_t *ctx) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = E[xs[g]], b = E[xe[g] + 1];
+    const int cl = (int)min((int64_t)(phi + 1), a), cr = (int)min((int64_t)(phi + 1), n - b);
+    ctxl[g] = cl;
+    ctxr[g] = cr;
+    ctx[g] = cl + cr;
+  }
+}
+
+struct SegArgs {
+  PLeaves pl;
+  Pool pool;
+  const int64_t *E;     // old leaves' prefix counts (L + 1)
+  const int32_t *dirty, *sstart, *xs, *xe, *ctxl, *ctxr;
+  const int64_t *gx;    // exclusive scan of sstart
+  const int64_t *woff;  // exclusive scan of the new counts (L + 1)
+  const int64_t *cxoff; // exclusive scan of the segments' context sizes
+  const int32_t *sbeg, *send, *keep;
+  const uint64_t *bkeys;
+  const uint32_t *rid;
+  const int32_t *rpt;
+  int64_t L, G, n;
+  uint32_t fresh;  // first fresh slot: dirty leaf x's new points go to fresh + woff[x] ...
+  bool insert;
+  uint64_t *wkey;  // work array
+  int32_t *wmask;
+  uint32_t *wslot;
+};
+
+// Work position of segment g's first point.
+__device__ __forceinline__ int64_t seg_wstart(const SegArgs &a, int64_t g) {
+  return a.woff[a.xs[g]] + a.cxoff[g] + a.ctxl[g];
+}
+
+// Context keys of every segment (a warp per segment): the old points just
+// before and just after it.
+__global__ void k_seg_context(SegArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < a.G; g += warps) {
+    const int64_t w0 = seg_wstart(a, g);
+    const int cl = a.ctxl[g], cr = a.ctxr[g];
+    const int64_t pa = a.E[a.xs[g]], pb = a.E[a.xe[g] + 1];
+    const int64_t seglen = a.woff[a.xe[g] + 1] - a.woff[a.xs[g]];
+    for (int t = lane; t < cl + cr; t += 32) {
+      const int64_t p = t < cl ? pa - cl + t : pb + (t - cl);
+      const int64_t w = t < cl ? w0 - cl + t : w0 + seglen + (t - cl);
+      const int64_t y = leaf_at(a.E, a.L, p);
+      a.wkey[w] = a.pool.pkey[a.pl.ref[y] + (uint32_t)(p - a.E[y])];
+      a.wmask[w] = 0;
+      a.wslot[w] = 0;
+    }
+  }
+}
+
+// The new points of every dirty leaf, in (key, id) order, into fresh slots and
+// the work array: insert merges the leaf's points with its slice; delete
+// keeps the unmarked ones.  A warp per dirty leaf.
+template <int D>
+__global__ void k_seg_points(SegArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < a.L; x += warps) {
+    if (!a.dirty[x]) continue;
+    const int64_t g = a.gx[x] + a.sstart[x] - 1;
+    const int64_t w0 = seg_wstart(a, g) + (a.woff[x] - a.woff[a.xs[g]]);
+    const uint32_t f0 = a.fresh + (uint32_t)a.woff[x];
+    const uint32_t s0 = a.pl.ref[x];
+    const int cnt = a.pl.cnt[x];
+    const int32_t b = a.sbeg[x], len = max(0, a.send[x] - b);
+    auto put = [&](int64_t t, uint64_t k, uint32_t id, const int32_t *c) {
+      const uint32_t dst = f0 + (uint32_t)t;
+#pragma unroll
+      for (int d = 0; d < D; ++d) a.pool.px[d][dst] = c[d];
+      a.pool.pid[dst] = id;
+      a.pool.pkey[dst] = k;
+      a.wkey[w0 + t] = k;
+      a.wmask[w0 + t] = 1;
+      a.wslot[w0 + t] = dst;
+    };
+    if (a.insert) {
+      const int64_t c = (int64_t)cnt + len;
+      for (int64_t p = lane; p < c; p += 32) {
+        // merge path: how many of the first p merged elements come from the leaf
+        int64_t l = max((int64_t)0, p - len), h = min(p, (int64_t)cnt);
+        while (l < h) {
+          const int64_t mid = (l + h) >> 1;
+          const int64_t bi = b + (p - mid - 1);
+          const uint64_t lk = a.pool.pkey[s0 + mid], sk = a.bkeys[bi];
+          if (lk < sk || (lk == sk && a.pool.pid[s0 + mid] <= a.rid[bi]))
+            l = mid + 1;
+          else
+            h = mid;
+        }
+        const int64_t li = l, si = p - l;
+        bool from_leaf = li < cnt;
+        if (from_leaf && si < len) {
+          const uint64_t lk = a.pool.pkey[s0 + li], sk = a.bkeys[b + si];
+          from_leaf = lk < sk || (lk == sk && a.pool.pid[s0 + li] <= a.rid[b + si]);
+        }
+        int32_t cc[D];
+        if (from_leaf) {
+          const uint32_t src = s0 + (uint32_t)li;
+#pragma unroll
+          for (int d = 0; d < D; ++d) cc[d] = a.pool.px[d][src];
+          put(p, a.pool.pkey[src], a.pool.pid[src], cc);
+        } else {
+          const int64_t bi = b + si;
+#pragma unroll
+          for (int d = 0; d < D; ++d) cc[d] = a.rpt[bi * D + d];
+          put(p, a.bkeys[bi], a.rid[bi], cc);
+        }
+      }
+    } else {
+      int64_t out = 0;
+      for (int s0r = 0; s0r < cnt; s0r += 32) {
+        const int s = s0r + lane;
+        const bool k = s < cnt && (len == 0 || a.keep[a.E[x] + s]);
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, k);
+        if (k) {
+          const uint32_t src = s0 + (uint32_t)s;
+          int32_t cc[D];
+#pragma unroll
+          for (int d = 0; d < D; ++d) cc[d] = a.pool.px[d][src];
+          put(out + __popc(m & lanemask_lt()), a.pool.pkey[src], a.pool.pid[src], cc);
+        }
+        out += __popc(m);
+      }
+    }
+  }
+}
+
+// First new leaf of each segment: the leaf rank at its first work position
+// (its context and points follow in work order); fl[G] = the new leaf count.
+__global__ void k_seg_first_leaf(SegArgs a, const int64_t *rank, int64_t W, int64_t NL, int64_t *fl) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= a.G; g += (int64_t)gridDim.x * blockDim.x) {
+    if (g == a.G) {
+      fl[g] = NL;
+    } else {
+      const int64_t w = seg_wstart(a, g);
+      fl[g] = w < W ? rank[w] : NL;
+    }
+  }
+}
+
+// Output leaves of each old leaf: a clean leaf is kept, a segment's new
+// leaves are counted at its first leaf.
+__global__ void k_pl_outl(const int32_t *dirty, const int32_t *sstart, const int64_t *gx, const int64_t *fl,
+                          int64_t L, int32_t *outl) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += (int64_t)gridDim.x * blockDim.x) {
+    if (!dirty[x])
+      outl[x] = 1;
+    else if (sstart[x])
+      outl[x] = (int32_t)(fl[gx[x] + 1] - fl[gx[x]]);
+    else
+      outl[x] = 0;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void pl_copy(const PLeaves &src, int64_t i, const PLeaves &dst, int64_t o) {
+  dst.ref[o] = src.ref[i];
+  dst.cnt[o] = src.cnt[i];
+  dst.depth[o] = src.depth[i];
+  dst.key[o] = src.key[i];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    dst.lo[d][o] = src.lo[d][i];
+    dst.hi[d][o] = src.hi[d][i];
+  }
+}
+
+// The new leaf list: clean leaves at pos[x]; new leaf r of segment g at
+// pos[xs[g]] + (r - fl[g]).
+template <int D>
+__global__ void k_pl_assemble(PLeaves old, const int32_t *dirty, const int64_t *pos, int64_t L, PLeaves fresh,
+                              int64_t NL, const int64_t *fl, const int32_t *xs, int64_t G, PLeaves out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += stride)
+    if (!dirty[x]) pl_copy<D>(old, x, out, pos[x]);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < NL; r += stride) {
+    int64_t lo = 0, hi = G;  // last segment g with fl[g] <= r
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (fl[mid] <= r)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    pl_copy<D>(fresh, r, out, pos[xs[lo]] + (r - fl[lo]));
+  }
+}
+
+// Compaction of the pool: every leaf's points to consecutive slots in leaf
+// order (a warp per leaf); the leaf records take their new first slots.
+template <int D>
+__global__ void k_pl_compact(PLeaves pl, const int64_t *E, int64_t L, Pool from, Pool to) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < L; x += warps) {
+    const uint32_t s0 = pl.ref[x];
+    const int c = pl.cnt[x];
+    const int64_t o = E[x];
+    for (int s = lane; s < c; s += 32) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) to.px[d][o + s] = from.px[d][s0 + s];
+      to.pid[o + s] = from.pid[s0 + s];
+      to.pkey[o + s] = from.pkey[s0 + s];
+    }
+    __syncwarp();
+    if (lane == 0) pl.ref[x] = (uint32_t)o;
+  }
 }
 
 __global__ void k_i64_from_u64(const unsigned long long *a, int64_t *b) { *b = (int64_t)*a; }
 
 }  // namespace
 
-// Leaves and nodes of the P-Orth tree over the ix->n sorted points in the pool.
-psi_status porth_derive(psi_index *ix, cudaStream_t s) {
-  const int64_t n = ix->n;
+// Node arrays of the P-Orth tree over the leaf list ix->pl (ix->L leaves).
+static psi_status porth_nodes(psi_index *ix, cudaStream_t s) {
   const int D = ix->D, bits = ix->cfg.coord_bits, K = ix->key_bits;
+  const int64_t L = ix->L;
   free_nodes(ix->nodes, s);
   DevMem::free(ix->leaf_node, s);
   ix->leaf_node = nullptr;
-  ix->L = 0;
   ix->nnodes = 0;
   ix->root = -1;
-  if (n == 0) return PSI_OK;
+  if (L == 0) return PSI_OK;
   psi_status st;
-  Buf<int32_t> ldepth, is_start;
-  Buf<int64_t> rank, tot;
-  if ((st = ldepth.alloc(n, s)) || (st = is_start.alloc(n, s)) || (st = rank.alloc(n, s)) || (st = tot.alloc(2, s)))
+  Buf<int64_t> nn, E, tot;
+  Buf<int32_t> c, hist;
+  if ((st = nn.alloc(L, s)) || (st = E.alloc(L + 1, s)) || (st = tot.alloc(2, s)) || (st = c.alloc(L, s)) ||
+      (st = hist.alloc(64, s)))
     return st;
-  PSI_LAUNCH(k_leaf_depth, (unsigned)ceil_div(n, LT), LT, 0, s, ix->pool.pkey, n, ix->phi, K, D, bits, ldepth.p);
-  PSI_LAUNCH(k_leaf_starts, grid_for(n), 256, 0, s, ix->pool.pkey, ldepth.p, n, D, bits, is_start.p);
-  if ((st = scan_i32_to_i64(is_start.p, rank.p, n, tot.p, s))) return st;
-  int64_t L = 0;
-  PSI_CK(cudaMemcpyAsync(&L, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  PSI_CK(cudaStreamSynchronize(s));
-
-  Buf<int64_t> lb, nn;
-  Buf<int32_t> ld, c, hist;
-  Buf<uint64_t> lkey;
-  if ((st = lb.alloc(L, s)) || (st = nn.alloc(L, s)) || (st = ld.alloc(L, s)) || (st = c.alloc(L, s)) ||
-      (st = lkey.alloc(L, s)) || (st = hist.alloc(64, s)))
-    return st;
-  PSI_LAUNCH(k_leaf_list, grid_for(n), 256, 0, s, ix->pool.pkey, ldepth.p, is_start.p, rank.p, n, D, bits, lb.p, ld.p,
-             lkey.p);
-  PSI_LAUNCH(k_heads, grid_for(L), 256, 0, s, ld.p, lkey.p, L, K, D, bits, c.p, nn.p);
-  if ((st = scan_i64(nn.p, nn.p, L, tot.p + 1, s))) return st;
+  if ((st = scan_i32_to_i64(ix->pl.cnt, E.p, L, E.p + L, s))) return st;
+  PSI_LAUNCH(k_heads, grid_for(L), 256, 0, s, ix->pl.depth, ix->pl.key, L, K, D, bits, c.p, nn.p);
+  if ((st = scan_i64(nn.p, nn.p, L, tot.p, s))) return st;
   int64_t N = 0;
-  PSI_CK(cudaMemcpyAsync(&N, tot.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaMemcpyAsync(&N, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   PSI_CK(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * 64, s));
   PSI_CK(cudaStreamSynchronize(s));
 
   Buf<uint64_t> nk0, nk1;
   Buf<uint32_t> nv0, nv1;
   if ((st = nk0.alloc(N, s)) || (st = nk1.alloc(N, s)) || (st = nv0.alloc(N, s)) || (st = nv1.alloc(N, s))) return st;
-  PSI_LAUNCH(k_emit_nodes, grid_for(L), 256, 0, s, ld.p, c.p, nn.p, L, nk0.p, nv0.p, hist.p);
+  PSI_LAUNCH(k_emit_nodes, grid_for(L), 256, 0, s, ix->pl.depth, c.p, nn.p, L, nk0.p, nv0.p, hist.p);
   int32_t h_hist[64];
   PSI_CK(cudaMemcpyAsync(h_hist, hist.p, sizeof(h_hist), cudaMemcpyDeviceToHost, s));
   SortResult r;
@@ -462,8 +821,7 @@ psi_status porth_derive(psi_index *ix, cudaStream_t s) {
   PSI_CK(cudaMemsetAsync(sst.p, 0, sizeof(int), s));
   // one stable digit pass on the depth (< 64); the input arrays double as the
   // second ping-pong buffer
-  if ((st = sort_pairs(none, nk0.p, nv0.p, N, 8, nullptr, nk1.p, nv1.p, nk0.p, nv0.p, sst.p, s, &r)))
-    return st;
+  if ((st = sort_pairs(none, nk0.p, nv0.p, N, 8, nullptr, nk1.p, nv1.p, nk0.p, nv0.p, sst.p, s, &r))) return st;
   PSI_CK(cudaStreamSynchronize(s));
   std::vector<int64_t> doff(bits + 3, 0);
   for (int l = 0; l <= bits; ++l) doff[l + 1] = doff[l] + h_hist[l];
@@ -474,33 +832,114 @@ psi_status porth_derive(psi_index *ix, cudaStream_t s) {
 
   if ((st = alloc_nodes(ix->nodes, D, N, true, s))) return st;
   if ((st = DevMem::alloc((void **)&ix->leaf_node, sizeof(int32_t) * L, s))) return st;
-  LinkArgs la{r.keys, r.vals, d_doff.p, lb.p, ld.p, lkey.p, L, N, n, D, bits, ix->nodes, ix->leaf_node};
-  PSI_LAUNCH(k_link, grid_for(N), 256, 0, s, la);
+  LinkArgs la{r.keys, r.vals, d_doff.p, E.p, ix->pl, L, N, D, bits, ix->nodes, ix->leaf_node};
+  if (D == 2)
+    PSI_LAUNCH_NAMED("k_link", k_link<2>, grid_for(N), 256, 0, s, la);
+  else
+    PSI_LAUNCH_NAMED("k_link", k_link<3>, grid_for(N), 256, 0, s, la);
   int maxd = 0;
   for (int l = 0; l <= bits; ++l)
     if (h_hist[l]) maxd = l;
-  for (int l = maxd; l >= 0; --l) {
+  for (int l = maxd - 1; l >= 0; --l) {  // leaves carry their boxes; internal nodes bottom up
     const int64_t cnt = doff[l + 1] - doff[l];
     if (!cnt) continue;
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cnt, 32), (int64_t)num_sms() * 32));
     if (D == 2)
-      PSI_LAUNCH_NAMED("k_boxes", k_boxes<2>, g, 256, 0, s, ix->nodes, ix->pool, doff[l], cnt);
+      PSI_LAUNCH_NAMED("k_boxes", k_boxes<2>, g, 256, 0, s, ix->nodes, doff[l], cnt);
     else
-      PSI_LAUNCH_NAMED("k_boxes", k_boxes<3>, g, 256, 0, s, ix->nodes, ix->pool, doff[l], cnt);
+      PSI_LAUNCH_NAMED("k_boxes", k_boxes<3>, g, 256, 0, s, ix->nodes, doff[l], cnt);
   }
-  ix->L = L;
   ix->nnodes = N;
   ix->root = 0;
   PSI_CK(cudaGetLastError());
   return PSI_OK;
 }
 
+// Leaves of a work array into a new leaf list `out` (allocated here) with
+// their boxes; *nl receives the leaf count.  rank_out (optional) keeps the
+// exclusive scan of the leaf starts.
+static psi_status work_leaves(psi_index *ix, const WorkArray &w, PLeaves &out, int64_t *nl, Buf<int64_t> *rank_out,
+                              cudaStream_t s) {
+  const int D = ix->D, bits = ix->cfg.coord_bits, K = ix->key_bits;
+  psi_status st;
+  Buf<int32_t> ldepth, start;
+  Buf<int64_t> rank_local, tot;
+  Buf<int64_t> &rank = rank_out ? *rank_out : rank_local;
+  if ((st = ldepth.alloc(w.n, s)) || (st = start.alloc(w.n, s)) || (st = rank.alloc(w.n, s)) ||
+      (st = tot.alloc(1, s)))
+    return st;
+  PSI_LAUNCH(k_leaf_depth, (unsigned)ceil_div(w.n, LT), LT, 0, s, w.key, w.n, ix->phi, K, D, bits, ldepth.p);
+  PSI_LAUNCH(k_work_starts, grid_for(w.n), 256, 0, s, w, ldepth.p, D, bits, start.p);
+  if ((st = scan_i32_to_i64(start.p, rank.p, w.n, tot.p, s))) return st;
+  int64_t L = 0;
+  PSI_CK(cudaMemcpyAsync(&L, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  if ((st = alloc_pleaves(out, D, L, s))) return st;
+  PSI_LAUNCH(k_work_leaves, grid_for(w.n), 256, 0, s, w, ldepth.p, start.p, rank.p, D, bits, out);
+  if (L > 0) {
+    if (D == 2)
+      PSI_LAUNCH_NAMED("k_pleaf_boxes", k_pleaf_boxes<2>, warp_grid(L), 256, 0, s, out, ix->pool, L);
+    else
+      PSI_LAUNCH_NAMED("k_pleaf_boxes", k_pleaf_boxes<3>, warp_grid(L), 256, 0, s, out, ix->pool, L);
+  }
+  *nl = L;
+  return PSI_OK;
+}
+
+// Grows the pool to at least `need` slots, keeping the used prefix.
+static psi_status porth_grow(psi_index *ix, int64_t need, cudaStream_t s) {
+  if (need <= ix->pool.cap_slots) return PSI_OK;
+  Pool np;
+  const int64_t cap = std::max(need + need / 4, ix->pool.cap_slots * 3 / 2);
+  psi_status st = alloc_pool(np, ix->D, cap, s);
+  if (st) {
+    free_pool(np, s);
+    return st;
+  }
+  const int64_t used = ix->pool_used;
+  if (used > 0) {
+    for (int d = 0; d < ix->D; ++d)
+      PSI_CK(cudaMemcpyAsync(np.px[d], ix->pool.px[d], sizeof(int32_t) * used, cudaMemcpyDeviceToDevice, s));
+    PSI_CK(cudaMemcpyAsync(np.pid, ix->pool.pid, sizeof(uint32_t) * used, cudaMemcpyDeviceToDevice, s));
+    PSI_CK(cudaMemcpyAsync(np.pkey, ix->pool.pkey, sizeof(uint64_t) * used, cudaMemcpyDeviceToDevice, s));
+  }
+  free_pool(ix->pool, s);
+  ix->pool = np;
+  return PSI_OK;
+}
+
+// Moves every leaf's points to consecutive slots in leaf order when more than
+// half of the pool's used slots are stale (points of rebuilt leaves).
+static psi_status porth_compact_if_needed(psi_index *ix, cudaStream_t s) {
+  if (ix->L == 0 || ix->pool_used <= 2 * ix->n + (int64_t(1) << 16)) return PSI_OK;
+  psi_status st;
+  Buf<int64_t> E;
+  if ((st = E.alloc(ix->L + 1, s))) return st;
+  if ((st = scan_i32_to_i64(ix->pl.cnt, E.p, ix->L, E.p + ix->L, s))) return st;
+  Pool np;
+  if ((st = alloc_pool(np, ix->D, ix->n + ix->n / 4 + 1024, s))) {
+    free_pool(np, s);
+    return st;
+  }
+  if (ix->D == 2)
+    PSI_LAUNCH_NAMED("k_pl_compact", k_pl_compact<2>, warp_grid(ix->L), 256, 0, s, ix->pl, E.p, ix->L, ix->pool, np);
+  else
+    PSI_LAUNCH_NAMED("k_pl_compact", k_pl_compact<3>, warp_grid(ix->L), 256, 0, s, ix->pl, E.p, ix->L, ix->pool, np);
+  free_pool(ix->pool, s);
+  ix->pool = np;
+  ix->pool_used = ix->n;
+  return PSI_OK;
+}
+
 psi_status porth_build(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t n, cudaStream_t s) {
   psi_status st;
   ix->n = n;
-  if ((st = alloc_pool(ix->pool, ix->D, std::max<int64_t>(n, 1), s))) return st;
+  free_pool(ix->pool, s);
+  free_pleaves(ix->pl, s);
+  ix->L = 0;
+  if ((st = alloc_pool(ix->pool, ix->D, std::max<int64_t>(n + n / 4, 1024), s))) return st;
   ix->pool_used = n;
-  if (n == 0) return porth_derive(ix, s);
+  if (n == 0) return porth_nodes(ix, s);
   Buf<uint64_t> k0, k1;
   Buf<uint32_t> v0, v1;
   if ((st = k0.alloc(n, s)) || (st = k1.alloc(n, s)) || (st = v0.alloc(n, s)) || (st = v1.alloc(n, s))) return st;
@@ -514,89 +953,196 @@ psi_status porth_build(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   else
     PSI_LAUNCH_NAMED("k_porth_gather", k_porth_gather<3>, grid_for(n), 256, 0, s, r.keys, r.vals, pts, ids, n,
                      ix->pool);
-  return porth_derive(ix, s);
+  WorkArray w{ix->pool.pkey, nullptr, nullptr, 0u, n};
+  int64_t L = 0;
+  if ((st = work_leaves(ix, w, ix->pl, &L, nullptr, s))) return st;
+  ix->L = L;
+  return porth_nodes(ix, s);
 }
 
-psi_status porth_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, cudaStream_t s) {
+// Local batch update (the batch sorted, then routed, dirty segments rebuilt).
+static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, bool insert,
+                               int64_t *d_deleted, cudaStream_t s) {
   psi_status st;
-  const int64_t n = ix->n;
+  const int D = ix->D, phi = ix->phi;
+  const int64_t L = ix->L, n = ix->n;
   Buf<uint64_t> k0, k1;
   Buf<uint32_t> v0, v1;
   if ((st = k0.alloc(m, s)) || (st = k1.alloc(m, s)) || (st = v0.alloc(m, s)) || (st = v1.alloc(m, s))) return st;
-  SortResult r;
+  SortResult br;
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, m, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
-                       ix->d_status, s, &r, ix->cfg.radix_bits)))
+                       ix->d_status, s, &br, ix->cfg.radix_bits)))
     return st;
-  Buf<int64_t> brank, shift;
-  Buf<int32_t> delta;
-  if ((st = brank.alloc(m, s)) || (st = delta.alloc(n + 1, s)) || (st = shift.alloc(n + 1, s))) return st;
-  PSI_CK(cudaMemsetAsync(delta.p, 0, sizeof(int32_t) * (n + 1), s));
-  PSI_LAUNCH(k_merge_ranks, grid_for(m), 256, 0, s, ix->pool.pkey, ix->pool.pid, n, r.keys, r.vals, ids, m, brank.p,
-             delta.p);
-  // Pool item i moves up by the number of batch items ranked at or before i:
-  // the exclusive scan of delta taken at i + 1.
-  if ((st = scan_i32_to_i64(delta.p, shift.p, n + 1, nullptr, s))) return st;
-  Pool np;
-  if ((st = alloc_pool(np, ix->D, n + m, s))) {
-    free_pool(np, s);
+  Buf<uint32_t> rid;
+  Buf<int32_t> rpt, bleaf, sbeg, send, diff, dirty, sstart, rem, keep, nc;
+  Buf<int64_t> E, dex, gx, woff, tot;
+  Buf<unsigned long long> del;
+  if ((st = rid.alloc(m, s)) || (st = rpt.alloc(m * D, s)) || (st = bleaf.alloc(m, s)) || (st = sbeg.alloc(L, s)) ||
+      (st = send.alloc(L, s)) || (st = diff.alloc(L + 1, s)) || (st = dirty.alloc(L, s)) ||
+      (st = sstart.alloc(L, s)) || (st = rem.alloc(L, s)) || (st = nc.alloc(L + 1, s)) || (st = E.alloc(L + 1, s)) ||
+      (st = dex.alloc(L + 2, s)) || (st = gx.alloc(L + 1, s)) || (st = woff.alloc(L + 1, s)) ||
+      (st = tot.alloc(4, s)) || (st = del.alloc(1, s)))
+    return st;
+  PSI_CK(cudaMemsetAsync(tot.p, 0, sizeof(int64_t) * 4, s));
+  if (D == 2)
+    PSI_LAUNCH_NAMED("k_prec", k_prec<2>, grid_for(m), 256, 0, s, br.vals, pts, ids, m, rid.p, rpt.p);
+  else
+    PSI_LAUNCH_NAMED("k_prec", k_prec<3>, grid_for(m), 256, 0, s, br.vals, pts, ids, m, rid.p, rpt.p);
+  PSI_CK(cudaMemsetAsync(sbeg.p, 0, sizeof(int32_t) * L, s));
+  PSI_CK(cudaMemsetAsync(send.p, 0, sizeof(int32_t) * L, s));
+  PSI_CK(cudaMemsetAsync(diff.p, 0, sizeof(int32_t) * (L + 1), s));
+  PSI_CK(cudaMemsetAsync(del.p, 0, sizeof(unsigned long long), s));
+  PSI_CK(cudaMemsetAsync(nc.p + L, 0, sizeof(int32_t), s));
+  if ((st = scan_i32_to_i64(ix->pl.cnt, E.p, L, E.p + L, s))) return st;
+  PSI_LAUNCH(k_route, grid_for(m), 256, 0, s, br.keys, m, ix->pl.key, L, bleaf.p);
+  PSI_LAUNCH(k_pslices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p);
+  PSI_LAUNCH(k_dirty_marks, grid_for(L), 256, 0, s, sbeg.p, send.p, E.p, L, n, phi, diff.p);
+  // dex = exclusive scan of diff over L + 1 entries (dex[x + 1] = inclusive sum at x)
+  if ((st = scan_i32_to_i64(diff.p, dex.p, L + 1, dex.p + L + 1, s))) return st;
+  PSI_LAUNCH(k_dirty_flags, grid_for(L), 256, 0, s, dex.p, L, dirty.p, sstart.p);
+  if (!insert) {
+    if ((st = keep.alloc(n, s))) return st;
+    if (D == 2)
+      PSI_LAUNCH_NAMED("k_pdel_marks", k_pdel_marks<2>, warp_grid(L), 256, 0, s, ix->pl, ix->pool, E.p, sbeg.p,
+                       send.p, L, br.keys, rid.p, rpt.p, keep.p, rem.p, del.p);
+    else
+      PSI_LAUNCH_NAMED("k_pdel_marks", k_pdel_marks<3>, warp_grid(L), 256, 0, s, ix->pl, ix->pool, E.p, sbeg.p,
+                       send.p, L, br.keys, rid.p, rpt.p, keep.p, rem.p, del.p);
+    PSI_LAUNCH(k_i64_from_u64, 1, 1, 0, s, del.p, tot.p + 3);
+    if (d_deleted) PSI_CK(cudaMemcpyAsync(d_deleted, tot.p + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  }
+  PSI_LAUNCH(k_newcount, grid_for(L), 256, 0, s, dirty.p, ix->pl.cnt, sbeg.p, send.p, rem.p, L, insert, nc.p);
+  if ((st = scan_i32_to_i64(nc.p, woff.p, L + 1, tot.p, s))) return st;  // woff[L] = total new points S
+  if ((st = scan_i32_to_i64(sstart.p, gx.p, L, tot.p + 1, s))) return st;
+  PSI_CK(cudaMemcpyAsync(gx.p + L, tot.p + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  int64_t h[4] = {0, 0, 0, 0};
+  PSI_CK(cudaMemcpyAsync(h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  const int64_t S = h[0], G = h[1];
+  const int64_t n_new = insert ? n + m : n - h[3];
+  if (G == 0) {  // nothing reached a leaf (a delete of absent points)
+    ix->n = n_new;
+    return PSI_OK;
+  }
+  // segments, their context, the work array
+  Buf<int32_t> xs, xe, ctxl, ctxr, ctx;
+  Buf<int64_t> cxoff;
+  if ((st = xs.alloc(G, s)) || (st = xe.alloc(G, s)) || (st = ctxl.alloc(G, s)) || (st = ctxr.alloc(G, s)) ||
+      (st = ctx.alloc(G, s)) || (st = cxoff.alloc(G + 1, s)))
+    return st;
+  PSI_LAUNCH(k_seg_bounds, grid_for(L), 256, 0, s, dirty.p, sstart.p, gx.p, L, xs.p, xe.p);
+  PSI_LAUNCH(k_seg_ctx, grid_for(G), 256, 0, s, xs.p, xe.p, E.p, G, n, phi, ctxl.p, ctxr.p, ctx.p);
+  if ((st = scan_i32_to_i64(ctx.p, cxoff.p, G, cxoff.p + G, s))) return st;
+  int64_t hc = 0;
+  PSI_CK(cudaMemcpyAsync(&hc, cxoff.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  const int64_t W = S + hc;
+  const uint32_t fresh = (uint32_t)ix->pool_used;
+  if ((st = porth_grow(ix, ix->pool_used + S, s))) return st;
+  Buf<uint64_t> wkey;
+  Buf<int32_t> wmask;
+  Buf<uint32_t> wslot;
+  if ((st = wkey.alloc(std::max<int64_t>(W, 1), s)) || (st = wmask.alloc(std::max<int64_t>(W, 1), s)) ||
+      (st = wslot.alloc(std::max<int64_t>(W, 1), s)))
+    return st;
+  SegArgs a;
+  a.pl = ix->pl;
+  a.pool = ix->pool;
+  a.E = E.p;
+  a.dirty = dirty.p;
+  a.sstart = sstart.p;
+  a.xs = xs.p;
+  a.xe = xe.p;
+  a.ctxl = ctxl.p;
+  a.ctxr = ctxr.p;
+  a.gx = gx.p;
+  a.woff = woff.p;
+  a.cxoff = cxoff.p;
+  a.sbeg = sbeg.p;
+  a.send = send.p;
+  a.keep = keep.p;
+  a.bkeys = br.keys;
+  a.rid = rid.p;
+  a.rpt = rpt.p;
+  a.L = L;
+  a.G = G;
+  a.n = n;
+  a.fresh = fresh;
+  a.insert = insert;
+  a.wkey = wkey.p;
+  a.wmask = wmask.p;
+  a.wslot = wslot.p;
+  PSI_LAUNCH(k_seg_context, warp_grid(G), 256, 0, s, a);
+  if (D == 2)
+    PSI_LAUNCH_NAMED("k_seg_points", k_seg_points<2>, warp_grid(L), 256, 0, s, a);
+  else
+    PSI_LAUNCH_NAMED("k_seg_points", k_seg_points<3>, warp_grid(L), 256, 0, s, a);
+  ix->pool_used += S;
+  // the segments' new leaves
+  PLeaves nl;
+  int64_t NL = 0;
+  Buf<int64_t> rank, fl;
+  WorkArray w{wkey.p, wmask.p, wslot.p, 0u, W};
+  if (W > 0) {
+    if ((st = work_leaves(ix, w, nl, &NL, &rank, s))) {
+      free_pleaves(nl, s);
+      return st;
+    }
+  }
+  Buf<int32_t> outl;
+  Buf<int64_t> pos;
+  if ((st = fl.alloc(G + 1, s)) || (st = outl.alloc(L, s)) || (st = pos.alloc(L + 1, s))) {
+    free_pleaves(nl, s);
     return st;
   }
-  if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_merge_scatter", k_merge_scatter<2>, grid_for(n + m), 256, 0, s, ix->pool, n, shift.p + 1,
-                     r.keys, r.vals, pts, ids, m, brank.p, np);
+  if (W > 0) {
+    PSI_LAUNCH(k_seg_first_leaf, grid_for(G + 1), 256, 0, s, a, rank.p, W, NL, fl.p);
+  } else {
+    PSI_CK(cudaMemsetAsync(fl.p, 0, sizeof(int64_t) * (G + 1), s));
+  }
+  PSI_LAUNCH(k_pl_outl, grid_for(L), 256, 0, s, dirty.p, sstart.p, gx.p, fl.p, L, outl.p);
+  if ((st = scan_i32_to_i64(outl.p, pos.p, L, pos.p + L, s))) {
+    free_pleaves(nl, s);
+    return st;
+  }
+  int64_t Lnew = 0;
+  PSI_CK(cudaMemcpyAsync(&Lnew, pos.p + L, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  PLeaves out;
+  if ((st = alloc_pleaves(out, D, Lnew, s))) {
+    free_pleaves(nl, s);
+    free_pleaves(out, s);
+    return st;
+  }
+  if (D == 2)
+    PSI_LAUNCH_NAMED("k_pl_assemble", k_pl_assemble<2>, grid_for(std::max(L, NL)), 256, 0, s, ix->pl, dirty.p, pos.p,
+                     L, nl, NL, fl.p, xs.p, G, out);
   else
-    PSI_LAUNCH_NAMED("k_merge_scatter", k_merge_scatter<3>, grid_for(n + m), 256, 0, s, ix->pool, n, shift.p + 1,
-                     r.keys, r.vals, pts, ids, m, brank.p, np);
-  free_pool(ix->pool, s);
-  ix->pool = np;
-  ix->n = n + m;
-  ix->pool_used = n + m;
-  return porth_derive(ix, s);
+    PSI_LAUNCH_NAMED("k_pl_assemble", k_pl_assemble<3>, grid_for(std::max(L, NL)), 256, 0, s, ix->pl, dirty.p, pos.p,
+                     L, nl, NL, fl.p, xs.p, G, out);
+  free_pleaves(nl, s);
+  free_pleaves(ix->pl, s);
+  ix->pl = out;
+  ix->L = Lnew;
+  ix->n = n_new;
+  if ((st = porth_compact_if_needed(ix, s))) return st;
+  return porth_nodes(ix, s);
+}
+
+psi_status porth_insert(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, cudaStream_t s) {
+  if (ix->L == 0) {  // empty index: a fresh build of the batch
+    return porth_build(ix, pts, ids, m, s);
+  }
+  return porth_update(ix, pts, ids, m, true, nullptr, s);
 }
 
 psi_status porth_delete(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t m, int64_t *d_deleted,
                         cudaStream_t s) {
-  psi_status st;
-  const int64_t n = ix->n;
-  Buf<uint64_t> k0, k1;
-  Buf<uint32_t> v0, v1;
-  if ((st = k0.alloc(m, s)) || (st = k1.alloc(m, s)) || (st = v0.alloc(m, s)) || (st = v1.alloc(m, s))) return st;
-  SortResult r;
-  if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, m, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
-                       ix->d_status, s, &r, ix->cfg.radix_bits)))
-    return st;
-  Buf<int32_t> keep;
-  Buf<int64_t> pos, tot;
-  Buf<unsigned long long> del;
-  if ((st = keep.alloc(n, s)) || (st = pos.alloc(n, s)) || (st = tot.alloc(2, s)) || (st = del.alloc(1, s))) return st;
-  PSI_LAUNCH(k_fill_i32, grid_for(n), 256, 0, s, keep.p, n, 1);
-  PSI_CK(cudaMemsetAsync(del.p, 0, sizeof(unsigned long long), s));
-  if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_mark_deleted", k_mark_deleted<2>, grid_for(m), 256, 0, s, ix->pool.pkey, ix->pool.pid,
-                     ix->pool, n, r.keys, r.vals, pts, ids, m, keep.p, del.p);
-  else
-    PSI_LAUNCH_NAMED("k_mark_deleted", k_mark_deleted<3>, grid_for(m), 256, 0, s, ix->pool.pkey, ix->pool.pid,
-                     ix->pool, n, r.keys, r.vals, pts, ids, m, keep.p, del.p);
-  if ((st = scan_i32_to_i64(keep.p, pos.p, n, tot.p, s))) return st;
-  PSI_LAUNCH(k_i64_from_u64, 1, 1, 0, s, del.p, tot.p + 1);
-  if (d_deleted) PSI_CK(cudaMemcpyAsync(d_deleted, tot.p + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-  int64_t h[2];
-  PSI_CK(cudaMemcpyAsync(h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-  PSI_CK(cudaStreamSynchronize(s));
-  Pool np;
-  if ((st = alloc_pool(np, ix->D, std::max<int64_t>(h[0], 1), s))) {
-    free_pool(np, s);
-    return st;
+  if (ix->L == 0) {
+    if (d_deleted) PSI_CK(cudaMemsetAsync(d_deleted, 0, sizeof(int64_t), s));
+    return PSI_OK;
   }
-  if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_compact_points", k_compact_points<2>, grid_for(n), 256, 0, s, ix->pool, n, keep.p, pos.p, np);
-  else
-    PSI_LAUNCH_NAMED("k_compact_points", k_compact_points<3>, grid_for(n), 256, 0, s, ix->pool, n, keep.p, pos.p, np);
-  free_pool(ix->pool, s);
-  ix->pool = np;
-  ix->n = h[0];
-  ix->pool_used = h[0];
-  return porth_derive(ix, s);
+  return porth_update(ix, pts, ids, m, false, d_deleted, s);
 }
 
 }  // namespace psi

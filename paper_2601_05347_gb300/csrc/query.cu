@@ -102,18 +102,17 @@ struct KnnArgs {
 // Scan one leaf: every point whose (d2, id) beats the current k-th enters the
 // list (klist_offer: in bulk when many enter at once, the seed leaves of a
 // query; one at a time otherwise).
-// Slots [s0, s0 + cnt), except those in [skip_lo, skip_hi) (already scanned).
+// Slots [s0, s0 + cnt).
 // EMPTY: the list is known to be empty (the first leaf a query scans).
 template <int D, int KPL, bool EMPTY = false>
 __device__ __forceinline__ void knn_scan_slots(const TreeView &t, uint32_t s0, int cnt, const int32_t *qc,
-                                               KList<KPL> &kl, int k, uint32_t skip_lo = 1, uint32_t skip_hi = 0) {
+                                               KList<KPL> &kl, int k) {
   const int lane = threadIdx.x & 31;
   for (int b = 0; b < cnt; b += 32) {
     const int s = b + lane;
     int64_t d2 = INT64_MAX;
     uint32_t id = 0xFFFFFFFFu;
-    const uint32_t sl = s0 + (uint32_t)s;
-    const bool valid = s < cnt && !(sl >= skip_lo && sl < skip_hi);
+    const bool valid = s < cnt;
     if (valid) {
       const uint32_t slot = s0 + (uint32_t)s;
       id = t.pid[slot];
@@ -135,8 +134,8 @@ __device__ __forceinline__ void knn_scan_slots(const TreeView &t, uint32_t s0, i
 
 template <int D, int KPL, bool EMPTY = false>
 __device__ __forceinline__ void knn_scan_leaf(const TreeView &t, uint32_t node, const int32_t *qc, KList<KPL> &kl,
-                                              int k, uint32_t skip_lo = 1, uint32_t skip_hi = 0) {
-  knn_scan_slots<D, KPL, EMPTY>(t, t.ref[node], t.cnt[node], qc, kl, k, skip_lo, skip_hi);
+                                              int k) {
+  knn_scan_slots<D, KPL, EMPTY>(t, t.ref[node], t.cnt[node], qc, kl, k);
 }
 
 // 32-bit image of a non-negative distance for pruning: the float bits of the
@@ -188,9 +187,7 @@ __global__ void k_knn_seed(const KnnSeed sd, const uint32_t *ref, const uint32_t
   for (int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < nq; qi += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = sd.qkey[qi] & sd.qkey_mask;
     int64_t p = 0;
-    if (sd.pkey && sd.n_slots > 0) {
-      p = seed_search([&](int64_t x) { return sd.pkey[x]; }, sd.n_slots, key, sd.key_shift);
-    } else if (sd.qseg) {
+    if (sd.qseg) {
       const int64_t q = order ? (int64_t)order[qi] : qi;
       const int sg = sd.qseg[q];
       const int64_t lb = sd.node_off[sg];
@@ -241,21 +238,9 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
       lb = sd.node_off[sg];
       L = (sd.off[sg + 1] - sd.off[sg] + sd.phi - 1) / sd.phi;
     }
-    // P-Orth (k > 32): the 32 * KPL points of the key-sorted pool around the
-    // query's key are scanned first, 32 at a time, and skipped point by point
-    // afterwards
-    const bool by_slots = sd.pkey && sd.n_slots > 0;
-    uint32_t sk_lo = 1, sk_hi = 0;
     if (sd.qkey && root >= 0) {
       const int64_t pos = sd.pos[qi];  // k_knn_seed
-      if (by_slots) {
-        const int64_t want = min((int64_t)32 * KPL, sd.n_slots);
-        const int64_t lo = max((int64_t)0, min(pos - want / 2, sd.n_slots - want));
-        sk_lo = (uint32_t)lo;
-        sk_hi = (uint32_t)(lo + want);
-        knn_scan_slots<D, KPL, true>(t, sk_lo, (int)want, qc, kl, a.k);
-        if (STATS) n_pts += want;
-      } else if (L > 0) {
+      if (L > 0) {
         const int64_t j = pos;
         const int64_t le = lb + L;
         knn_scan_leaf<D, KPL, true>(t, (uint32_t)j, qc, kl, a.k);
@@ -282,8 +267,8 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
       }
     }
     // seed leaves as a node range [slo, shi] (empty: slo > shi)
-    const uint32_t slo = by_slots || s_hi < s_lo ? 1u : (uint32_t)s_lo;
-    const uint32_t shi = by_slots || s_hi < s_lo ? 0u : (uint32_t)s_hi;
+    const uint32_t slo = s_hi < s_lo ? 1u : (uint32_t)s_lo;
+    const uint32_t shi = s_hi < s_lo ? 0u : (uint32_t)s_hi;
     uint32_t kdk = order_key(kl.kd);
     int sp = 0;
     // Children [c0, c0 + nk) of an expanded node: the internal ones that may
@@ -346,7 +331,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
         ml &= ~(1u << src);
         const uint32_t lref = __shfl_sync(0xFFFFFFFFu, cref, src);
         const int lcnt = __shfl_sync(0xFFFFFFFFu, ccnt, src);
-        knn_scan_slots<D, KPL>(t, lref, lcnt, qc, kl, a.k, sk_lo, sk_hi);
+        knn_scan_slots<D, KPL>(t, lref, lcnt, qc, kl, a.k);
         kdk = order_key(kl.kd);
         if (STATS) {
           ++n_leaf;
@@ -357,7 +342,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     if (root >= 0) {
       if (t.kids[root] == 0) {
         if (!((uint32_t)root >= slo && (uint32_t)root <= shi))
-          knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k, sk_lo, sk_hi);
+          knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k);
       } else {
         // the root as the first entry: one call site keeps `expand` inlined
         uint32_t c0 = t.ref[root];
@@ -864,15 +849,10 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
     seed.L = ix->L;
     seed.key_shift = qo.key_shift;
     seed.pos = qo.spare;
-    if (ix->cfg.kind == PSI_PORTH) {
-      // P-Orth leaves do not overlap and the search is near its floor; the
-      // seed pays off only in cutting single insertions into long lists
-      if (k <= 32) seed.qkey = nullptr;
-      seed.pkey = ix->pool.pkey;
-      seed.n_slots = ix->n;
-    } else {
-      seed.sep_key = ix->sep_key;
-    }
+    seed.sep_key = ix->sep_key;
+    // P-Orth leaves do not overlap: its search starts at the root without a
+    // seed and stays near the floor of leaves it must scan
+    if (ix->cfg.kind == PSI_PORTH) seed.qkey = nullptr;
   }
   return run_knn_roots(ix->view(), q, nq, k, qo.order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s,
                        seed, ix->cfg.kind == PSI_PORTH ? -1 : ix->L);

@@ -28,6 +28,7 @@
 // k_tie_long (a later canonical leaf layout depends on it).
 #include "common.cuh"
 #include <cuda.h>
+#include <cmath>
 #include <mutex>
 #include <type_traits>
 
@@ -58,6 +59,7 @@ struct EventGuard {
 constexpr int64_t kPackMin = int64_t(1) << 22;  // smallest encoding sort that may pack
 constexpr int kPrefixBits = 48;                   // key bits sorted by a prefix sort
 constexpr int kPrefixShort = 8;                   // longest run fixed in registers
+constexpr double kPrefixMaxRun = 1.15;            // largest mean run of equal top bits for a prefix sort
 constexpr int64_t kPrefixMin = int64_t(1) << 20;  // smallest encoding sort that may sort a prefix only
 
 // Digit width RB in {8, 10, 11}: RADIX digits, DPT digits per thread in the
@@ -128,14 +130,23 @@ enum : int {
 };
 
 // Optional extras of the histogram pass: the histogram of an alternative
-// first digit ((key >> alt_shift) & mask, into hist_alt) and a second count of
-// input neighbours agreeing above near2_shift.
+// first digit ((key >> alt_shift) & mask, into hist_alt) and a HyperLogLog
+// sketch of the distinct values of key >> alt_shift (kHllRegs registers, into
+// hll), from which the host estimates how many keys share their top bits.
+constexpr int kHllBits = 12, kHllRegs = 1 << kHllBits;
 struct HistExtra {
   uint32_t *hist_alt = nullptr;
   int alt_shift = 0;
-  unsigned long long *near2 = nullptr;
-  int near2_shift = 0;
+  uint32_t *hll = nullptr;
 };
+
+// SplitMix64's finaliser (Steele, Lea, Flood 2014) as the sketch's hash.
+__device__ __forceinline__ uint64_t hll_hash(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
 
 // Digit histograms of all passes in one read; when encoding with kst set, the
 // keys are also written out (in input order) for the digit passes to read.  With 8-bit digits the counts go
@@ -153,12 +164,14 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   const int secs = passes + (ex.hist_alt ? 1 : 0);
   uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][secs][RADIX]
   uint8_t *htab = smem_raw + sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX;
+  uint32_t *shll = reinterpret_cast<uint32_t *>(htab + kCurveTabBytes);  // [kHllRegs] when ex.hll
   for (int i = threadIdx.x; i < R::HIST_PARTS * secs * R::RADIX; i += blockDim.x) shp[i] = 0;
+  if (ex.hll)
+    for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) shll[i] = 0;
   if (MODE == 1) curve_table_init<D, CURVE>(htab);
   __syncthreads();
   bool bad_any = false;
-  uint32_t n_near = 0;   // input neighbours (i, i + 1) whose keys agree above near_shift
-  uint32_t n_near2 = 0;  // ... above ex.near2_shift
+  uint32_t n_near = 0;  // input neighbours (i, i + 1) whose keys agree above near_shift
   uint32_t *mine = shp + (threadIdx.x % R::HIST_PARTS) * secs * R::RADIX;
   // HIST_U items per thread per round, their loads issued together
   const int64_t chunk = (int64_t)blockDim.x * HIST_U;
@@ -192,15 +205,23 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
         }
       }
     }
-    if (near || ex.near2) {
+    if (near) {
 #pragma unroll
       for (int u = 0; u < HIST_U; ++u) {
         const uint64_t kn = __shfl_down_sync(0xFFFFFFFFu, k[u], 1);
         const bool okn = __shfl_down_sync(0xFFFFFFFFu, ok[u], 1);
-        const bool pair = (threadIdx.x & 31) < 31 && ok[u] && okn;
-        n_near += pair && ((k[u] ^ kn) >> near_shift) == 0;
-        n_near2 += pair && ((k[u] ^ kn) >> ex.near2_shift) == 0;
+        n_near += (threadIdx.x & 31) < 31 && ok[u] && okn && ((k[u] ^ kn) >> near_shift) == 0;
       }
+    }
+    if (ex.hll) {
+#pragma unroll
+      for (int u = 0; u < HIST_U; ++u)
+        if (ok[u]) {
+          const uint64_t h = hll_hash(k[u] >> ex.alt_shift);
+          // register: the top kHllBits of the hash; value: 1 + leading zeros of the rest
+          const uint32_t rho = (uint32_t)__clzll((long long)((h << kHllBits) | (1ull << (kHllBits - 1)))) + 1u;
+          atomicMax(&shll[h >> (64 - kHllBits)], rho);
+        }
     }
 #pragma unroll
     for (int u = 0; u < HIST_U; ++u) {
@@ -222,8 +243,10 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   }
   if (bad_any) atomicOr(status, ST_RANGE);
   if (near) block_count_add(near, n_near);
-  if (ex.near2) block_count_add(ex.near2, n_near2);
   __syncthreads();
+  if (ex.hll)
+    for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x)
+      if (shll[i]) atomicMax(&ex.hll[i], shll[i]);
   for (int i = threadIdx.x; i < secs * R::RADIX; i += blockDim.x) {
     uint32_t v = 0;
 #pragma unroll
@@ -819,7 +842,8 @@ static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_
                               unsigned long long *near = nullptr, int near_shift = 0, HistExtra ex = HistExtra()) {
   using R = Radix<RB>;
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
-  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX + kCurveTabBytes;
+  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX + kCurveTabBytes +
+                      (ex.hll ? sizeof(uint32_t) * kHllRegs : 0);
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // all blocks resident at once (the grid-stride rounds stay balanced)
   int per_sm = 0;
@@ -851,6 +875,22 @@ static psi_status launch_packed(const EncodeSpec &enc, const PassArgs &a, int64_
   }
   set_error("sort: packed passes need 8-bit digits");
   return PSI_ERR_INVALID;
+}
+
+// HyperLogLog estimate of the number of distinct values sketched in M
+// (Flajolet, Fusy, Gandouet, Meunier 2007), with linear counting for small
+// cardinalities.
+static double hll_estimate(const uint32_t *M) {
+  const double m = kHllRegs;
+  double z = 0.0;
+  int zeros = 0;
+  for (int j = 0; j < kHllRegs; ++j) {
+    z += std::ldexp(1.0, -(int)M[j]);
+    zeros += M[j] == 0;
+  }
+  double e = 0.7213 / (1.0 + 1.079 / m) * m * m / z;
+  if (e <= 2.5 * m && zeros > 0) e = m * std::log(m / zeros);
+  return e;
 }
 
 // Digit width: 8 unless 10 or 11 is asked for.  Wider digits save passes but
@@ -912,17 +952,22 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   // reading each key (or point) at its position.  Those reads are local only
   // when the input is: the histogram pass counts input neighbours whose keys
   // share their top 24 bits, and the sort packs when at least half do.
-  // The counts reach the host through pinned words behind an event, read when
-  // the first decision needs them (the prefix decision before pass 0; else
-  // the packing decision just before the pack pass, the passes before it
-  // queued meanwhile).  Two words per host thread, allocated on its first
-  // such sort and kept for the thread's lifetime.
-  static thread_local unsigned long long *h_near = nullptr;
+  // The count (and the prefix sort's sketch) reach the host through pinned
+  // memory behind an event, read when the first decision needs them (the
+  // prefix decision before pass 0; else the packing decision just before the
+  // pack pass, the passes before it queued meanwhile).  The pinned buffer is
+  // per host thread, allocated on its first such sort and kept for the
+  // thread's lifetime.
+  struct HostCounts {
+    unsigned long long near;
+    uint32_t hll[kHllRegs];
+  };
+  static thread_local HostCounts *h_cnt = nullptr;
   bool counts = pref_cand || pack_cand;
-  if (counts && !h_near &&
-      cudaHostAlloc((void **)&h_near, 2 * sizeof(unsigned long long), cudaHostAllocPortable) != cudaSuccess) {
+  if (counts && !h_cnt &&
+      cudaHostAlloc((void **)&h_cnt, sizeof(HostCounts), cudaHostAllocPortable) != cudaSuccess) {
     cudaGetLastError();
-    h_near = nullptr;
+    h_cnt = nullptr;
     counts = false;
   }
   Buf<unsigned long long> nearc;
@@ -932,17 +977,22 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     near_ev.e = nullptr;
     counts = false;
   }
+  Buf<uint32_t> hll;
   if (counts) {
-    if ((st = nearc.alloc(2, s))) return st;
-    PSI_CK(cudaMemsetAsync(nearc.p, 0, 2 * sizeof(unsigned long long), s));
+    if ((st = nearc.alloc(1, s))) return st;
+    PSI_CK(cudaMemsetAsync(nearc.p, 0, sizeof(unsigned long long), s));
+  }
+  const bool sketch = counts && pref_cand;
+  if (sketch) {
+    if ((st = hll.alloc(kHllRegs, s))) return st;
+    PSI_CK(cudaMemsetAsync(hll.p, 0, sizeof(uint32_t) * kHllRegs, s));
   }
   const int near_shift = std::max(0, key_bits - 24);
   HistExtra ex;
-  if (counts && pref_cand) {
+  if (sketch) {
     ex.hist_alt = hist.p + (size_t)passes_full * R::RADIX;
     ex.alt_shift = low_c;
-    ex.near2 = nearc.p + 1;
-    ex.near2_shift = low_c;
+    ex.hll = hll.p;
   }
   unsigned long long *nearp = counts ? nearc.p : nullptr;
 
@@ -960,14 +1010,17 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   if (st) return st;
   bool synced = false;
   if (counts) {
-    PSI_CK(cudaMemcpyAsync(h_near, nearc.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PSI_CK(cudaMemcpyAsync(&h_cnt->near, nearc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    if (sketch) PSI_CK(cudaMemcpyAsync(h_cnt->hll, hll.p, sizeof(h_cnt->hll), cudaMemcpyDeviceToHost, s));
     PSI_CK(cudaEventRecord(near_ev.e, s));
   }
   int low = 0;
-  if (counts && pref_cand) {
+  if (sketch) {
     PSI_CK(cudaEventSynchronize(near_ev.e));
     synced = true;
-    if (2 * h_near[1] < (unsigned long long)n) low = low_c;
+    // prefix sort when the keys' top bits take nearly n distinct values (runs
+    // of equal top bits are then few and short)
+    if ((double)n < kPrefixMaxRun * hll_estimate(h_cnt->hll)) low = low_c;
   }
   const int passes = (key_bits - low + RB - 1) / RB;
   int pk = passes, p_pack = passes;
@@ -985,7 +1038,7 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     if (p == p_pack) {
       if (!synced) PSI_CK(cudaEventSynchronize(near_ev.e));
       synced = true;
-      if (2 * h_near[0] >= (unsigned long long)n) {
+      if (2 * h_cnt->near >= (unsigned long long)n) {
         pk = p_pack;
         drop = low + RB * (pk + 1);
         kr = key_bits - drop;

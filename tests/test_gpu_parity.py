@@ -168,25 +168,34 @@ def test_build_across_the_packed_sort_threshold(kind, dim, bits, n, clustered):
         check_spac_layout(ix, o)
 
 
-@pytest.mark.parametrize("kind,dim,bits,n,region", [("spac_z", 2, 30, (1 << 20) + 17, 15),
-                                                    ("spac_h", 2, 30, (1 << 20) + 3, 12),
-                                                    ("spac_z", 2, 30, (1 << 20) + 13, 9),
-                                                    ("porth", 2, 30, (1 << 20) + 9, 15),
-                                                    ("spac_z", 3, 21, (1 << 20) + 1, 21),
-                                                    ("spac_h", 3, 21, (1 << 20) + 11, 11),
-                                                    ("spac_h", 2, 30, (1 << 20) + 5, 30)])
-def test_build_prefix_sort_runs(kind, dim, bits, n, region):
-    # an encoding sort of at least 2^20 pairs whose input neighbours rarely
-    # share their top 48 key bits (points in random order) sorts those bits
-    # only, then puts each run of equal top bits in (key, id) order: points in
-    # [0, 2^region)^dim give runs of up to a few points (fixed in registers),
-    # about 250 (fixed in shared memory) and 1.6e4 (fixed in global memory),
-    # with duplicate points among them
-    p = gen.uniform(n, dim, region, 500 + n % 1000).astype(np.int32)
+@pytest.mark.parametrize("kind,dim,bits,n", [("spac_z", 2, 30, (1 << 20) + 17), ("spac_h", 2, 30, (1 << 20) + 3),
+                                             ("porth", 2, 30, (1 << 20) + 9), ("spac_z", 3, 21, (1 << 20) + 1),
+                                             ("spac_h", 3, 21, (1 << 20) + 11), ("porth", 3, 21, (1 << 20) + 5)])
+def test_build_prefix_sort_runs(kind, dim, bits, n):
+    # an encoding sort of at least 2^20 pairs whose keys take nearly n distinct
+    # values in their top 48 bits (here: points in random order over the whole
+    # domain) sorts those bits only, then puts each run of equal top bits in
+    # (key, id) order.  Copies of existing points make runs of every kind:
+    # 2..8 (fixed in registers), 20 and 300 (fixed in shared memory) and 5000
+    # (fixed in global memory); the runs are few, so the prefix sort is taken.
+    p = gen.uniform(n, dim, bits, 500 + n % 1000).astype(np.int32)
+    rng = np.random.default_rng(n)
+    src = rng.integers(0, n, 9000)
+    pos = rng.permutation(n)[:len(src) + 5320]
+    p[pos[:9000]] = p[src]                      # pairs and small runs
+    for size, off in ((20, 9000), (300, 9020), (5000, 9320)):
+        p[pos[off:off + size]] = p[src[size % 97]]  # piles of one point
     perm = np.argsort(gen.splitmix64(n, np.arange(n, dtype=np.uint64)), kind="stable").astype(np.uint64)
     with np.errstate(over="ignore"):
         ids = ((perm * np.uint64(2654435761) + np.uint64(7)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
-    ix = psi.Index(T(p), T(ids), kind=kind, leaf_size=32, coord_bits=bits)
+    dp, di = T(p), T(ids)
+    psi.profile_enable(True)
+    psi.profile_reset()
+    ix = psi.Index(dp, di, kind=kind, leaf_size=32, coord_bits=bits)
+    ix.sync()
+    launched = psi.profile_dump()
+    psi.profile_enable(False)
+    assert "k_prefix_runs" in launched and "k_prefix_long" in launched  # the prefix sort was taken
     o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
     if kind == "porth":
         check_porth_nodes(ix, o)
@@ -529,6 +538,66 @@ def test_porth_build_matches_oracle(dim, bits, phi, clustered, dup):
     ix = psi.Index(T(p), T(ids), kind="porth", leaf_size=phi, coord_bits=bits)
     o = O.Index(p, ids, dim=dim, kind=O.PORTH, phi=phi, bits=bits)
     check_porth_nodes(ix, o)
+
+
+@pytest.mark.parametrize("dim,bits,phi", [(2, 30, 8), (3, 21, 32), (2, 30, 32)])
+def test_porth_local_updates_match_a_fresh_build(dim, bits, phi):
+    # many small batches: each rebuilds only the leaves within phi + 1 points
+    # of a changed point; after every batch the node list must equal the
+    # canonical tree of the new point set
+    n = 40000
+    p, ids = points(n, dim, bits, 300 + phi, clustered=True)
+    ix = psi.Index(T(p), T(ids), kind="porth", leaf_size=phi, coord_bits=bits)
+    o = O.Index(p, ids, dim=dim, kind=O.PORTH, phi=phi, bits=bits)
+    live_p, live_i = p.copy(), ids.copy()
+    rng = np.random.default_rng(phi + dim)
+    next_id = 10_000_000
+    for step in range(16):
+        kind = step % 4
+        if kind in (0, 2):   # insert: new points, copies of existing points (duplicate piles), far points
+            mi = int(rng.integers(1, 300))
+            newp = gen.varden(mi, dim, bits, 400 + step)
+            cp = live_p[rng.integers(0, len(live_p), mi // 3 + 1)]
+            far = gen.uniform(3, dim, bits, 500 + step)
+            newp = np.concatenate([newp, cp, cp[:2], far]).astype(np.int32)
+            newi = (np.arange(len(newp)) + next_id).astype(np.uint32)
+            next_id += len(newp)
+            ix.insert(T(newp), T(newi))
+            o.insert(newp, newi)
+            live_p = np.concatenate([live_p, newp])
+            live_i = np.concatenate([live_i, newi])
+        else:                # delete: live points (a whole neighbourhood when kind == 3) and absent ones
+            md = int(rng.integers(1, 300))
+            if kind == 3:
+                c = rng.integers(0, len(live_p))
+                d2 = ((live_p.astype(np.int64) - live_p[c].astype(np.int64)) ** 2).sum(1)
+                sel = np.argsort(d2, kind="stable")[:md]
+            else:
+                sel = rng.choice(len(live_p), md, replace=False)
+            dp = np.concatenate([live_p[sel], gen.uniform(2, dim, bits, 600 + step)]).astype(np.int32)
+            di = np.concatenate([live_i[sel], [0xFFFFFFF0, 0xFFFFFFF1]]).astype(np.uint32)
+            nd = torch.zeros(1, dtype=torch.int64, device=DEV)
+            ix.delete(T(dp), T(di), nd)
+            assert int(nd.item()) == o.delete(dp, di) == len(sel)
+            keep = np.ones(len(live_i), bool)
+            keep[sel] = False
+            live_p, live_i = live_p[keep], live_i[keep]
+        ix.sync()
+        assert len(ix) == len(o) == len(live_i)
+        check_porth_nodes(ix, o)
+    q = query_points(3000, dim, bits, 9, live_p)
+    for k in (10, 100):
+        gi, gd = ix.knn(T(q), k)
+        oi, od = o.knn(q, k)
+        assert (U32(gi) == oi).all() and (gd.cpu().numpy() == od).all()
+    # delete everything, then insert into the empty tree
+    nd = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ix.delete(T(live_p), T(live_i), nd)
+    ix.sync()
+    assert int(nd.item()) == len(live_i) and len(ix) == 0 and ix.num_nodes == 0
+    ix.insert(T(p[:5000]), T(ids[:5000]))
+    ix.sync()
+    check_porth_nodes(ix, O.Index(p[:5000], ids[:5000], dim=dim, kind=O.PORTH, phi=phi, bits=bits))
 
 
 def test_porth_tiny():
