@@ -218,63 +218,79 @@ __global__ void k_work_starts(WorkArray w, const int32_t *ldepth, int D, int bit
   }
 }
 
-// Leaf records: leaf rank[i] for every start i (first slot, depth, cell key),
-// and its count at its last point.
+// Leaf records: leaf rank[i] for every start i (first slot, depth, cell
+// key).  The points of consecutive leaves occupy consecutive slots (a build's
+// pool, or the fresh slots of an update in work order), so counts follow
+// from the first slots (k_leaf_counts).
 __global__ void k_work_leaves(WorkArray w, const int32_t *ldepth, const int32_t *start, const int64_t *rank, int D,
                               int bits, PLeaves out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (!work_point(w, i)) continue;
-    const int64_t r = rank[i] + start[i] - 1;  // the leaf of point i
-    if (start[i]) {
-      const int d = ldepth[i];
-      const int sh = D * (bits - d);
-      out.ref[r] = work_slot(w, i);
-      out.depth[r] = d;
-      out.key[r] = sh >= 64 ? 0 : ((w.key[i] >> sh) << sh);
+    if (!work_point(w, i) || !start[i]) continue;
+    const int64_t r = rank[i];
+    const int d = ldepth[i];
+    const int sh = D * (bits - d);
+    out.ref[r] = work_slot(w, i);
+    out.depth[r] = d;
+    out.key[r] = sh >= 64 ? 0 : ((w.key[i] >> sh) << sh);
+  }
+}
+
+// cnt[r] = ref[r + 1] - ref[r]; the last leaf ends at slot `end`.
+__global__ void k_leaf_counts(PLeaves pl, int64_t L, uint32_t end) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < L; r += (int64_t)gridDim.x * blockDim.x)
+    pl.cnt[r] = (int32_t)((r + 1 < L ? pl.ref[r + 1] : end) - pl.ref[r]);
+}
+
+// Leaf boxes by a segmented reduction over the points in work order (each
+// point's leaf = the rank of its leaf's start): lanes of a warp combine the
+// points of the same leaf, and the first lane of each leaf in the warp
+// merges the result into the leaf's box (boxes start empty).
+template <int D>
+__global__ void k_work_boxes(WorkArray w, const int32_t *start, const int64_t *rank, Pool pool, PLeaves pl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < w.n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool pt = i < w.n && work_point(w, i);
+    int64_t leaf = pt ? rank[i] + start[i] - 1 : -1;
+    int32_t lo[D], hi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int32_t v = pt ? pool.px[d][work_slot(w, i)] : 0;
+      lo[d] = pt ? v : INT32_MAX;
+      hi[d] = pt ? v : INT32_MIN;
     }
-    const bool last = i + 1 == w.n || !work_point(w, i + 1) || start[i + 1];
-    if (last) {
-      // the leaf's first slot, read back through its first point
-      int64_t f = i;
-      while (!start[f]) --f;  // at most the leaf's size back (phi, or a pile of duplicates)
-      out.cnt[r] = (int32_t)(work_slot(w, i) - work_slot(w, f) + 1);
+    // inclusive segmented scan (min / max) over lanes with the same leaf
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t ol = __shfl_down_sync(0xFFFFFFFFu, leaf, o);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int32_t a = __shfl_down_sync(0xFFFFFFFFu, lo[d], o);
+        const int32_t b = __shfl_down_sync(0xFFFFFFFFu, hi[d], o);
+        if (lane + o < 32 && ol == leaf) {
+          lo[d] = min(lo[d], a);
+          hi[d] = max(hi[d], b);
+        }
+      }
+    }
+    const int64_t pl_leaf = __shfl_up_sync(0xFFFFFFFFu, leaf, 1);
+    if (pt && (lane == 0 || pl_leaf != leaf)) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        atomicMin(&pl.lo[d][leaf], lo[d]);
+        atomicMax(&pl.hi[d][leaf], hi[d]);
+      }
     }
   }
 }
 
-// Tight box of leaves [0, L) of a leaf list: a warp per leaf.
-template <int D>
-__global__ void k_pleaf_boxes(PLeaves pl, Pool pool, int64_t L) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < L; i += warps) {
-    const uint32_t s0 = pl.ref[i];
-    const int c = pl.cnt[i];
-    int32_t lo[D], hi[D];
-#pragma unroll
+__global__ void k_empty_boxes(PLeaves pl, int64_t L, int D) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < L; r += (int64_t)gridDim.x * blockDim.x)
     for (int d = 0; d < D; ++d) {
-      lo[d] = INT32_MAX;
-      hi[d] = INT32_MIN;
+      pl.lo[d][r] = INT32_MAX;
+      pl.hi[d][r] = INT32_MIN;
     }
-    for (int s = lane; s < c; s += 32)
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const int32_t v = pool.px[d][s0 + s];
-        lo[d] = min(lo[d], v);
-        hi[d] = max(hi[d], v);
-      }
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      lo[d] = __reduce_min_sync(0xFFFFFFFFu, lo[d]);
-      hi[d] = __reduce_max_sync(0xFFFFFFFFu, hi[d]);
-    }
-    if (lane == 0)
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        pl.lo[d][i] = lo[d];
-        pl.hi[d][i] = hi[d];
-      }
-  }
 }
 
 // ---- nodes from the leaf list ---------------------------------------------
@@ -490,6 +506,17 @@ __global__ void k_dirty_marks(const int32_t *sbeg, const int32_t *send, const in
   }
 }
 
+__global__ void k_fill1(int32_t *p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 1;
+}
+
+__global__ void k_all_dirty(int64_t L, int32_t *dirty, int32_t *sstart) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += (int64_t)gridDim.x * blockDim.x) {
+    dirty[x] = 1;
+    sstart[x] = x == 0;
+  }
+}
+
 // dirty[x] from the exclusive scan ex of diff (its inclusive sum is ex[x + 1]);
 // segment starts and ends.
 __global__ void k_dirty_flags(const int64_t *ex, int64_t L, int32_t *dirty, int32_t *sstart) {
@@ -577,7 +604,7 @@ __global__ void k_seg_ctx(const int32_t *xs, const int32_t *xe, const int64_t *E
 
 struct SegArgs {
   PLeaves pl;
-  Pool pool;
+  Pool src, dst;  // the leaves' points; where the new points go
   const int64_t *E;     // old leaves' prefix counts (L + 1)
   const int32_t *dirty, *sstart, *xs, *xe, *ctxl, *ctxr;
   const int64_t *gx;    // exclusive scan of sstart
@@ -590,6 +617,13 @@ struct SegArgs {
   int64_t L, G, n;
   uint32_t fresh;  // first fresh slot: dirty leaf x's new points go to fresh + woff[x] ...
   bool insert;
+  int32_t *big;    // dirty leaves with more than kSeqMax new points (at most 4 kChunk)
+  uint32_t *n_big;
+  int32_t *huge;   // ... with more than 4 kChunk
+  uint32_t *n_huge;
+  const int64_t *K;  // global delete: exclusive scan of keep over all old points
+  const int32_t *bleaf;  // leaf of each sorted batch entry
+  int64_t m;
   uint64_t *wkey;  // work array
   int32_t *wmask;
   uint32_t *wslot;
@@ -614,87 +648,285 @@ __global__ void k_seg_context(SegArgs a) {
       const int64_t p = t < cl ? pa - cl + t : pb + (t - cl);
       const int64_t w = t < cl ? w0 - cl + t : w0 + seglen + (t - cl);
       const int64_t y = leaf_at(a.E, a.L, p);
-      a.wkey[w] = a.pool.pkey[a.pl.ref[y] + (uint32_t)(p - a.E[y])];
+      a.wkey[w] = a.src.pkey[a.pl.ref[y] + (uint32_t)(p - a.E[y])];
       a.wmask[w] = 0;
       a.wslot[w] = 0;
     }
   }
 }
 
-// The new points of every dirty leaf, in (key, id) order, into fresh slots and
-// the work array: insert merges the leaf's points with its slice; delete
-// keeps the unmarked ones.  A warp per dirty leaf.
+constexpr int kSeqMax = 64;    // a dirty leaf with at most this many new points is built by one lane
+constexpr int kChunk = 4096;   // new points per warp task of a large dirty leaf
+
+// Writes new point t of dirty leaf x (segment g) to its fresh slot and to the
+// work array.
 template <int D>
-__global__ void k_seg_points(SegArgs a) {
+__device__ __forceinline__ void seg_put(const SegArgs &a, int64_t x, int64_t g, int64_t t, uint64_t k, uint32_t id,
+                                        const int32_t *c) {
+  const uint32_t dst = a.fresh + (uint32_t)(a.woff[x] + t);
+  const int64_t w = seg_wstart(a, g) + (a.woff[x] - a.woff[a.xs[g]]) + t;
+#pragma unroll
+  for (int d = 0; d < D; ++d) a.dst.px[d][dst] = c[d];
+  a.dst.pid[dst] = id;
+  a.dst.pkey[dst] = k;
+  a.wkey[w] = k;
+  a.wmask[w] = 1;
+  a.wslot[w] = dst;
+}
+
+// Merged order of a leaf point and a batch entry: the leaf point first on
+// equal (key, id).
+__device__ __forceinline__ bool leaf_first(uint64_t lk, uint32_t lid, uint64_t bk, uint32_t bid) {
+  return lk < bk || (lk == bk && lid <= bid);
+}
+
+// The new points of every small dirty leaf, in (key, id) order: one lane per
+// leaf (32 consecutive leaves per warp) merges the leaf's points with its
+// slice (insert) or keeps its unmarked points (delete), one point per step.
+// Larger dirty leaves are listed for k_seg_big.
+template <int D>
+__global__ void k_seg_small(SegArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < a.L; x += warps) {
-    if (!a.dirty[x]) continue;
+  for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < a.L; j0 += warps * 32) {
+    const int64_t x = j0 + lane;
+    if (x >= a.L || !a.dirty[x]) continue;
+    const int64_t nc = a.woff[x + 1] - a.woff[x];
+    if (nc > kSeqMax) {  // listed: whole leaves per warp, or chunks of a huge one over all warps
+      if (nc > 4 * kChunk)
+        a.huge[atomicAdd(a.n_huge, 1u)] = (int32_t)x;
+      else
+        a.big[atomicAdd(a.n_big, 1u)] = (int32_t)x;
+      continue;
+    }
     const int64_t g = a.gx[x] + a.sstart[x] - 1;
-    const int64_t w0 = seg_wstart(a, g) + (a.woff[x] - a.woff[a.xs[g]]);
-    const uint32_t f0 = a.fresh + (uint32_t)a.woff[x];
     const uint32_t s0 = a.pl.ref[x];
     const int cnt = a.pl.cnt[x];
     const int32_t b = a.sbeg[x], len = max(0, a.send[x] - b);
-    auto put = [&](int64_t t, uint64_t k, uint32_t id, const int32_t *c) {
-      const uint32_t dst = f0 + (uint32_t)t;
-#pragma unroll
-      for (int d = 0; d < D; ++d) a.pool.px[d][dst] = c[d];
-      a.pool.pid[dst] = id;
-      a.pool.pkey[dst] = k;
-      a.wkey[w0 + t] = k;
-      a.wmask[w0 + t] = 1;
-      a.wslot[w0 + t] = dst;
-    };
+    int32_t c[D];
     if (a.insert) {
-      const int64_t c = (int64_t)cnt + len;
-      for (int64_t p = lane; p < c; p += 32) {
-        // merge path: how many of the first p merged elements come from the leaf
-        int64_t l = max((int64_t)0, p - len), h = min(p, (int64_t)cnt);
-        while (l < h) {
-          const int64_t mid = (l + h) >> 1;
-          const int64_t bi = b + (p - mid - 1);
-          const uint64_t lk = a.pool.pkey[s0 + mid], sk = a.bkeys[bi];
-          if (lk < sk || (lk == sk && a.pool.pid[s0 + mid] <= a.rid[bi]))
-            l = mid + 1;
-          else
-            h = mid;
-        }
-        const int64_t li = l, si = p - l;
-        bool from_leaf = li < cnt;
-        if (from_leaf && si < len) {
-          const uint64_t lk = a.pool.pkey[s0 + li], sk = a.bkeys[b + si];
-          from_leaf = lk < sk || (lk == sk && a.pool.pid[s0 + li] <= a.rid[b + si]);
-        }
-        int32_t cc[D];
+      int i = 0, j = 0;
+      for (int64_t t = 0; t < nc; ++t) {
+        bool from_leaf = i < cnt;
+        if (from_leaf && j < len)
+          from_leaf = leaf_first(a.src.pkey[s0 + i], a.src.pid[s0 + i], a.bkeys[b + j], a.rid[b + j]);
         if (from_leaf) {
-          const uint32_t src = s0 + (uint32_t)li;
 #pragma unroll
-          for (int d = 0; d < D; ++d) cc[d] = a.pool.px[d][src];
-          put(p, a.pool.pkey[src], a.pool.pid[src], cc);
+          for (int d = 0; d < D; ++d) c[d] = a.src.px[d][s0 + i];
+          seg_put<D>(a, x, g, t, a.src.pkey[s0 + i], a.src.pid[s0 + i], c);
+          ++i;
         } else {
-          const int64_t bi = b + si;
 #pragma unroll
-          for (int d = 0; d < D; ++d) cc[d] = a.rpt[bi * D + d];
-          put(p, a.bkeys[bi], a.rid[bi], cc);
+          for (int d = 0; d < D; ++d) c[d] = a.rpt[(int64_t)(b + j) * D + d];
+          seg_put<D>(a, x, g, t, a.bkeys[b + j], a.rid[b + j], c);
+          ++j;
         }
       }
     } else {
-      int64_t out = 0;
-      for (int s0r = 0; s0r < cnt; s0r += 32) {
-        const int s = s0r + lane;
-        const bool k = s < cnt && (len == 0 || a.keep[a.E[x] + s]);
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, k);
-        if (k) {
-          const uint32_t src = s0 + (uint32_t)s;
-          int32_t cc[D];
+      int64_t t = 0;
+      for (int i = 0; i < cnt; ++i) {
+        if (len > 0 && !a.keep[a.E[x] + i]) continue;
 #pragma unroll
-          for (int d = 0; d < D; ++d) cc[d] = a.pool.px[d][src];
-          put(out + __popc(m & lanemask_lt()), a.pool.pkey[src], a.pool.pid[src], cc);
-        }
-        out += __popc(m);
+        for (int d = 0; d < D; ++d) c[d] = a.src.px[d][s0 + i];
+        seg_put<D>(a, x, g, t++, a.src.pkey[s0 + i], a.src.pid[s0 + i], c);
       }
     }
+  }
+}
+
+// New point p (of nc) of a listed dirty leaf x in segment g.  Insert: found
+// by a merge-path search over the leaf's points and its slice.
+template <int D>
+__device__ __forceinline__ void seg_insert_at(const SegArgs &a, int64_t x, int64_t g, int64_t p) {
+  const uint32_t s0 = a.pl.ref[x];
+  const int cnt = a.pl.cnt[x];
+  const int32_t b = a.sbeg[x], len = max(0, a.send[x] - b);
+  // merge path: how many of the first p merged points come from the leaf
+  int64_t l = max((int64_t)0, p - len), h = min(p, (int64_t)cnt);
+  while (l < h) {
+    const int64_t mid = (l + h) >> 1;
+    const int64_t bj = b + (p - mid - 1);
+    if (leaf_first(a.src.pkey[s0 + mid], a.src.pid[s0 + mid], a.bkeys[bj], a.rid[bj]))
+      l = mid + 1;
+    else
+      h = mid;
+  }
+  const int64_t li = l, si = p - l;
+  bool from_leaf = li < cnt;
+  if (from_leaf && si < len)
+    from_leaf = leaf_first(a.src.pkey[s0 + li], a.src.pid[s0 + li], a.bkeys[b + si], a.rid[b + si]);
+  int32_t c[D];
+  if (from_leaf) {
+    const uint32_t sl = s0 + (uint32_t)li;
+#pragma unroll
+    for (int d = 0; d < D; ++d) c[d] = a.src.px[d][sl];
+    seg_put<D>(a, x, g, p, a.src.pkey[sl], a.src.pid[sl], c);
+  } else {
+    const int64_t bj = b + si;
+#pragma unroll
+    for (int d = 0; d < D; ++d) c[d] = a.rpt[bj * D + d];
+    seg_put<D>(a, x, g, p, a.bkeys[bj], a.rid[bj], c);
+  }
+}
+
+// Delete: a warp keeps the unmarked points of leaf x in order.
+template <int D>
+__device__ __forceinline__ void seg_delete_leaf(const SegArgs &a, int64_t x, int64_t g) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t s0 = a.pl.ref[x];
+  const int cnt = a.pl.cnt[x];
+  const int32_t len = max(0, a.send[x] - a.sbeg[x]);
+  int64_t out = 0;
+  for (int r0 = 0; r0 < cnt; r0 += 32) {
+    const int i = r0 + lane;
+    const bool k = i < cnt && (len == 0 || a.keep[a.E[x] + i]);
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, k);
+    if (k) {
+      const uint32_t sl = s0 + (uint32_t)i;
+      int32_t c[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) c[d] = a.src.px[d][sl];
+      seg_put<D>(a, x, g, out + __popc(m & lanemask_lt()), a.src.pkey[sl], a.src.pid[sl], c);
+    }
+    out += __popc(m);
+  }
+}
+
+// The new points of the listed dirty leaves: a warp per leaf of the big list;
+// the chunks of kChunk new points of each huge leaf spread over all warps.
+template <int D>
+__global__ void k_seg_big(SegArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nb = *a.n_big, nh = *a.n_huge;
+  for (int64_t bi = wid; bi < nb; bi += warps) {
+    const int64_t x = a.big[bi];
+    const int64_t g = a.gx[x] + a.sstart[x] - 1;
+    if (a.insert) {
+      const int64_t nc = a.woff[x + 1] - a.woff[x];
+      for (int64_t p = lane; p < nc; p += 32) seg_insert_at<D>(a, x, g, p);
+    } else {
+      seg_delete_leaf<D>(a, x, g);
+    }
+  }
+  for (int64_t hi = 0; hi < nh; ++hi) {
+    const int64_t x = a.huge[hi];
+    const int64_t g = a.gx[x] + a.sstart[x] - 1;
+    if (a.insert) {
+      const int64_t nc = a.woff[x + 1] - a.woff[x];
+      const int64_t chunks = (nc + kChunk - 1) / kChunk;
+      for (int64_t ch = wid; ch < chunks; ch += warps) {
+        const int64_t pe = min(nc, (ch + 1) * kChunk);
+        for (int64_t p = ch * kChunk + lane; p < pe; p += 32) seg_insert_at<D>(a, x, g, p);
+      }
+    } else if (hi % warps == wid) {
+      seg_delete_leaf<D>(a, x, g);
+    }
+  }
+}
+
+// Last index x in [lo, hi) with v[x] <= t (v non-decreasing, v[lo] <= t).
+__device__ __forceinline__ int64_t last_le(const int64_t *v, int64_t lo, int64_t hi, int64_t t) {
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (v[mid] <= t)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Global insert (every leaf dirty, one segment, no context: the work array is
+// the fresh pool's keys themselves): a thread per old point and per batch entry, each
+// placing itself among the other side of its leaf by a binary search (a
+// leaf's points and its slice are both in (key, id) order; the leaf point
+// comes first on equal (key, id)); writes are nearly in order.  A block's old
+// points lie in a narrow range of leaves, found once per block.
+template <int D>
+__global__ void k_glob_insert(SegArgs a) {
+  __shared__ int64_t xr[2];
+  const int64_t total = a.n + a.m;
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x; q0 < total; q0 += (int64_t)gridDim.x * blockDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0 && q0 < a.n) {
+      xr[0] = last_le(a.E, 0, a.L, q0);
+      xr[1] = last_le(a.E, 0, a.L, min(a.n - 1, q0 + (int64_t)blockDim.x - 1)) + 1;
+    }
+    __syncthreads();
+    const int64_t q = q0 + threadIdx.x;
+    if (q >= total) continue;
+    int64_t x, o;
+    uint64_t k;
+    uint32_t id;
+    int32_t c[D];
+    if (q < a.n) {  // old point q (leaf order)
+      x = last_le(a.E, xr[0], xr[1], q);
+      const int64_t i = q - a.E[x];
+      const uint32_t sl = a.pl.ref[x] + (uint32_t)i;
+      k = a.src.pkey[sl];
+      id = a.src.pid[sl];
+#pragma unroll
+      for (int d = 0; d < D; ++d) c[d] = a.src.px[d][sl];
+      int32_t lo = a.sbeg[x], hi = max(lo, a.send[x]);  // slice entries before it: (key, id) strictly less
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (!leaf_first(k, id, a.bkeys[mid], a.rid[mid]))
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      o = a.woff[x] + i + (lo - a.sbeg[x]);
+    } else {  // batch entry j (sorted order)
+      const int64_t j = q - a.n;
+      x = a.bleaf[j];
+      k = a.bkeys[j];
+      id = a.rid[j];
+#pragma unroll
+      for (int d = 0; d < D; ++d) c[d] = a.rpt[j * D + d];
+      const uint32_t s0 = a.pl.ref[x];
+      int lo = 0, hi = a.pl.cnt[x];  // leaf points before it: those that come first
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (leaf_first(a.src.pkey[s0 + mid], a.src.pid[s0 + mid], k, id))
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      o = a.woff[x] + (j - a.sbeg[x]) + lo;
+    }
+    a.dst.pkey[o] = k;
+    a.dst.pid[o] = id;
+#pragma unroll
+    for (int d = 0; d < D; ++d) a.dst.px[d][o] = c[d];
+  }
+}
+
+// Global delete: a thread per old point (leaf found as above); a kept point
+// goes to its rank among the kept ones (the fresh pool is the work array).
+template <int D>
+__global__ void k_glob_delete(SegArgs a) {
+  __shared__ int64_t xr[2];
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < a.n; p0 += (int64_t)gridDim.x * blockDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      xr[0] = last_le(a.E, 0, a.L, p0);
+      xr[1] = last_le(a.E, 0, a.L, min(a.n - 1, p0 + (int64_t)blockDim.x - 1)) + 1;
+    }
+    __syncthreads();
+    const int64_t p = p0 + threadIdx.x;
+    if (p >= a.n || !a.keep[p]) continue;
+    const int64_t x = last_le(a.E, xr[0], xr[1], p);
+    const uint32_t sl = a.pl.ref[x] + (uint32_t)(p - a.E[x]);
+    int32_t c[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) c[d] = a.src.px[d][sl];
+    const int64_t o = a.K[p];
+    a.dst.pid[o] = a.src.pid[sl];
+    a.dst.pkey[o] = a.src.pkey[sl];
+#pragma unroll
+    for (int d = 0; d < D; ++d) a.dst.px[d][o] = c[d];
   }
 }
 
@@ -760,23 +992,25 @@ __global__ void k_pl_assemble(PLeaves old, const int32_t *dirty, const int64_t *
 }
 
 // Compaction of the pool: every leaf's points to consecutive slots in leaf
-// order (a warp per leaf); the leaf records take their new first slots.
+// order (an 8-lane group per leaf, four leaves per warp); the leaf records
+// take their new first slots.
 template <int D>
 __global__ void k_pl_compact(PLeaves pl, const int64_t *E, int64_t L, Pool from, Pool to) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < L; x += warps) {
+  for (int64_t x0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; x0 < L; x0 += warps * 4) {
+    const int64_t x = x0 + g;
+    if (x >= L) continue;
     const uint32_t s0 = pl.ref[x];
     const int c = pl.cnt[x];
     const int64_t o = E[x];
-    for (int s = lane; s < c; s += 32) {
+    for (int s = gl; s < c; s += 8) {
 #pragma unroll
       for (int d = 0; d < D; ++d) to.px[d][o + s] = from.px[d][s0 + s];
       to.pid[o + s] = from.pid[s0 + s];
       to.pkey[o + s] = from.pkey[s0 + s];
     }
-    __syncwarp();
-    if (lane == 0) pl.ref[x] = (uint32_t)o;
+    if (gl == 0) pl.ref[x] = (uint32_t)o;
   }
 }
 
@@ -858,8 +1092,8 @@ static psi_status porth_nodes(psi_index *ix, cudaStream_t s) {
 // Leaves of a work array into a new leaf list `out` (allocated here) with
 // their boxes; *nl receives the leaf count.  rank_out (optional) keeps the
 // exclusive scan of the leaf starts.
-static psi_status work_leaves(psi_index *ix, const WorkArray &w, PLeaves &out, int64_t *nl, Buf<int64_t> *rank_out,
-                              cudaStream_t s) {
+static psi_status work_leaves(psi_index *ix, const WorkArray &w, uint32_t end_slot, PLeaves &out, int64_t *nl,
+                              Buf<int64_t> *rank_out, cudaStream_t s) {
   const int D = ix->D, bits = ix->cfg.coord_bits, K = ix->key_bits;
   psi_status st;
   Buf<int32_t> ldepth, start;
@@ -877,10 +1111,12 @@ static psi_status work_leaves(psi_index *ix, const WorkArray &w, PLeaves &out, i
   if ((st = alloc_pleaves(out, D, L, s))) return st;
   PSI_LAUNCH(k_work_leaves, grid_for(w.n), 256, 0, s, w, ldepth.p, start.p, rank.p, D, bits, out);
   if (L > 0) {
+    PSI_LAUNCH(k_leaf_counts, grid_for(L), 256, 0, s, out, L, end_slot);
+    PSI_LAUNCH(k_empty_boxes, grid_for(L), 256, 0, s, out, L, D);
     if (D == 2)
-      PSI_LAUNCH_NAMED("k_pleaf_boxes", k_pleaf_boxes<2>, warp_grid(L), 256, 0, s, out, ix->pool, L);
+      PSI_LAUNCH_NAMED("k_work_boxes", k_work_boxes<2>, grid_for(w.n), 256, 0, s, w, start.p, rank.p, ix->pool, out);
     else
-      PSI_LAUNCH_NAMED("k_pleaf_boxes", k_pleaf_boxes<3>, warp_grid(L), 256, 0, s, out, ix->pool, L);
+      PSI_LAUNCH_NAMED("k_work_boxes", k_work_boxes<3>, grid_for(w.n), 256, 0, s, w, start.p, rank.p, ix->pool, out);
   }
   *nl = L;
   return PSI_OK;
@@ -955,7 +1191,7 @@ psi_status porth_build(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
                      ix->pool);
   WorkArray w{ix->pool.pkey, nullptr, nullptr, 0u, n};
   int64_t L = 0;
-  if ((st = work_leaves(ix, w, ix->pl, &L, nullptr, s))) return st;
+  if ((st = work_leaves(ix, w, (uint32_t)n, ix->pl, &L, nullptr, s))) return st;
   ix->L = L;
   return porth_nodes(ix, s);
 }
@@ -984,6 +1220,9 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
       (st = tot.alloc(4, s)) || (st = del.alloc(1, s)))
     return st;
   PSI_CK(cudaMemsetAsync(tot.p, 0, sizeof(int64_t) * 4, s));
+  // A batch of more than 1/16 of the points reaches nearly every leaf: it is
+  // merged with all of them into a fresh pool (one segment, no garbage).
+  const bool global = m * 16 > n;
   if (D == 2)
     PSI_LAUNCH_NAMED("k_prec", k_prec<2>, grid_for(m), 256, 0, s, br.vals, pts, ids, m, rid.p, rpt.p);
   else
@@ -996,12 +1235,17 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
   if ((st = scan_i32_to_i64(ix->pl.cnt, E.p, L, E.p + L, s))) return st;
   PSI_LAUNCH(k_route, grid_for(m), 256, 0, s, br.keys, m, ix->pl.key, L, bleaf.p);
   PSI_LAUNCH(k_pslices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p);
-  PSI_LAUNCH(k_dirty_marks, grid_for(L), 256, 0, s, sbeg.p, send.p, E.p, L, n, phi, diff.p);
-  // dex = exclusive scan of diff over L + 1 entries (dex[x + 1] = inclusive sum at x)
-  if ((st = scan_i32_to_i64(diff.p, dex.p, L + 1, dex.p + L + 1, s))) return st;
-  PSI_LAUNCH(k_dirty_flags, grid_for(L), 256, 0, s, dex.p, L, dirty.p, sstart.p);
+  if (global) {
+    PSI_LAUNCH(k_all_dirty, grid_for(L), 256, 0, s, L, dirty.p, sstart.p);
+  } else {
+    PSI_LAUNCH(k_dirty_marks, grid_for(L), 256, 0, s, sbeg.p, send.p, E.p, L, n, phi, diff.p);
+    // dex = exclusive scan of diff over L + 1 entries (dex[x + 1] = inclusive sum at x)
+    if ((st = scan_i32_to_i64(diff.p, dex.p, L + 1, dex.p + L + 1, s))) return st;
+    PSI_LAUNCH(k_dirty_flags, grid_for(L), 256, 0, s, dex.p, L, dirty.p, sstart.p);
+  }
   if (!insert) {
     if ((st = keep.alloc(n, s))) return st;
+    if (global) PSI_LAUNCH(k_fill1, grid_for(n), 256, 0, s, keep.p, n);  // every old point of a dirty leaf is read
     if (D == 2)
       PSI_LAUNCH_NAMED("k_pdel_marks", k_pdel_marks<2>, warp_grid(L), 256, 0, s, ix->pl, ix->pool, E.p, sbeg.p,
                        send.p, L, br.keys, rid.p, rpt.p, keep.p, rem.p, del.p);
@@ -1037,17 +1281,42 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
   PSI_CK(cudaMemcpyAsync(&hc, cxoff.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   PSI_CK(cudaStreamSynchronize(s));
   const int64_t W = S + hc;
-  const uint32_t fresh = (uint32_t)ix->pool_used;
-  if ((st = porth_grow(ix, ix->pool_used + S, s))) return st;
+  // new points: appended to the pool, or (global) into a fresh pool
+  Pool npool;
+  if (global) {
+    if ((st = alloc_pool(npool, D, std::max<int64_t>(S + S / 4, 1024), s))) {
+      free_pool(npool, s);
+      return st;
+    }
+  } else if ((st = porth_grow(ix, ix->pool_used + S, s))) {
+    return st;
+  }
+  const uint32_t fresh = global ? 0u : (uint32_t)ix->pool_used;
+  Buf<int32_t> big, huge;
+  Buf<uint32_t> n_big;
+  Buf<int64_t> K;
+  if ((st = big.alloc(L, s)) || (st = huge.alloc(L, s)) || (st = n_big.alloc(2, s)) ||
+      (global && !insert && (st = K.alloc(n + 1, s)))) {
+    free_pool(npool, s);
+    return st;
+  }
+  PSI_CK(cudaMemsetAsync(n_big.p, 0, 2 * sizeof(uint32_t), s));
+  if (global && !insert && (st = scan_i32_to_i64(keep.p, K.p, n, K.p + n, s))) {
+    free_pool(npool, s);
+    return st;
+  }
   Buf<uint64_t> wkey;
   Buf<int32_t> wmask;
   Buf<uint32_t> wslot;
-  if ((st = wkey.alloc(std::max<int64_t>(W, 1), s)) || (st = wmask.alloc(std::max<int64_t>(W, 1), s)) ||
-      (st = wslot.alloc(std::max<int64_t>(W, 1), s)))
+  const int64_t Wb = global ? 1 : std::max<int64_t>(W, 1);  // global: the fresh pool is the work array
+  if ((st = wkey.alloc(Wb, s)) || (st = wmask.alloc(Wb, s)) || (st = wslot.alloc(Wb, s))) {
+    free_pool(npool, s);
     return st;
+  }
   SegArgs a;
   a.pl = ix->pl;
-  a.pool = ix->pool;
+  a.src = ix->pool;
+  a.dst = global ? npool : ix->pool;
   a.E = E.p;
   a.dirty = dirty.p;
   a.sstart = sstart.p;
@@ -1072,19 +1341,45 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
   a.wkey = wkey.p;
   a.wmask = wmask.p;
   a.wslot = wslot.p;
-  PSI_LAUNCH(k_seg_context, warp_grid(G), 256, 0, s, a);
-  if (D == 2)
-    PSI_LAUNCH_NAMED("k_seg_points", k_seg_points<2>, warp_grid(L), 256, 0, s, a);
-  else
-    PSI_LAUNCH_NAMED("k_seg_points", k_seg_points<3>, warp_grid(L), 256, 0, s, a);
-  ix->pool_used += S;
+  a.big = big.p;
+  a.n_big = n_big.p;
+  a.huge = huge.p;
+  a.n_huge = n_big.p + 1;
+  a.K = K.p;
+  a.bleaf = bleaf.p;
+  a.m = m;
+  if (hc > 0) PSI_LAUNCH(k_seg_context, warp_grid(G), 256, 0, s, a);
+  if (global && insert) {
+    if (D == 2)
+      PSI_LAUNCH_NAMED("k_glob_insert", k_glob_insert<2>, grid_for(n + m), 256, 0, s, a);
+    else
+      PSI_LAUNCH_NAMED("k_glob_insert", k_glob_insert<3>, grid_for(n + m), 256, 0, s, a);
+  } else if (global) {
+    if (D == 2)
+      PSI_LAUNCH_NAMED("k_glob_delete", k_glob_delete<2>, grid_for(n), 256, 0, s, a);
+    else
+      PSI_LAUNCH_NAMED("k_glob_delete", k_glob_delete<3>, grid_for(n), 256, 0, s, a);
+  } else if (D == 2) {
+    PSI_LAUNCH_NAMED("k_seg_small", k_seg_small<2>, warp_grid(ceil_div(L, 32)), 256, 0, s, a);
+    PSI_LAUNCH_NAMED("k_seg_big", k_seg_big<2>, num_sms() * 8, 256, 0, s, a);
+  } else {
+    PSI_LAUNCH_NAMED("k_seg_small", k_seg_small<3>, warp_grid(ceil_div(L, 32)), 256, 0, s, a);
+    PSI_LAUNCH_NAMED("k_seg_big", k_seg_big<3>, num_sms() * 8, 256, 0, s, a);
+  }
+  if (global) {
+    free_pool(ix->pool, s);
+    ix->pool = npool;
+    ix->pool_used = S;
+  } else {
+    ix->pool_used += S;
+  }
   // the segments' new leaves
   PLeaves nl;
   int64_t NL = 0;
   Buf<int64_t> rank, fl;
-  WorkArray w{wkey.p, wmask.p, wslot.p, 0u, W};
+  WorkArray w = global ? WorkArray{ix->pool.pkey, nullptr, nullptr, 0u, W} : WorkArray{wkey.p, wmask.p, wslot.p, 0u, W};
   if (W > 0) {
-    if ((st = work_leaves(ix, w, nl, &NL, &rank, s))) {
+    if ((st = work_leaves(ix, w, fresh + (uint32_t)S, nl, &NL, &rank, s))) {
       free_pleaves(nl, s);
       return st;
     }
