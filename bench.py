@@ -538,10 +538,10 @@ def run_batched(nidx: int, steps: int, warmup: int, rank: int = 0, max_size: int
     # autotune on a sample of the indexes
     ns = min(nidx, tune_sample)
     t_off, t_qoff = off[: ns + 1], qoff[: ns + 1]
-    phi, threads, tinfo = tune.autotune(t_off, dp[: t_off[-1]], di[: t_off[-1]], dq[: t_qoff[-1]],
-                                        dqo[: ns + 1], int(t_qoff[-1]), k, dim=2, kind="spac_h",
-                                        dist="half-uniform-half-varden", sizes=sizes[:ns])
-    b = psi.Batch(off, kind="spac_h", leaf_size=phi, threads=threads)
+    phi, threads, rbits, tinfo = tune.autotune(t_off, dp[: t_off[-1]], di[: t_off[-1]], dq[: t_qoff[-1]],
+                                               dqo[: ns + 1], int(t_qoff[-1]), k, dim=2, kind="spac_h",
+                                               dist="half-uniform-half-varden", sizes=sizes[:ns])
+    b = psi.Batch(off, kind="spac_h", leaf_size=phi, threads=threads, radix_bits=rbits)
     b.reserve(nq)
     oi = torch.empty((nq, k), dtype=torch.int32, device=dev)
     od = torch.empty((nq, k), dtype=torch.int64, device=dev)
@@ -596,7 +596,8 @@ def run_batched(nidx: int, steps: int, warmup: int, rank: int = 0, max_size: int
     npts = int(off[-1])
     return {"indexes": nidx, "points": npts, "queries": nq, "k": k,
             "sizes": "log-uniform [1e3, %.0e]" % max_size, "query_counts": "log-uniform [1e2, 1e5]",
-            "tuned": {"leaf_size": phi, "threads": threads, "tune_sample_indexes": ns},
+            "tuned": {"leaf_size": phi, "threads": threads, "radix_bits": rbits, "tune_sample_indexes": ns,
+                      "trials_ms": tinfo.get("trials_ms")},
             "batched_ms": round(batched_ms, 3), "batched_build_ms": round(build_ms, 3),
             "batched_value": round((npts / 1e6) / (batched_ms * 1e-3), 1),
             "plain_ms": round(plain_ms, 3), "plain_value": round((npts / 1e6) / (plain_ms * 1e-3), 1),

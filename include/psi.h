@@ -144,7 +144,9 @@ typedef struct psi_batch psi_batch;
  * point array: index i owns points [h_offsets[i], h_offsets[i+1]) (host array
  * of nidx+1 entries, h_offsets[0] = 0).  All indexes share cfg (SPAC_Z or
  * SPAC_H).  `threads` is the thread-block size of the build (256, 512, 1024; 0
- * = 512).  Allocates everything the build needs, so psi_batch_build and
+ * = 512); cfg->radix_bits is the digit width of the build's block sort (0 or 8:
+ * 8-bit digits; 11: 11-bit digits, with 256 or 512 threads only).  The index
+ * layout does not depend on either.  Allocates everything the build needs, so psi_batch_build and
  * psi_batch_knn allocate nothing and can be captured in a CUDA graph.
  * Synchronises `stream`. */
 psi_status psi_batch_create(const psi_config *cfg, const int64_t *h_offsets, int32_t nidx, int32_t threads,

@@ -17,6 +17,7 @@
 // so the launch allocates nothing and can be captured in a CUDA graph.
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "bitonic.cuh"
@@ -26,6 +27,7 @@
 struct psi_batch {
   psi_config cfg;
   int D = 2, phi = 32, C = 64, F = 32, curve = 0, key_bits = 60, threads = 512;
+  int rb = 8;  // digit width of the block sort
   int nidx = 0;
   int64_t total = 0;
   std::vector<int64_t> off, leaves, node_off, block_off, nodes_per;
@@ -55,7 +57,17 @@ int64_t summary_capacity(int64_t L, int F);
 
 namespace {
 
-constexpr int RB = 8, RADIX = 256, MAXP = 8, IPT = 8;
+constexpr int IPT = 8;  // keys per thread of a chunk
+
+// Digit width of the block sort: 8 or 11 bits (a tuner dimension).
+template <int RB>
+struct BRadix {
+  static constexpr int RADIX = 1 << RB;
+  static constexpr int MAXP = (64 + RB - 1) / RB;  // passes of a 64-bit key
+  // per-warp counters of a chunk (a warp ranks IPT * 32 keys) and staged digits
+  using Count = typename std::conditional<RB == 8, uint32_t, uint16_t>::type;
+  using Digit = typename std::conditional<RB == 8, uint8_t, uint16_t>::type;
+};
 
 struct BuildArgs {
   const int32_t *pts;
@@ -74,16 +86,19 @@ struct BuildArgs {
   int *status;
 };
 
-template <int BT>
+template <int BT, int RB>
 struct BuildSmem {
+  using R = BRadix<RB>;
   static constexpr int W = BT / 32;
   static constexpr int CH = BT * IPT;
-  uint32_t hist[MAXP][RADIX];  // digit counts, then exclusive bases
-  uint32_t run[RADIX];         // running offset of each digit in the current pass
-  uint32_t wcnt[W][RADIX];     // per-warp counts of the current chunk
-  uint32_t coff[RADIX];        // chunk-exclusive digit offsets
-  uint64_t stage[CH];          // chunk keys (then values) in digit order
-  uint8_t dig[CH];             // digit of each staged position
+  static constexpr int RADIX = R::RADIX;
+  static constexpr int DPT = (RADIX + BT - 1) / BT;  // digits per thread in the per-digit steps
+  uint32_t hist[R::MAXP][RADIX];      // digit counts, then exclusive bases
+  uint32_t run[RADIX];                // running offset of each digit in the current pass
+  typename R::Count wcnt[W][RADIX];   // per-warp counts of the current chunk
+  uint32_t coff[RADIX];               // chunk-exclusive digit offsets
+  uint64_t stage[CH];                 // chunk keys (then values) in digit order
+  typename R::Digit dig[CH];          // digit of each staged position
   uint32_t wsum[32];
   alignas(16) uint8_t htab[kCurveTabBytes];
   int job;
@@ -91,29 +106,42 @@ struct BuildSmem {
   int64_t long_start[64];
 };
 
-// Block-wide exclusive scan of RADIX counters held one per thread (thread t < RADIX).
-template <int BT>
-__device__ __forceinline__ uint32_t block_excl_scan_digits(uint32_t v, uint32_t *wsum) {
+// Block-wide exclusive scan of digit counters: thread t holds the counts v of
+// digits [t * DPT, (t + 1) * DPT) (zero past the last digit) and receives
+// their exclusive prefixes in e.
+template <int BT, int DPT>
+__device__ __forceinline__ void block_excl_scan_digits(const uint32_t (&v)[DPT], uint32_t (&e)[DPT],
+                                                       uint32_t *wsum) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  uint32_t x = v;
+  uint32_t tot = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) tot += v[q];
+  uint32_t x = tot;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
     if (lane >= o) x += y;
   }
-  if (t < RADIX && lane == 31) wsum[w] = x;
+  if (lane == 31) wsum[w] = x;
   __syncthreads();
-  uint32_t before = 0;
-  for (int i = 0; i < w && i < RADIX / 32; ++i) before += wsum[i];
+  uint32_t run = x - tot;
+  for (int i = 0; i < w; ++i) run += wsum[i];
   __syncthreads();
-  return before + x - v;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    e[q] = run;
+    run += v[q];
+  }
 }
 
-template <int D, int CURVE, int BT>
+template <int D, int CURVE, int BT, int RB>
 __global__ __launch_bounds__(BT) void k_batch_build(BuildArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BuildSmem<BT> &sm = *reinterpret_cast<BuildSmem<BT> *>(smem_raw);
-  constexpr int W = BuildSmem<BT>::W, CH = BuildSmem<BT>::CH;
+  using SM = BuildSmem<BT, RB>;
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  constexpr int W = SM::W, CH = SM::CH, RADIX = SM::RADIX, DPT = SM::DPT, MAXP = BRadix<RB>::MAXP;
+  using Count = typename BRadix<RB>::Count;
+  using Digit = typename BRadix<RB>::Digit;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   curve_table_init<D, CURVE>(sm.htab);
   for (;;) {
@@ -151,9 +179,18 @@ __global__ __launch_bounds__(BT) void k_batch_build(BuildArgs a) {
     if (bad_any) atomicOr(a.status, ST_RANGE);
     __syncthreads();
     for (int p = 0; p < a.passes; ++p) {
-      const uint32_t v = tid < RADIX ? sm.hist[p][tid] : 0u;
-      const uint32_t e = block_excl_scan_digits<BT>(v, sm.wsum);
-      if (tid < RADIX) sm.hist[p][tid] = e;
+      uint32_t v[DPT], e[DPT];
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        v[q] = d < RADIX ? sm.hist[p][d] : 0u;
+      }
+      block_excl_scan_digits<BT, DPT>(v, e, sm.wsum);
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        if (d < RADIX) sm.hist[p][d] = e[q];
+      }
     }
     __syncthreads();
     // P: digit passes, A -> B -> A ...
@@ -163,7 +200,7 @@ __global__ __launch_bounds__(BT) void k_batch_build(BuildArgs a) {
       uint64_t *ko = (p & 1) ? a.kA : a.kB;
       uint32_t *vo = (p & 1) ? a.vA : a.vB;
       const int shift = p * RB;
-      if (tid < RADIX) sm.run[tid] = sm.hist[p][tid];
+      for (int d = tid; d < RADIX; d += BT) sm.run[d] = sm.hist[p][d];
       for (int64_t c0 = 0; c0 < n; c0 += CH) {
         const int cn = (int)min((int64_t)CH, n - c0);
         for (int i = tid; i < W * RADIX; i += BT) (&sm.wcnt[0][0])[i] = 0;
@@ -182,25 +219,32 @@ __global__ __launch_bounds__(BT) void k_batch_build(BuildArgs a) {
           const uint32_t dg = valid ? (uint32_t)(key[j] >> shift) & (RADIX - 1) : 0xFFFFFFFFu;
           const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
           const uint32_t before = __popc(peers & lanemask_lt());
-          const uint32_t wb = valid ? sm.wcnt[w][dg] : 0u;
+          const uint32_t wb = valid ? (uint32_t)sm.wcnt[w][dg] : 0u;
           __syncwarp();
-          if (valid && before == 0) sm.wcnt[w][dg] = wb + __popc(peers);
+          if (valid && before == 0) sm.wcnt[w][dg] = (Count)(wb + __popc(peers));
           __syncwarp();
           rank[j] = wb + before;
         }
         __syncthreads();
-        uint32_t ccount = 0;
-        if (tid < RADIX) {
+        uint32_t ccount[DPT], cx[DPT];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+          const int d = tid * DPT + q;
           uint32_t r = 0;
-          for (int ww = 0; ww < W; ++ww) {
-            const uint32_t c = sm.wcnt[ww][tid];
-            sm.wcnt[ww][tid] = r;
-            r += c;
-          }
-          ccount = r;
+          if (d < RADIX)
+            for (int ww = 0; ww < W; ++ww) {
+              const uint32_t c = sm.wcnt[ww][d];
+              sm.wcnt[ww][d] = (Count)r;
+              r += c;
+            }
+          ccount[q] = r;
         }
-        const uint32_t cx = block_excl_scan_digits<BT>(ccount, sm.wsum);
-        if (tid < RADIX) sm.coff[tid] = cx;
+        block_excl_scan_digits<BT, DPT>(ccount, cx, sm.wsum);
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+          const int d = tid * DPT + q;
+          if (d < RADIX) sm.coff[d] = cx[q];
+        }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
@@ -216,7 +260,7 @@ __global__ __launch_bounds__(BT) void k_batch_build(BuildArgs a) {
         for (int pp = tid; pp < cn; pp += BT) {
           const uint64_t k = sm.stage[pp];
           const uint32_t dg = (uint32_t)(k >> shift) & (RADIX - 1);
-          sm.dig[pp] = (uint8_t)dg;
+          sm.dig[pp] = (Digit)dg;
           ko[base + sm.run[dg] + (pp - sm.coff[dg])] = k;
         }
         __syncthreads();
@@ -232,7 +276,11 @@ __global__ __launch_bounds__(BT) void k_batch_build(BuildArgs a) {
           vo[base + sm.run[dg] + (pp - sm.coff[dg])] = sv[pp];
         }
         __syncthreads();
-        if (tid < RADIX) sm.run[tid] += ccount;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+          const int d = tid * DPT + q;
+          if (d < RADIX) sm.run[d] += ccount[q];
+        }
         __syncthreads();
       }
     }
@@ -422,10 +470,10 @@ __global__ void k_query_keys(const int32_t *q, const int32_t *qseg, int64_t nq, 
   }
 }
 
-template <int D, int CURVE, int BT>
+template <int D, int CURVE, int BT, int RB>
 psi_status launch_build(psi_batch *b, const BuildArgs &a, cudaStream_t s) {
-  const size_t smem = sizeof(BuildSmem<BT>);
-  auto kern = k_batch_build<D, CURVE, BT>;
+  const size_t smem = sizeof(BuildSmem<BT, RB>);
+  auto kern = k_batch_build<D, CURVE, BT, RB>;
   PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   PSI_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem));
@@ -472,6 +520,14 @@ psi_status psi_batch_create(const psi_config *cfg, const int64_t *h_offsets, int
     set_error("threads must be 0 (512), 256, 512 or 1024");
     return PSI_ERR_INVALID;
   }
+  if (cfg->radix_bits != 0 && cfg->radix_bits != 8 && cfg->radix_bits != 11) {
+    set_error("batched indexes sort with 8- or 11-bit digits (radix_bits 0, 8 or 11)");
+    return PSI_ERR_INVALID;
+  }
+  if (cfg->radix_bits == 11 && threads == 1024) {
+    set_error("11-bit digits need 256 or 512 threads (the block's shared memory)");
+    return PSI_ERR_INVALID;
+  }
   for (int i = 0; i < nidx; ++i)
     if (h_offsets[i + 1] < h_offsets[i] || h_offsets[0] != 0) {
       set_error("offsets must start at 0 and be non-decreasing");
@@ -491,6 +547,7 @@ psi_status psi_batch_create(const psi_config *cfg, const int64_t *h_offsets, int
   b->curve = cfg->kind == PSI_SPAC_H ? CURVE_HILBERT : CURVE_MORTON;
   b->key_bits = cfg->dim * cfg->coord_bits;
   b->threads = threads ? threads : 512;
+  b->rb = cfg->radix_bits == 11 ? 11 : 8;
   b->nidx = nidx;
   b->last_stream = s;
   b->off.assign(h_offsets, h_offsets + nidx + 1);
@@ -588,13 +645,17 @@ psi_status psi_batch_build(psi_batch *b, const int32_t *d_pts, const uint32_t *d
   a.phi = b->phi;
   a.C = b->C;
   a.F = b->F;
-  a.passes = (b->key_bits + RB - 1) / RB;
+  a.passes = (b->key_bits + b->rb - 1) / b->rb;
   a.status = b->d_status;
 #define BUILD_CASE(DD, CC)                                                        \
   do {                                                                            \
-    if (b->threads == 256) return launch_build<DD, CC, 256>(b, a, s);             \
-    if (b->threads == 1024) return launch_build<DD, CC, 1024>(b, a, s);           \
-    return launch_build<DD, CC, 512>(b, a, s);                                    \
+    if (b->rb == 11) {                                                            \
+      if (b->threads == 256) return launch_build<DD, CC, 256, 11>(b, a, s);       \
+      return launch_build<DD, CC, 512, 11>(b, a, s);                              \
+    }                                                                             \
+    if (b->threads == 256) return launch_build<DD, CC, 256, 8>(b, a, s);          \
+    if (b->threads == 1024) return launch_build<DD, CC, 1024, 8>(b, a, s);        \
+    return launch_build<DD, CC, 512, 8>(b, a, s);                                 \
   } while (0)
   if (b->D == 3 && b->curve == CURVE_HILBERT) BUILD_CASE(3, 1);
   if (b->D == 3) BUILD_CASE(3, 0);

@@ -283,13 +283,14 @@ class Batch:
     one persistent launch (psi_batch_*)."""
 
     def __init__(self, offsets, *, dim: int = 2, kind: int | str = SPAC_H, leaf_size: int = 32,
-                 coord_bits: int | None = None, fanout: int = 32, threads: int = 0, stream=None):
+                 coord_bits: int | None = None, fanout: int = 32, threads: int = 0, radix_bits: int = 0,
+                 stream=None):
         import numpy as np
         if isinstance(kind, str):
             kind = KINDS[kind]
         coord_bits = coord_bits or (30 if dim == 2 else 21)
         self.dim, self.nidx = dim, len(offsets) - 1
-        self.cfg = Config(dim, kind, leaf_size, coord_bits, fanout, 0)
+        self.cfg = Config(dim, kind, leaf_size, coord_bits, fanout, radix_bits)
         self._off = np.ascontiguousarray(offsets, dtype=np.int64)
         h = ctypes.c_void_p()
         _check(lib().psi_batch_create(ctypes.byref(self.cfg), self._off.ctypes.data_as(ctypes.c_void_p), self.nidx,

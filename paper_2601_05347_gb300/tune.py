@@ -1,10 +1,11 @@
 """Autotuner of the batched many-index form.
 
-Chooses the leaf size (16, 32, 64) and the thread-block size of the persistent
-build (256, 512, 1024) by timing build + k-NN on a sample of the batch with
-CUDA events, and caches the choice in a JSON file keyed by (kind, dim, size
-bucket, distribution).  Results do not depend on the choice: k-NN answers are
-defined by the point set alone.
+Chooses the leaf size (16, 32, 64), the thread-block size of the persistent
+build (256, 512, 1024) and the digit width of its block sort (8 or 11 bits;
+11-bit digits with 256 or 512 threads only) by timing build + k-NN on a sample
+of the batch with CUDA events, and caches the choice in a JSON file keyed by
+(kind, dim, size bucket, distribution).  Results do not depend on the choice:
+k-NN answers are defined by the point set alone.
 """
 from __future__ import annotations
 
@@ -20,6 +21,7 @@ from . import psi
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
 LEAF_SIZES = (16, 32, 64)
 THREADS = (256, 512, 1024)
+RADIX_BITS = (8, 11)
 
 
 def cache_key(kind: str, dim: int, sizes: np.ndarray, dist: str) -> str:
@@ -43,9 +45,10 @@ def _save(d: dict):
     os.replace(tmp, CACHE)
 
 
-def time_config(off, dpts, dids, dq, dqoff, nq, k, *, dim, kind, leaf_size, threads, reps=3) -> float:
+def time_config(off, dpts, dids, dq, dqoff, nq, k, *, dim, kind, leaf_size, threads, radix_bits=8,
+                reps=3) -> float:
     """Milliseconds of one batched build + k-NN pass (mean of reps after one warm-up)."""
-    b = psi.Batch(off, dim=dim, kind=kind, leaf_size=leaf_size, threads=threads)
+    b = psi.Batch(off, dim=dim, kind=kind, leaf_size=leaf_size, threads=threads, radix_bits=radix_bits)
     b.reserve(nq)
     out_i = torch.empty((nq, k), dtype=torch.int32, device=dpts.device)
     out_d = torch.empty((nq, k), dtype=torch.int64, device=dpts.device)
@@ -64,18 +67,21 @@ def time_config(off, dpts, dids, dq, dqoff, nq, k, *, dim, kind, leaf_size, thre
 
 
 def autotune(off, dpts, dids, dq, dqoff, nq, k, *, dim: int, kind: str, dist: str, sizes, refresh=False):
-    """Best (leaf_size, threads) for this batch shape, from the cache or by timing."""
+    """Best (leaf_size, threads, radix_bits) for this batch shape, from the cache or by timing."""
     key = cache_key(kind, dim, np.asarray(sizes), dist)
     cache = _load()
-    if key in cache and not refresh:
-        return cache[key]["leaf_size"], cache[key]["threads"], cache[key]
+    if key in cache and not refresh and "radix_bits" in cache[key]:
+        return cache[key]["leaf_size"], cache[key]["threads"], cache[key]["radix_bits"], cache[key]
     trials = {}
     for phi in LEAF_SIZES:
         for th in THREADS:
-            trials[f"{phi}/{th}"] = time_config(off, dpts, dids, dq, dqoff, nq, k, dim=dim, kind=kind,
-                                                leaf_size=phi, threads=th)
+            for rb in RADIX_BITS:
+                if rb == 11 and th == 1024:
+                    continue  # 11-bit digits do not fit a 1024-thread block's shared memory
+                trials[f"{phi}/{th}/{rb}"] = time_config(off, dpts, dids, dq, dqoff, nq, k, dim=dim, kind=kind,
+                                                         leaf_size=phi, threads=th, radix_bits=rb)
     best = min(trials, key=trials.get)
-    phi, th = (int(x) for x in best.split("/"))
-    cache[key] = {"leaf_size": phi, "threads": th, "ms": trials[best], "trials_ms": trials}
+    phi, th, rb = (int(x) for x in best.split("/"))
+    cache[key] = {"leaf_size": phi, "threads": th, "radix_bits": rb, "ms": trials[best], "trials_ms": trials}
     _save(cache)
-    return phi, th, cache[key]
+    return phi, th, rb, cache[key]

@@ -92,3 +92,12 @@ def test_withheld_tile_hook_rejects_bad_arguments():
     assert f(None, None, -1, 0, 16, None) == 1          # n < 0
     assert f(None, None, 10, 0, 16, None) == 1          # null arrays
     assert f(None, None, 0, 0, 16, None) == 0           # nothing to sort
+
+
+def test_batch_create_rejects_unsupported_digit_widths(L):
+    off = (ctypes.c_int64 * 3)(0, 10, 20)
+    h = ctypes.c_void_p()
+    assert L.psi_batch_create(ctypes.byref(cfg(kind=psi.SPAC_H, radix=10)), off, 2, 0, None, ctypes.byref(h)) == INVALID
+    assert b"radix_bits" in L.psi_last_error()
+    assert L.psi_batch_create(ctypes.byref(cfg(kind=psi.SPAC_H, radix=11)), off, 2, 1024, None, ctypes.byref(h)) == INVALID
+    assert b"11-bit" in L.psi_last_error()

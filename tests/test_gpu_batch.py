@@ -51,12 +51,12 @@ SIZES = [0, 1, 31, 32, 33, 1000, 4095, 4097, 12345, 70001, 5, 800, 0, 3000, 9000
 
 
 @pytest.mark.parametrize("kind", ["spac_z", "spac_h"])
-@pytest.mark.parametrize("threads", [256, 512, 1024])
+@pytest.mark.parametrize("threads,radix_bits", [(256, 8), (512, 8), (1024, 8), (256, 11), (512, 11)])
 @pytest.mark.parametrize("phi", [16, 32, 64])
-def test_batch_layout_and_knn_match_oracle(kind, threads, phi):
-    # every leaf size and block size the autotuner can choose
+def test_batch_layout_and_knn_match_oracle(kind, threads, radix_bits, phi):
+    # every leaf size, block size and digit width the autotuner can choose
     pts, ids, off = make_batch(SIZES)
-    b = psi.Batch(off, kind=kind, leaf_size=phi, threads=threads)
+    b = psi.Batch(off, kind=kind, leaf_size=phi, threads=threads, radix_bits=radix_bits)
     b.build(T(pts), T(ids))
     q, qoff = queries(SIZES, pts, off, 2, 30, 5)
     gi, gd = b.knn(T(q), T(qoff), 10)
@@ -82,7 +82,7 @@ def test_batch_layout_and_knn_match_oracle(kind, threads, phi):
 def test_batch_3d_and_k100(kind):
     sizes = [500, 20000, 3, 7000]
     pts, ids, off = make_batch(sizes, dim=3, bits=21, seed=4)
-    b = psi.Batch(off, dim=3, kind=kind, leaf_size=16, coord_bits=21)
+    b = psi.Batch(off, dim=3, kind=kind, leaf_size=16, coord_bits=21, threads=256, radix_bits=11)
     b.build(T(pts), T(ids))
     q, qoff = queries(sizes, pts, off, 3, 21, 9)
     gi, gd = b.knn(T(q), T(qoff), 100)
