@@ -100,12 +100,15 @@ NodeW node_w(const NodeArrays &a) {
 // each leaf; lane u writes leaf u's).  All sorted positions of the group are loaded first, then all
 // gathers are issued, so a warp keeps GL x 3 independent loads in flight
 // instead of waiting on each leaf's dependent position -> point chain.
+// With REC the points and ids are read from 16-byte records (k_pack_records):
+// one scattered load per point instead of two.
 constexpr int GL = 4;
 
-template <int D>
+template <int D, bool REC>
 __global__ __launch_bounds__(256, 3) void k_leaf_gather(const uint64_t *skeys, const uint32_t *svals, const int32_t *pts,
-                                                     const uint32_t *ids, int64_t n, int phi, int C, PoolW pool,
-                                                     NodeW nodes, uint64_t *sep_key, uint32_t *sep_id, int64_t L) {
+                                                     const uint32_t *ids, const int4 *rec, int64_t n, int phi, int C,
+                                                     PoolW pool, NodeW nodes, uint64_t *sep_key, uint32_t *sep_id,
+                                                     int64_t L) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * GL < L; g += warps) {
@@ -130,9 +133,17 @@ __global__ __launch_bounds__(256, 3) void k_leaf_gather(const uint64_t *skeys, c
 #pragma unroll
       for (int u = 0; u < GL; ++u) {
         if (okm >> u & 1u) {
+          if (REC) {
+            const int4 r = __ldg(rec + v[u]);
+            c[u][0] = r.x;
+            c[u][1] = r.y;
+            if (D == 3) c[u][D - 1] = r.z;
+            id[u] = (uint32_t)r.w;
+          } else {
 #pragma unroll
-          for (int d = 0; d < D; ++d) c[u][d] = pts[(int64_t)v[u] * D + d];
-          id[u] = ids[v[u]];
+            for (int d = 0; d < D; ++d) c[u][d] = pts[(int64_t)v[u] * D + d];
+            id[u] = ids[v[u]];
+          }
         }
       }
 #pragma unroll
@@ -192,6 +203,20 @@ __global__ __launch_bounds__(256, 3) void k_leaf_gather(const uint64_t *skeys, c
         }
       }
     }
+  }
+}
+
+// Points and ids of the input as 16-byte records (x, y, z or 0, id), in
+// input order, for gathers by position from input that is not locally ordered.
+template <int D>
+__global__ void k_pack_records(const int32_t *pts, const uint32_t *ids, int64_t n, int4 *rec) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int4 r;
+    r.x = pts[i * D];
+    r.y = pts[i * D + 1];
+    r.z = D == 3 ? pts[i * D + D - 1] : 0;
+    r.w = (int)ids[i];
+    rec[i] = r;
   }
 }
 
@@ -291,7 +316,7 @@ int64_t summary_capacity(int64_t L, int F) {
 }
 
 psi_status spac_from_sorted(psi_index *ix, const uint64_t *skeys, const uint32_t *svals, const int32_t *pts,
-                            const uint32_t *ids, int64_t n, cudaStream_t s) {
+                            const uint32_t *ids, int64_t n, cudaStream_t s, bool records) {
   ix->n = n;
   ix->L = ceil_div(n, ix->phi);
   ix->pool_used = ix->L;
@@ -302,12 +327,22 @@ psi_status spac_from_sorted(psi_index *ix, const uint64_t *skeys, const uint32_t
   NodeW nw = node_w(ix->nodes);
   if (ix->L > 0) {
     const int g = warp_grid(ceil_div(ix->L, GL));
-    if (ix->D == 2)
-      PSI_LAUNCH_NAMED("k_leaf_gather", k_leaf_gather<2>, g, 256, 0, s, skeys, svals, pts, ids, n, ix->phi, ix->C, pw,
-                       nw, ix->sep_key, ix->sep_id, ix->L);
-    else
-      PSI_LAUNCH_NAMED("k_leaf_gather", k_leaf_gather<3>, g, 256, 0, s, skeys, svals, pts, ids, n, ix->phi, ix->C, pw,
-                       nw, ix->sep_key, ix->sep_id, ix->L);
+    Buf<int4> rec;
+    if (records) {
+      psi_status st = rec.alloc(n, s);
+      if (st || (st = pack_records(pts, ids, n, ix->D, rec.p, s))) return st;
+    }
+#define GATHER(DD, RR)                                                                                          \
+  PSI_LAUNCH_NAMED("k_leaf_gather", (k_leaf_gather<DD, RR>), g, 256, 0, s, skeys, svals, pts, ids, rec.p, n, ix->phi, \
+                   ix->C, pw, nw, ix->sep_key, ix->sep_id, ix->L)
+    if (ix->D == 2) {
+      if (records) GATHER(2, true);
+      else GATHER(2, false);
+    } else {
+      if (records) GATHER(3, true);
+      else GATHER(3, false);
+    }
+#undef GATHER
   }
   return build_spac_summary(ix, s);
 }
@@ -315,6 +350,15 @@ psi_status spac_from_sorted(psi_index *ix, const uint64_t *skeys, const uint32_t
 }  // namespace psi
 
 namespace psi {
+
+psi_status pack_records(const int32_t *pts, const uint32_t *ids, int64_t n, int D, int4 *rec, cudaStream_t s) {
+  if (n <= 0) return PSI_OK;
+  if (D == 2)
+    PSI_LAUNCH(k_pack_records<2>, warp_grid(ceil_div(n, 32)), 256, 0, s, pts, ids, n, rec);
+  else
+    PSI_LAUNCH(k_pack_records<3>, warp_grid(ceil_div(n, 32)), 256, 0, s, pts, ids, n, rec);
+  return PSI_OK;
+}
 
 // (Re)builds a SPaC index from scratch over n points, replacing its storage.
 psi_status spac_build_fresh(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t n, cudaStream_t s) {
@@ -338,7 +382,9 @@ psi_status spac_build_fresh(psi_index *ix, const int32_t *pts, const uint32_t *i
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, n, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
                        ix->d_status, s, &r, ix->cfg.radix_bits)))
     return st;
-  return spac_from_sorted(ix, r.keys, r.vals, pts, ids, n, s);
+  // input in random order: each point's gather by position is a scattered
+  // read, so points and ids are first packed into one record per point
+  return spac_from_sorted(ix, r.keys, r.vals, pts, ids, n, s, r.local == 0);
 }
 
 }  // namespace psi

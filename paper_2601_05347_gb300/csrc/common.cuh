@@ -149,6 +149,9 @@ struct SortResult {
   uint64_t *keys;
   uint32_t *vals;
   int prefix_low = 0;  // > 0: sorted by key bits [prefix_low, key_bits) only (then runs fixed up)
+  // encoding sorts that counted input locality: 1 when at least half of the
+  // input neighbours share their top 24 key bits, 0 when not; -1 not counted
+  int local = -1;
 };
 
 // Sorts n pairs.  If enc.pts is non-null the keys are computed from the points

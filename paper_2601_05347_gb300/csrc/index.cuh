@@ -115,7 +115,10 @@ void free_pool(Pool &p, cudaStream_t s);
 psi_status build_spac_summary(psi_index *ix, cudaStream_t s);
 // SPaC build from sorted (key, position) pairs.
 psi_status spac_from_sorted(psi_index *ix, const uint64_t *skeys, const uint32_t *svals, const int32_t *pts,
-                            const uint32_t *ids, int64_t n, cudaStream_t s);
+                            const uint32_t *ids, int64_t n, cudaStream_t s,
+                            bool records = false);
+// Points and ids as 16-byte records (x, y, z or 0, id) in input order.
+psi_status pack_records(const int32_t *pts, const uint32_t *ids, int64_t n, int D, int4 *rec, cudaStream_t s);
 psi_status alloc_pleaves(PLeaves &a, int D, int64_t cap, cudaStream_t s);
 void free_pleaves(PLeaves &a, cudaStream_t s);
 psi_status porth_build(psi_index *ix, const int32_t *pts, const uint32_t *ids, int64_t n, cudaStream_t s);
@@ -147,6 +150,9 @@ struct KnnSeed {
   // scratch of nq entries (required with qkey): the seed leaf node (or slot)
   // of each query in curve order, written by the k-NN call before its search
   uint32_t *pos = nullptr;
+  // P-Orth: node of each leaf of the key-ordered leaf list, whose cell base
+  // keys sep_key then holds; null for SPaC, where leaf i is node i
+  const int32_t *leaf_node = nullptr;
 };
 
 // k-NN of nq queries, each starting at qroot[q] (or tv.root when qroot is

@@ -40,6 +40,7 @@ __device__ __forceinline__ bool pair_less<int64_t>(int64_t da, uint32_t ia, int6
       : "=&r"(t), "=r"(r)
       : "r"(ia), "r"(ib), "r"((uint32_t)da), "r"((uint32_t)db), "r"((uint32_t)((uint64_t)da >> 32)),
         "r"((uint32_t)((uint64_t)db >> 32)));
+  (void)t;  // the low words' difference: only the borrow out of the top word is used
   return r != 0;
 }
 

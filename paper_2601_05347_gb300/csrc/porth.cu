@@ -91,12 +91,13 @@ __device__ __forceinline__ uint64_t cell_of(uint64_t k, int depth, int D, int bi
 
 // Gather the sorted points into the contiguous pool: GP items per thread,
 // all positions loaded first, then all gathers, so that each thread keeps
-// several independent random loads in flight.
+// several independent random loads in flight.  With REC the points and ids
+// are read from 16-byte records (pack_records): one load per point.
 constexpr int GP = 4;
 
-template <int D>
+template <int D, bool REC>
 __global__ void k_porth_gather(const uint64_t *skeys, const uint32_t *svals, const int32_t *pts, const uint32_t *ids,
-                               int64_t n, Pool pool) {
+                               const int4 *rec, int64_t n, Pool pool) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * GP;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * GP + threadIdx.x; i0 < n; i0 += stride) {
     uint32_t v[GP];
@@ -111,9 +112,17 @@ __global__ void k_porth_gather(const uint64_t *skeys, const uint32_t *svals, con
     for (int u = 0; u < GP; ++u) {
       const int64_t i = i0 + (int64_t)u * blockDim.x;
       if (i < n) {
+        if (REC) {
+          const int4 r = __ldg(rec + v[u]);
+          c[u][0] = r.x;
+          c[u][1] = r.y;
+          if (D == 3) c[u][D - 1] = r.z;
+          id[u] = (uint32_t)r.w;
+        } else {
 #pragma unroll
-        for (int d = 0; d < D; ++d) c[u][d] = pts[(int64_t)v[u] * D + d];
-        id[u] = ids[v[u]];
+          for (int d = 0; d < D; ++d) c[u][d] = pts[(int64_t)v[u] * D + d];
+          id[u] = ids[v[u]];
+        }
       }
     }
 #pragma unroll
@@ -1183,12 +1192,22 @@ psi_status porth_build(psi_index *ix, const int32_t *pts, const uint32_t *ids, i
   if ((st = sort_pairs(encode_spec(ix, pts), nullptr, nullptr, n, ix->key_bits, ids, k0.p, v0.p, k1.p, v1.p,
                        ix->d_status, s, &r, ix->cfg.radix_bits)))
     return st;
-  if (ix->D == 2)
-    PSI_LAUNCH_NAMED("k_porth_gather", k_porth_gather<2>, grid_for(n), 256, 0, s, r.keys, r.vals, pts, ids, n,
-                     ix->pool);
-  else
-    PSI_LAUNCH_NAMED("k_porth_gather", k_porth_gather<3>, grid_for(n), 256, 0, s, r.keys, r.vals, pts, ids, n,
-                     ix->pool);
+  // input in random order: points and ids packed into one record per point
+  // first, so that each gather by position is one scattered read, not two
+  const bool records = r.local == 0;
+  Buf<int4> rec;
+  if (records && ((st = rec.alloc(n, s)) || (st = pack_records(pts, ids, n, ix->D, rec.p, s)))) return st;
+#define GATHER(DD, RR)                                                                                           \
+  PSI_LAUNCH_NAMED("k_porth_gather", (k_porth_gather<DD, RR>), grid_for(n), 256, 0, s, r.keys, r.vals, pts, ids, \
+                   rec.p, n, ix->pool)
+  if (ix->D == 2) {
+    if (records) GATHER(2, true);
+    else GATHER(2, false);
+  } else {
+    if (records) GATHER(3, true);
+    else GATHER(3, false);
+  }
+#undef GATHER
   WorkArray w{ix->pool.pkey, nullptr, nullptr, 0u, n};
   int64_t L = 0;
   if ((st = work_leaves(ix, w, (uint32_t)n, ix->pl, &L, nullptr, s))) return st;

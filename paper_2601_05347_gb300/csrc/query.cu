@@ -18,6 +18,8 @@
 // Range list: the same traversal counts first; after an exclusive scan of the
 // counts a second traversal writes each query's ids at its offset (a
 // subtree inside the box is enumerated without further box tests).
+#include <type_traits>
+
 #include "bitonic.cuh"
 #include "index.cuh"
 #include "keys.cuh"
@@ -162,6 +164,8 @@ struct KnnStats {
 constexpr int KSTACK = 256;
 // Queries per warp of the grouped k-NN kernel (k <= 32, queries in curve order).
 constexpr int kGroup = 2;
+// Flag of a stack entry that is a leaf to scan (in its count word).
+constexpr uint32_t kLeafEntry = 0x80000000u;
 
 // Last position p in [0, n) whose first key (>> shift) is <= key, or 0 when
 // the key precedes every position (binary search by one thread).
@@ -180,7 +184,8 @@ __device__ __forceinline__ int64_t seed_search(FirstKey first_key, int64_t n, ui
 
 // Seed position of every query (queries in curve order), one thread each:
 // SPaC, the node of the last leaf of the query's index whose first key is at
-// most the query's key; P-Orth, the last pool slot with that property.  Many
+// most the query's key; P-Orth, the position in the key-ordered leaf list of
+// the last leaf whose cell starts at or before the query's key.  Many
 // independent searches in flight hide the dependent loads that one warp-wide
 // search per query would wait on.
 __global__ void k_knn_seed(const KnnSeed sd, const uint32_t *ref, const uint32_t *order, int64_t nq, uint32_t *pos) {
@@ -211,7 +216,8 @@ __global__ void k_knn_seed(const KnnSeed sd, const uint32_t *ref, const uint32_t
 // overlap, so the nearest box is often not the leaf around the query; the
 // curve neighbours make the k-th distance nearly final before the search
 // starts (so the order of the later pops matters little), and the search then
-// skips the seed leaves.
+// skips the seed leaves.  Seed (P-Orth): the leaf whose cell holds the query's
+// key (or the last leaf before it in key order), alone.
 template <int D, int KPL, bool STATS>
 __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
   // internal nodes still to visit: (node, key, first child, children)
@@ -241,7 +247,8 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     if (sd.qkey && root >= 0) {
       const int64_t pos = sd.pos[qi];  // k_knn_seed
       if (L > 0) {
-        const int64_t j = pos;
+        // P-Orth: pos is a position in the key-ordered leaf list
+        const int64_t j = sd.leaf_node ? (int64_t)sd.leaf_node[pos] : pos;
         const int64_t le = lb + L;
         knn_scan_leaf<D, KPL, true>(t, (uint32_t)j, qc, kl, a.k);
         int64_t got = t.cnt[j];
@@ -251,7 +258,10 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
         }
         s_lo = j;
         s_hi = j;
-        while (got < a.k && (s_lo > lb || s_hi + 1 < le)) {
+        // widened along the curve only where leaves are consecutive nodes
+        // (SPaC; P-Orth's key-order neighbours give a loose bound in 3D and
+        // did not cut the leaves its search scans)
+        while (!sd.leaf_node && got < a.k && (s_lo > lb || s_hi + 1 < le)) {
           int64_t nx;
           if (s_hi + 1 < le && (s_lo == lb || s_hi - j <= j - s_lo))
             nx = ++s_hi;
@@ -274,16 +284,27 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
     // Children [c0, c0 + nk) of an expanded node: the internal ones that may
     // hold a neighbour are pushed (the nearest on top); the leaves that may
     // are scanned at once, nearest first, each re-checked against the k-th
-    // distance left by the ones before it.  Each lane loads its child's
-    // reference and count with its box, so a popped entry needs no further
-    // load before its own children are read.
-    auto expand = [&](uint32_t c0, int nk) {
+    // distance left by the ones before it.  Where a node has both (P-Orth),
+    // only the leaves nearer than every internal survivor are scanned at once
+    // and the others are pushed beside the internal ones (count | kLeafEntry),
+    // so the search still takes the nearest child first.  A popped leaf entry
+    // comes back here as `pl` (its lane 0 stands for the leaf).  Each lane
+    // loads its child's reference and count with its box, so a popped entry
+    // needs no further load before its own children are read.
+    auto expand = [&](uint32_t c0, int nk, bool pl, uint32_t pkey) {
       const uint32_t c = c0 + (uint32_t)lane;
       uint32_t key = 0xFFFFFFFFu;  // above any k-th distance key
       bool leafc = false;
       uint32_t cref = 0;
       int ccnt = 0;
-      if (lane < nk) {  // every node of every layout holds a point
+      if (pl) {
+        if (lane == 0) {
+          key = pkey;
+          leafc = true;
+          cref = c0;
+          ccnt = nk;
+        }
+      } else if (lane < nk) {  // every node of every layout holds a point
         cref = t.ref[c];
         if (a.leaf_limit >= 0) {
           leafc = (int64_t)c < a.leaf_limit;
@@ -297,19 +318,25 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
         if (leafc && c >= slo && c <= shi) key = 0xFFFFFFFFu;  // scanned as a seed
       }
       const bool in = key <= kdk;
-      if (STATS) {
+      if (STATS && !pl) {
         ++n_int;
         n_kids += nk;
       }
-      const uint32_t mi = __ballot_sync(0xFFFFFFFFu, in && !leafc);
+      uint32_t mi = __ballot_sync(0xFFFFFFFFu, in && !leafc);
       uint32_t ml = __ballot_sync(0xFFFFFFFFu, in && leafc);
+      if (mi && ml) {  // warp-uniform: leaves not nearer than the nearest internal survivor wait
+        const uint32_t imin = __reduce_min_sync(0xFFFFFFFFu, ((mi >> lane) & 1u) ? key : 0xFFFFFFFFu);
+        const uint32_t defer = __ballot_sync(0xFFFFFFFFu, in && leafc && key >= imin);
+        ml &= ~defer;
+        mi |= defer;
+      }
       if (mi) {
         const int n = __popc(mi);
         if (sp + n > KSTACK) {  // cannot happen within the depth bound above
           if (lane == 0) atomicOr(a.status, ST_STACK);
         } else {
-          // the nearest internal survivor (lowest lane on ties) takes the top
-          // slot, the one that held the top slot takes its place
+          // the nearest survivor (lowest lane on ties) takes the top slot, the
+          // one that held the top slot takes its place
           const bool ii = (mi >> lane) & 1u;
           const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, ii ? key : 0xFFFFFFFFu);
           const int win = __ffs(__ballot_sync(0xFFFFFFFFu, ii && key == mn)) - 1;
@@ -319,7 +346,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
           else if (pos == n - 1)
             pos = __popc(mi & ((1u << win) - 1u));
           __syncwarp();
-          if (ii) s_stk[w][sp + pos] = make_uint4(c, key, cref, (uint32_t)ccnt);
+          if (ii) s_stk[w][sp + pos] = make_uint4(c, key, cref, (uint32_t)ccnt | (leafc ? kLeafEntry : 0u));
           sp += n;
           __syncwarp();
         }
@@ -345,10 +372,11 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
           knn_scan_leaf<D, KPL>(t, (uint32_t)root, qc, kl, a.k);
       } else {
         // the root as the first entry: one call site keeps `expand` inlined
-        uint32_t c0 = t.ref[root];
+        uint32_t c0 = t.ref[root], pkey = 0;
         int nk = t.kids[root];
+        bool pl = false;
         for (;;) {
-          expand(c0, nk);
+          expand(c0, nk, pl, pkey);
           uint4 e = make_uint4(0, 0, 0, 0);
           bool more = false;
           while (sp > 0) {
@@ -360,7 +388,9 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
           }
           if (!more) break;
           c0 = e.z;
-          nk = (int)e.w;
+          nk = (int)(e.w & ~kLeafEntry);
+          pl = (e.w & kLeafEntry) != 0;
+          pkey = e.y;
         }
       }
     }
@@ -428,11 +458,15 @@ __device__ __forceinline__ void knn_scan_group(const TreeView &t, uint32_t s0, i
 // distance admits it), and each leaf's points are loaded once and offered to
 // the lists of the queries that need the leaf.  Per query the result is the
 // same as k_knn's: exact (distance, id) order, each query pruned by its own
-// k-th distance.  Seeds (SPaC): the distinct seed leaves of the group's
-// queries are scanned first, for all of them.
-template <int D, int G, bool STATS>
+// k-th distance.  Seeds: the distinct seed leaves of the group's queries are
+// scanned first, for all of them.
+template <int D, int G, bool STATS, bool RECHECK>
 __global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats) {
-  __shared__ uint2 s_stk[QW][KSTACK];  // internal nodes still to visit: (first child, children)
+  static_assert(G <= 2 || !RECHECK, "a stack entry holds the box keys of two queries");
+  // internal nodes still to visit: (first child, children) and, with RECHECK,
+  // the box keys of queries 0 and G - 1
+  using Entry = typename std::conditional<RECHECK, uint4, uint2>::type;
+  __shared__ Entry s_stk[QW][KSTACK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const TreeView &t = a.t;
   const KnnSeed &sd = a.seed;
@@ -449,7 +483,7 @@ __global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats
       const int64_t q = a.order ? (int64_t)a.order[qi] : qi;
 #pragma unroll
       for (int d = 0; d < D; ++d) qc[g][d] = a.q[q * D + d];
-      seed[g] = sd.qkey ? sd.pos[qi] : 0xFFFFFFFFu;
+      seed[g] = !sd.qkey ? 0xFFFFFFFFu : sd.leaf_node ? (uint32_t)sd.leaf_node[sd.pos[qi]] : sd.pos[qi];
     }
     KList<1> kl[G];
 #pragma unroll
@@ -479,7 +513,10 @@ __global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats
     // Children [c0, c0 + nk): the internal ones some query may need are pushed
     // (the one nearest to some query on top); the leaves some query may need
     // are scanned at once, nearest first, for the queries that still need them.
-    auto expand = [&](uint32_t c0, int nk) {
+    // With RECHECK (P-Orth), leaves that are not nearer than every internal
+    // survivor are pushed too (count | kLeafEntry) and come back as `pl`, as
+    // in k_knn.
+    auto expand = [&](uint32_t c0, int nk, bool pl, uint32_t pk0, uint32_t pk1) {
       const uint32_t c = c0 + (uint32_t)lane;
       uint32_t key[G];
 #pragma unroll
@@ -488,7 +525,21 @@ __global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats
       bool leafc = false;
       uint32_t cref = 0;
       int ccnt = 0;
-      if (lane < nk) {
+      if (RECHECK && pl) {
+        if (lane == 0) {
+          key[0] = pk0;
+          if (G > 1) key[G - 1] = pk1;
+          leafc = true;
+          cref = c0;
+          ccnt = nk;
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (key[g] <= kdk[g]) {
+              need |= 1u << g;
+              mkey = min(mkey, key[g]);
+            }
+        }
+      } else if (lane < nk) {
         cref = t.ref[c];
         if (a.leaf_limit >= 0) {
           leafc = (int64_t)c < a.leaf_limit;
@@ -518,12 +569,18 @@ __global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats
             if (c == seed[g]) need = 0;  // scanned as a seed
         }
       }
-      if (STATS) {
+      if (STATS && !(RECHECK && pl)) {
         ++n_int;
         n_kids += nk;
       }
-      const uint32_t mi = __ballot_sync(0xFFFFFFFFu, need && !leafc);
+      uint32_t mi = __ballot_sync(0xFFFFFFFFu, need && !leafc);
       uint32_t ml = __ballot_sync(0xFFFFFFFFu, need && leafc);
+      if (RECHECK && mi && ml) {  // warp-uniform
+        const uint32_t imin = __reduce_min_sync(0xFFFFFFFFu, ((mi >> lane) & 1u) ? mkey : 0xFFFFFFFFu);
+        const uint32_t defer = __ballot_sync(0xFFFFFFFFu, need && leafc && mkey >= imin);
+        ml &= ~defer;
+        mi |= defer;
+      }
       if (mi) {
         const int n = __popc(mi);
         if (sp + n > KSTACK) {  // cannot happen within the depth bound
@@ -538,7 +595,13 @@ __global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats
           else if (pos == n - 1)
             pos = __popc(mi & ((1u << win) - 1u));
           __syncwarp();
-          if (ii) s_stk[w][sp + pos] = make_uint2(cref, (uint32_t)ccnt);
+          if (ii) {
+            if constexpr (RECHECK)
+              s_stk[w][sp + pos] = make_uint4(cref, (uint32_t)ccnt | (leafc ? kLeafEntry : 0u), key[0],
+                                              G > 1 ? key[G - 1] : 0xFFFFFFFFu);
+            else
+              s_stk[w][sp + pos] = make_uint2(cref, (uint32_t)ccnt);
+          }
           sp += n;
           __syncwarp();
         }
@@ -577,14 +640,31 @@ __global__ __launch_bounds__(QW * 32) void k_knn_group(KnnArgs a, KnnStats stats
         for (int g = 0; g < G; ++g) sd_root |= seed[g] == (uint32_t)root;
         if (!sd_root) knn_scan_group<D, G, false>(t, t.ref[root], t.cnt[root], qc, kl, a.k, all);
       } else {
-        uint32_t c0 = t.ref[root];
+        uint32_t c0 = t.ref[root], pk0 = 0, pk1 = 0;
         int nk = t.kids[root];
+        bool pl = false;
         for (;;) {  // one call site keeps `expand` inlined
-          expand(c0, nk);
-          if (sp == 0) break;
-          const uint2 e = s_stk[w][--sp];
-          c0 = e.x;
-          nk = (int)e.y;
+          expand(c0, nk, pl, pk0, pk1);
+          // RECHECK: the next entry that some query still needs under its
+          // k-th distance of this moment (the others are dropped unexpanded)
+          bool more = false;
+          while (sp > 0) {
+            const Entry e = s_stk[w][--sp];
+            bool need = true;
+            if constexpr (RECHECK) {
+              need = e.z <= kdk[0] || (G > 1 && e.w <= kdk[G - 1]);
+              pl = (e.y & kLeafEntry) != 0;
+              pk0 = e.z;
+              pk1 = e.w;
+            }
+            if (need) {
+              c0 = e.x;
+              nk = (int)(e.y & ~kLeafEntry);
+              more = true;
+              break;
+            }
+          }
+          if (!more) break;
         }
       }
     }
@@ -793,21 +873,30 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
   const int kpl = k <= 32 ? 1 : (k <= 64 ? 2 : 4);
   // k <= 32 over one tree with queries in curve order: kGroup queries per warp
   if (kpl == 1 && !qroot && order && kGroup > 1) {
-#define KNN_GROUP(DD)                                                                                       \
+#define KNN_GROUP(DD, RC)                                                                                   \
   do {                                                                                                      \
     if (d_stats)                                                                                            \
-      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn_group<DD, kGroup, true>),                                      \
-                       resident_query_grid(k_knn_group<DD, kGroup, true>, ceil_div(nq, kGroup)), QW * 32, 0, s, \
-                       a, stats);                                                                           \
+      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn_group<DD, kGroup, true, RC>),                                  \
+                       resident_query_grid(k_knn_group<DD, kGroup, true, RC>, ceil_div(nq, kGroup)), QW * 32, \
+                       0, s, a, stats);                                                                     \
     else                                                                                                    \
-      PSI_LAUNCH_NAMED("k_knn", (k_knn_group<DD, kGroup, false>),                                           \
-                       resident_query_grid(k_knn_group<DD, kGroup, false>, ceil_div(nq, kGroup)), QW * 32, 0, \
-                       s, a, stats);                                                                        \
+      PSI_LAUNCH_NAMED("k_knn", (k_knn_group<DD, kGroup, false, RC>),                                       \
+                       resident_query_grid(k_knn_group<DD, kGroup, false, RC>, ceil_div(nq, kGroup)), QW * 32, \
+                       0, s, a, stats);                                                                     \
   } while (0)
-    if (D == 2)
-      KNN_GROUP(2);
-    else
-      KNN_GROUP(3);
+    // Popped nodes are re-checked against the k-th distances where the
+    // search pushes many that later bounds rule out: P-Orth, whose nodes mix
+    // leaf and internal children at every depth.  SPaC's seeds make the
+    // bounds nearly final before the first push, and there the larger stack
+    // entries cost more than the re-check saves.
+    const bool recheck = leaf_limit < 0;
+    if (D == 2) {
+      if (recheck) KNN_GROUP(2, true);
+      else KNN_GROUP(2, false);
+    } else {
+      if (recheck) KNN_GROUP(3, true);
+      else KNN_GROUP(3, false);
+    }
 #undef KNN_GROUP
     PSI_CK(cudaGetLastError());
     return PSI_OK;
@@ -850,9 +939,11 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
     seed.key_shift = qo.key_shift;
     seed.pos = qo.spare;
     seed.sep_key = ix->sep_key;
-    // P-Orth leaves do not overlap: its search starts at the root without a
-    // seed and stays near the floor of leaves it must scan
-    if (ix->cfg.kind == PSI_PORTH) seed.qkey = nullptr;
+    if (ix->cfg.kind == PSI_PORTH) {
+      // the leaf whose cell holds (or last precedes) the query's key
+      seed.sep_key = ix->pl.key;
+      seed.leaf_node = ix->leaf_node;
+    }
   }
   return run_knn_roots(ix->view(), q, nq, k, qo.order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s,
                        seed, ix->cfg.kind == PSI_PORTH ? -1 : ix->L);

@@ -133,7 +133,14 @@ enum : int {
 // first digit ((key >> alt_shift) & mask, into hist_alt) and a HyperLogLog
 // sketch of the distinct values of key >> alt_shift (kHllRegs registers, into
 // hll), from which the host estimates how many keys share their top bits.
+// The sketch takes the first item of each thread's round (a quarter of the
+// keys, hll_sampled of them): the decision it feeds needs the ratio of keys
+// to distinct top bits only roughly.
 constexpr int kHllBits = 12, kHllRegs = 1 << kHllBits;
+static int64_t hll_sampled(int64_t n) {
+  const int64_t round = 256 * HIST_U;  // items of one block round (256 threads)
+  return (n / round) * 256 + std::min<int64_t>(n % round, 256);
+}
 struct HistExtra {
   uint32_t *hist_alt = nullptr;
   int alt_shift = 0;
@@ -213,15 +220,11 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
         n_near += (threadIdx.x & 31) < 31 && ok[u] && okn && ((k[u] ^ kn) >> near_shift) == 0;
       }
     }
-    if (ex.hll) {
-#pragma unroll
-      for (int u = 0; u < HIST_U; ++u)
-        if (ok[u]) {
-          const uint64_t h = hll_hash(k[u] >> ex.alt_shift);
-          // register: the top kHllBits of the hash; value: 1 + leading zeros of the rest
-          const uint32_t rho = (uint32_t)__clzll((long long)((h << kHllBits) | (1ull << (kHllBits - 1)))) + 1u;
-          atomicMax(&shll[h >> (64 - kHllBits)], rho);
-        }
+    if (ex.hll && ok[0]) {
+      const uint64_t h = hll_hash(k[0] >> ex.alt_shift);
+      // register: the top kHllBits of the hash; value: 1 + leading zeros of the rest
+      const uint32_t rho = (uint32_t)__clzll((long long)((h << kHllBits) | (1ull << (kHllBits - 1)))) + 1u;
+      atomicMax(&shll[h >> (64 - kHllBits)], rho);
     }
 #pragma unroll
     for (int u = 0; u < HIST_U; ++u) {
@@ -1020,7 +1023,7 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
     synced = true;
     // prefix sort when the keys' top bits take nearly n distinct values (runs
     // of equal top bits are then few and short)
-    if ((double)n < kPrefixMaxRun * hll_estimate(h_cnt->hll)) low = low_c;
+    if ((double)hll_sampled(n) < kPrefixMaxRun * hll_estimate(h_cnt->hll)) low = low_c;
   }
   const int passes = (key_bits - low + RB - 1) / RB;
   int pk = passes, p_pack = passes;
@@ -1085,6 +1088,7 @@ static psi_status sort_pairs_rb(const EncodeSpec &enc, const uint64_t *keys_in, 
   out->keys = kb[(passes - 1) & 1];
   out->vals = vb[(passes - 1) & 1];
   out->prefix_low = low;
+  out->local = synced ? (2 * h_cnt->near >= (unsigned long long)n ? 1 : 0) : -1;
   return PSI_OK;
 }
 
