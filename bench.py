@@ -819,27 +819,34 @@ def run_config1():
     boxes = gen.square_boxes(10_000, 2, BITS, side, gen.config_seed(0, 4))
     d = dict(p=T(pts), i=T(live_i[:n]), ip=T(ins), ii=T(live_i[n:]), dp=T(live_p[dsel]), di=T(live_i[dsel]), q=T(q),
              b=T(boxes))
-    res = {}
-    t, _ = _timed(lambda: psi.Index(d["p"], d["i"], kind="spac_z", leaf_size=32).close())
-    res["build_ms"] = round(t, 3)
-    ix = psi.Index(d["p"], d["i"], kind="spac_z", leaf_size=32)
-    s = torch.cuda.current_stream()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    e[0].record(s)
-    ix.insert(d["ip"], d["ii"])
-    e[1].record(s)
-    ix.delete(d["dp"], d["di"])
-    e[2].record(s)
-    ix.knn(d["q"], 10)
-    e[3].record(s)
-    c = ix.range_count(d["b"])
-    e[4].record(s)
-    torch.cuda.synchronize()
-    res.update(insert_ms=round(e[0].elapsed_time(e[1]), 3), delete_ms=round(e[1].elapsed_time(e[2]), 3),
-               knn_ms=round(e[2].elapsed_time(e[3]), 3), range_count_ms=round(e[3].elapsed_time(e[4]), 3),
-               mean_range_count=round(float(c.float().mean()), 1), size=len(ix))
+    # one untimed pass of the whole sequence (first launches load the kernels),
+    # then the best of three timed passes, each phase on a fresh index
+    best = None
+    for rep in range(4):
+        t, _ = _timed(lambda: psi.Index(d["p"], d["i"], kind="spac_z", leaf_size=32).close())
+        ix = psi.Index(d["p"], d["i"], kind="spac_z", leaf_size=32)
+        s = torch.cuda.current_stream()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(s)
+        ix.insert(d["ip"], d["ii"])
+        e[1].record(s)
+        ix.delete(d["dp"], d["di"])
+        e[2].record(s)
+        ix.knn(d["q"], 10)
+        e[3].record(s)
+        c = ix.range_count(d["b"])
+        e[4].record(s)
+        torch.cuda.synchronize()
+        cur = dict(build_ms=round(t, 3), insert_ms=round(e[0].elapsed_time(e[1]), 3),
+                   delete_ms=round(e[1].elapsed_time(e[2]), 3), knn_ms=round(e[2].elapsed_time(e[3]), 3),
+                   range_count_ms=round(e[3].elapsed_time(e[4]), 3),
+                   mean_range_count=round(float(c.float().mean()), 1), size=len(ix))
+        ix.close()
+        if rep == 0:
+            continue
+        best = cur if best is None else {k: min(best[k], v) if k.endswith("_ms") else v for k, v in cur.items()}
+    res = best
     res["build_Mpts_s"] = round(n / res["build_ms"] / 1e3, 1)
-    ix.close()
     return res
 
 

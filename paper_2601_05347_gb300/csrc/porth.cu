@@ -138,55 +138,59 @@ __global__ void k_porth_gather(const uint64_t *skeys, const uint32_t *svals, con
   }
 }
 
-constexpr int LT = 256;  // positions per block in the leaf-depth kernel (8 blocks per SM overlap their loads)
+// Leaf-depth kernel: LDE positions per block of LDT threads (phi <= 64).
+constexpr int LDT = 256, LDE = 2048;
 
 // Leaf depth of every position of a key array (positions outside [0, n)
-// contribute no window).
-__global__ __launch_bounds__(LT) void k_leaf_depth(const uint64_t *keys, int64_t n, int phi, int K, int D, int bits,
-                                                   int32_t *ldepth) {
-  __shared__ uint64_t sk[LT + 2 * 64 + 1];
-  __shared__ int8_t sm[LT + 64];
-  const int64_t base = (int64_t)blockIdx.x * LT;
-  // keys [base - phi, base + LT + phi)
-  for (int t = threadIdx.x; t < LT + 2 * phi; t += blockDim.x) {
+// contribute no window).  m_j = common digits of (k_j, k_{j+phi}); position i
+// takes 1 + the maximum of m_j over the window j in [i - phi, i].  The window
+// maximum comes from running maxima over segments of phi entries (van Herk;
+// Gil and Werman): the window starting at entry u spans the rest of u's
+// segment and the next segment up to u + phi, so it is the maximum of u's
+// suffix maximum and the prefix maximum at u + phi.
+__global__ __launch_bounds__(LDT) void k_leaf_depth(const uint64_t *keys, int64_t n, int phi, int K, int D, int bits,
+                                                    int32_t *ldepth) {
+  __shared__ uint64_t sk[LDE + 2 * 64];
+  __shared__ int8_t sm[LDE + 64], spre[LDE + 64], ssuf[LDE + 64];
+  const int64_t base = (int64_t)blockIdx.x * LDE;
+  // keys [base - phi, base + LDE + phi)
+  for (int t = threadIdx.x; t < LDE + 2 * phi; t += LDT) {
     const int64_t g = base - phi + t;
     sk[t] = (g >= 0 && g < n) ? keys[g] : 0;
   }
   __syncthreads();
-  // m_j for j in [base - phi, base + LT): window [j, j + phi]
-  for (int t = threadIdx.x; t < LT + phi; t += blockDim.x) {
+  // entry t is m_j for j = base - phi + t, t in [0, LDE + phi); -1 ("no
+  // pair") is neutral for the maximum
+  const int nm = LDE + phi;
+  for (int t = threadIdx.x; t < nm; t += LDT) {
     const int64_t j = base - phi + t;
     int m = -1;
     if (j >= 0 && j + phi < n) m = common_digits(sk[t], sk[t + phi], K, D, bits);
     sm[t] = (int8_t)m;
   }
   __syncthreads();
-  // maximum over each window [t, t + phi] by doubling: after the round with
-  // step k every entry holds the maximum of the 2k entries from it (-1, "no
-  // pair", is neutral); the window is then two overlapping power-of-two spans
-  const int w = phi + 1;
-  int p2 = 1;
-  while (2 * p2 <= w) p2 *= 2;
-  for (int k = 1; k < p2; k *= 2) {
-    int8_t v[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int t = threadIdx.x + r * LT;
-      v[r] = -1;
-      if (t < LT + phi) v[r] = (int8_t)max((int)sm[t], t + k < LT + phi ? (int)sm[t + k] : -1);
+  // per segment [a, a + phi): prefix maxima (even tasks), suffix maxima (odd)
+  const int nseg = (nm + phi - 1) / phi;
+  for (int q = threadIdx.x; q < 2 * nseg; q += LDT) {
+    const int a = (q >> 1) * phi, b = min(a + phi, nm);
+    int r = -1;
+    if (q & 1) {
+      for (int t = b - 1; t >= a; --t) {
+        r = max(r, (int)sm[t]);
+        ssuf[t] = (int8_t)r;
+      }
+    } else {
+      for (int t = a; t < b; ++t) {
+        r = max(r, (int)sm[t]);
+        spre[t] = (int8_t)r;
+      }
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int t = threadIdx.x + r * LT;
-      if (t < LT + phi) sm[t] = v[r];
-    }
-    __syncthreads();
   }
-  const int64_t i = base + threadIdx.x;
-  if (i < n) {
-    const int t = threadIdx.x;
-    const int M = max((int)sm[t], (int)sm[t + w - p2]);
+  __syncthreads();
+  for (int u = threadIdx.x; u < LDE; u += LDT) {
+    const int64_t i = base + u;
+    if (i >= n) break;
+    const int M = max((int)ssuf[u], (int)spre[u + phi]);
     ldepth[i] = min(M + 1, bits);
   }
 }
@@ -1111,7 +1115,7 @@ static psi_status work_leaves(psi_index *ix, const WorkArray &w, uint32_t end_sl
   if ((st = ldepth.alloc(w.n, s)) || (st = start.alloc(w.n, s)) || (st = rank.alloc(w.n, s)) ||
       (st = tot.alloc(1, s)))
     return st;
-  PSI_LAUNCH(k_leaf_depth, (unsigned)ceil_div(w.n, LT), LT, 0, s, w.key, w.n, ix->phi, K, D, bits, ldepth.p);
+  PSI_LAUNCH(k_leaf_depth, (unsigned)ceil_div(w.n, LDE), LDT, 0, s, w.key, w.n, ix->phi, K, D, bits, ldepth.p);
   PSI_LAUNCH(k_work_starts, grid_for(w.n), 256, 0, s, w, ldepth.p, D, bits, start.p);
   if ((st = scan_i32_to_i64(start.p, rank.p, w.n, tot.p, s))) return st;
   int64_t L = 0;

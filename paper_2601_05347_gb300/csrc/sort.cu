@@ -1238,13 +1238,114 @@ psi_status scan_impl(const T *in, int64_t *out, int64_t n, int64_t *d_total, cud
   PSI_CK(cudaGetLastError());
   return PSI_OK;
 }
+
+// int32 -> int64 exclusive scan with 16 consecutive elements per thread (four
+// 16-byte loads, a running sum in registers, eight 16-byte stores), so that
+// the block sums and the offsets cost one read, and one read and write, of the
+// array at full width.  A block takes SCAN_CHUNK = 256 x 16 elements.
+constexpr int SCANV_T = 256, SCANV_E = 16;
+static_assert(SCANV_T * SCANV_E == SCAN_CHUNK, "block sums are laid out per SCAN_CHUNK elements");
+
+// The SCANV_E elements of this thread (zero past n).
+__device__ __forceinline__ void scanv_load(const int32_t *in, int64_t n, int64_t i0, int32_t (&v)[SCANV_E]) {
+  if (i0 + SCANV_E <= n) {
+    const int4 *p = reinterpret_cast<const int4 *>(in + i0);
+#pragma unroll
+    for (int j = 0; j < SCANV_E / 4; ++j) {
+      const int4 q = p[j];
+      v[4 * j] = q.x;
+      v[4 * j + 1] = q.y;
+      v[4 * j + 2] = q.z;
+      v[4 * j + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < SCANV_E; ++j) v[j] = i0 + j < n ? in[i0 + j] : 0;
+  }
+}
+
+// Block sum of 64-bit values (every thread gets it).
+__device__ __forceinline__ int64_t scanv_block_excl(int64_t x, int64_t *total) {
+  __shared__ int64_t ws[SCANV_T / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  int64_t before = 0, all = 0;
+#pragma unroll
+  for (int j = 0; j < SCANV_T / 32; ++j) {
+    before += j < w ? ws[j] : 0;
+    all += ws[j];
+  }
+  *total = all;
+  return before + inc - x;
+}
+
+__global__ __launch_bounds__(SCANV_T) void k_scanv_reduce(const int32_t *in, int64_t n, int64_t *sums) {
+  const int64_t i0 = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCANV_E;
+  int32_t v[SCANV_E];
+  scanv_load(in, n, i0, v);
+  int64_t t = 0;
+#pragma unroll
+  for (int j = 0; j < SCANV_E; ++j) t += v[j];
+  int64_t total;
+  scanv_block_excl(t, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ __launch_bounds__(SCANV_T) void k_scanv_apply(const int32_t *in, int64_t *out, int64_t n,
+                                                         const int64_t *sums) {
+  const int64_t i0 = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCANV_E;
+  int32_t v[SCANV_E];
+  scanv_load(in, n, i0, v);
+  int64_t t = 0;
+#pragma unroll
+  for (int j = 0; j < SCANV_E; ++j) t += v[j];
+  int64_t total;
+  int64_t run = sums[blockIdx.x] + scanv_block_excl(t, &total);
+  if (i0 + SCANV_E <= n) {
+    longlong2 *p = reinterpret_cast<longlong2 *>(out + i0);
+#pragma unroll
+    for (int j = 0; j < SCANV_E / 2; ++j) {
+      longlong2 q;
+      q.x = run;
+      run += v[2 * j];
+      q.y = run;
+      run += v[2 * j + 1];
+      p[j] = q;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < SCANV_E; ++j) {
+      if (i0 + j < n) out[i0 + j] = run;
+      run += v[j];
+    }
+  }
+}
+
 }  // namespace
 
 psi_status scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *d_total, cudaStream_t s) {
   return scan_impl<int64_t>(in, out, n, d_total, s);
 }
 psi_status scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *d_total, cudaStream_t s) {
-  return scan_impl<int32_t>(in, out, n, d_total, s);
+  // the vector form needs 16-byte aligned arrays (the library's own are)
+  if (n <= 0 || (reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+    return scan_impl<int32_t>(in, out, n, d_total, s);
+  const int64_t nb = ceil_div(n, SCAN_CHUNK);
+  Buf<int64_t> sums;
+  psi_status st = sums.alloc(nb, s);
+  if (st) return st;
+  PSI_LAUNCH_NAMED("k_scan_reduce", k_scanv_reduce, (unsigned)nb, SCANV_T, 0, s, in, n, sums.p);
+  PSI_LAUNCH(k_scan_sums, 1, 1024, 0, s, sums.p, nb, d_total);
+  PSI_LAUNCH_NAMED("k_scan_apply", k_scanv_apply, (unsigned)nb, SCANV_T, 0, s, in, out, n, sums.p);
+  PSI_CK(cudaGetLastError());
+  return PSI_OK;
 }
 
 }  // namespace psi
