@@ -708,9 +708,11 @@ __device__ __forceinline__ void prefix_network(uint64_t (&k)[kPrefixShort], uint
 // registers with a network sized to the run.
 constexpr int kPrefixU = 4;
 
-__global__ __launch_bounds__(256) void k_prefix_runs(uint64_t *keys, uint32_t *vals, const uint32_t *ids, int64_t n,
-                                                     int low, int64_t *long_runs, uint32_t *n_long,
-                                                     int64_t cap_long) {
+// (4 blocks of 256 per SM: 64 registers, no spills; the run path's networks
+// would otherwise take 80)
+__global__ __launch_bounds__(256, 4) void k_prefix_runs(uint64_t *keys, uint32_t *vals, const uint32_t *ids,
+                                                        int64_t n, int low, int64_t *long_runs, uint32_t *n_long,
+                                                        int64_t cap_long) {
   const int64_t chunk = (int64_t)blockDim.x * kPrefixU;
   for (int64_t b0 = (int64_t)blockIdx.x * chunk; b0 < n; b0 += (int64_t)gridDim.x * chunk) {
     uint64_t kp[kPrefixU], kc[kPrefixU], kn[kPrefixU];
