@@ -350,7 +350,14 @@ struct LinkArgs {
   int D, bits;
   NodeArrays nodes;
   int32_t *leaf_node;
+  // internal nodes whose boxes are left to k_boxes: depth l's listed at
+  // wide[doff[l] ...], wide_cnt[l] of them
+  int32_t *wide, *wide_cnt;
 };
+
+// An internal node spanning at most kDirectLeaves leaves has its box computed
+// from the leaf boxes by k_link; the others by k_boxes, depth by depth.
+constexpr int kDirectLeaves = 32;
 
 template <int D>
 __global__ void k_link(LinkArgs a) {
@@ -373,9 +380,16 @@ __global__ void k_link(LinkArgs a) {
       a.leaf_node[i] = (int32_t)x;
       continue;
     }
-    // first leaf past this node's cell
+    // first leaf past this node's cell: galloping from i + 1 (most cells
+    // span few leaves), then a binary search in the last step's range
     const uint64_t lim = (prefix + 1) << sh;  // sh <= 63 for an internal node
-    int64_t lo = i + 1, hi = a.L;
+    int64_t lo = i + 1, hi = i + 1, step = 1;  // leaves before lo are inside the cell
+    while (hi < a.L && a.pl.key[hi] < lim) {
+      lo = hi + 1;
+      hi = lo + step;
+      step <<= 1;
+    }
+    hi = min(hi, a.L);
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
       if (a.pl.key[mid] < lim)
@@ -395,58 +409,83 @@ __global__ void k_link(LinkArgs a) {
         q = mid;
     }
     const int64_t c0 = p;
-    q = s1;
-    while (p < q) {
-      const int64_t mid = (p + q) >> 1;
-      if ((int64_t)a.nleaf[mid] < e)
-        p = mid + 1;
-      else
-        q = mid;
-    }
+    // the first child's first leaf is i; at most 2^D children in all
+    while (p < s1 && (int64_t)a.nleaf[p] < e) ++p;
     a.nodes.ref[x] = (uint32_t)c0;
     a.nodes.kids[x] = (int32_t)(p - c0);
     a.nodes.cnt[x] = (int32_t)(a.E[e] - a.E[i]);
+    if (e - i <= kDirectLeaves) {
+      int32_t blo[D], bhi[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        blo[d] = INT32_MAX;
+        bhi[d] = INT32_MIN;
+      }
+      for (int64_t j = i; j < e; ++j)
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          blo[d] = min(blo[d], a.pl.lo[d][j]);
+          bhi[d] = max(bhi[d], a.pl.hi[d][j]);
+        }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        a.nodes.lo[d][x] = blo[d];
+        a.nodes.hi[d][x] = bhi[d];
+      }
+    } else {
+      a.wide[a.doff[l] + atomicAdd(&a.wide_cnt[l], 1)] = (int32_t)x;
+    }
   }
 }
 
-// Boxes of the internal nodes of one depth from their children (leaf boxes
-// come with the leaf records): an 8-lane group per node (at most 2^D <= 8
-// children), four nodes per warp.
+// Boxes of the listed internal nodes of one depth (list[0, cnt)) from their
+// children, which are leaves (boxes from the leaf records), nodes spanning few
+// leaves (boxes set by k_link) or listed nodes of the depth below (boxes set
+// by the previous launch): an 8-lane group per node (at most 2^D <= 8
+// children), four nodes per warp and kBoxRounds such rounds per pass, whose
+// loads are issued together.
+constexpr int kBoxRounds = 4;
+
 template <int D>
-__global__ void k_boxes(NodeArrays nodes, int64_t off, int64_t cnt) {
+__global__ void k_boxes(NodeArrays nodes, const int32_t *list, int64_t cnt) {
   const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
   const unsigned gmask = 0xFFu << (g * 8);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x0 = off + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; x0 < off + cnt;
-       x0 += warps * 4) {
-    const int64_t x = x0 + g;
-    const bool valid = x < off + cnt;
-    const int nk = valid ? nodes.kids[x] : 0;
-    int32_t lo[D], hi[D];
+  for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (4 * kBoxRounds); j0 < cnt;
+       j0 += warps * (4 * kBoxRounds)) {
+    int nk[kBoxRounds];
+    uint32_t r[kBoxRounds];
+    int64_t xs[kBoxRounds];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      lo[d] = INT32_MAX;
-      hi[d] = INT32_MIN;
+    for (int u = 0; u < kBoxRounds; ++u) {
+      const int64_t j = j0 + u * 4 + g;
+      xs[u] = j < cnt ? list[j] : -1;
     }
-    if (gl < nk) {
-      const uint32_t r = nodes.ref[x];
+#pragma unroll
+    for (int u = 0; u < kBoxRounds; ++u) {
+      nk[u] = xs[u] >= 0 ? nodes.kids[xs[u]] : 0;
+      r[u] = xs[u] >= 0 ? nodes.ref[xs[u]] : 0;
+    }
+    int32_t lo[kBoxRounds][D], hi[kBoxRounds][D];
+#pragma unroll
+    for (int u = 0; u < kBoxRounds; ++u)
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        lo[d] = nodes.lo[d][r + gl];
-        hi[d] = nodes.hi[d][r + gl];
+        lo[u][d] = gl < nk[u] ? nodes.lo[d][r[u] + gl] : INT32_MAX;
+        hi[u][d] = gl < nk[u] ? nodes.hi[d][r[u] + gl] : INT32_MIN;
       }
-    }
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      lo[d] = __reduce_min_sync(gmask, lo[d]);
-      hi[d] = __reduce_max_sync(gmask, hi[d]);
-    }
-    if (nk > 0 && gl == 0)
+    for (int u = 0; u < kBoxRounds; ++u) {
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        nodes.lo[d][x] = lo[d];
-        nodes.hi[d][x] = hi[d];
+        const int32_t l = __reduce_min_sync(gmask, lo[u][d]);
+        const int32_t h = __reduce_max_sync(gmask, hi[u][d]);
+        if (nk[u] > 0 && gl == 0) {
+          nodes.lo[d][xs[u]] = l;
+          nodes.hi[d][xs[u]] = h;
+        }
       }
+    }
   }
 }
 
@@ -636,6 +675,7 @@ struct SegArgs {
   uint32_t *n_huge;
   const int64_t *K;  // global delete: exclusive scan of keep over all old points
   const int32_t *bleaf;  // leaf of each sorted batch entry
+  const int32_t *block_leaf;  // global paths: leaf holding old position b * kGlobBlock
   int64_t m;
   uint64_t *wkey;  // work array
   int32_t *wmask;
@@ -851,6 +891,27 @@ __device__ __forceinline__ int64_t last_le(const int64_t *v, int64_t lo, int64_t
   return lo;
 }
 
+// Threads per block of the global kernels; their blocks take kGlobBlock
+// consecutive old positions per round.
+constexpr int kGlobBlock = 256;
+
+// block_leaf[b] = the leaf holding old position b * kGlobBlock (b < nb): the
+// leaf range of each block of the global kernels without a search over E.
+__global__ void k_block_leaf(const int64_t *E, int64_t L, int64_t nb, int32_t *block_leaf) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = E[x], e = E[x + 1];
+    for (int64_t b = (s + kGlobBlock - 1) / kGlobBlock; b < nb && b * kGlobBlock < e; ++b)
+      block_leaf[b] = (int32_t)x;
+  }
+}
+
+// Leaf range [xr[0], xr[1]) holding the old positions [q0, q0 + kGlobBlock).
+__device__ __forceinline__ void glob_block_range(const SegArgs &a, int64_t q0, int64_t *xr) {
+  const int64_t b = q0 / kGlobBlock;
+  xr[0] = a.block_leaf[b];
+  xr[1] = q0 + kGlobBlock < a.n ? a.block_leaf[b + 1] + 1 : a.L;
+}
+
 // Global insert (every leaf dirty, one segment, no context: the work array is
 // the fresh pool's keys themselves): a thread per old point and per batch entry, each
 // placing itself among the other side of its leaf by a binary search (a
@@ -863,10 +924,7 @@ __global__ void k_glob_insert(SegArgs a) {
   const int64_t total = a.n + a.m;
   for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x; q0 < total; q0 += (int64_t)gridDim.x * blockDim.x) {
     __syncthreads();
-    if (threadIdx.x == 0 && q0 < a.n) {
-      xr[0] = last_le(a.E, 0, a.L, q0);
-      xr[1] = last_le(a.E, 0, a.L, min(a.n - 1, q0 + (int64_t)blockDim.x - 1)) + 1;
-    }
+    if (threadIdx.x == 0 && q0 < a.n) glob_block_range(a, q0, xr);
     __syncthreads();
     const int64_t q = q0 + threadIdx.x;
     if (q >= total) continue;
@@ -923,10 +981,7 @@ __global__ void k_glob_delete(SegArgs a) {
   __shared__ int64_t xr[2];
   for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < a.n; p0 += (int64_t)gridDim.x * blockDim.x) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-      xr[0] = last_le(a.E, 0, a.L, p0);
-      xr[1] = last_le(a.E, 0, a.L, min(a.n - 1, p0 + (int64_t)blockDim.x - 1)) + 1;
-    }
+    if (threadIdx.x == 0) glob_block_range(a, p0, xr);
     __syncthreads();
     const int64_t p = p0 + threadIdx.x;
     if (p >= a.n || !a.keep[p]) continue;
@@ -1079,22 +1134,27 @@ static psi_status porth_nodes(psi_index *ix, cudaStream_t s) {
 
   if ((st = alloc_nodes(ix->nodes, D, N, true, s))) return st;
   if ((st = DevMem::alloc((void **)&ix->leaf_node, sizeof(int32_t) * L, s))) return st;
-  LinkArgs la{r.keys, r.vals, d_doff.p, E.p, ix->pl, L, N, D, bits, ix->nodes, ix->leaf_node};
+  Buf<int32_t> wide, wide_cnt;
+  if ((st = wide.alloc(N, s)) || (st = wide_cnt.alloc(64, s))) return st;
+  PSI_CK(cudaMemsetAsync(wide_cnt.p, 0, sizeof(int32_t) * 64, s));
+  LinkArgs la{r.keys, r.vals, d_doff.p, E.p, ix->pl, L, N, D, bits, ix->nodes, ix->leaf_node, wide.p, wide_cnt.p};
   if (D == 2)
     PSI_LAUNCH_NAMED("k_link", k_link<2>, grid_for(N), 256, 0, s, la);
   else
     PSI_LAUNCH_NAMED("k_link", k_link<3>, grid_for(N), 256, 0, s, la);
-  int maxd = 0;
-  for (int l = 0; l <= bits; ++l)
-    if (h_hist[l]) maxd = l;
-  for (int l = maxd - 1; l >= 0; --l) {  // leaves carry their boxes; internal nodes bottom up
-    const int64_t cnt = doff[l + 1] - doff[l];
+  // the boxes of the listed (wide) internal nodes, depth by depth bottom up
+  int32_t h_wide[64];
+  PSI_CK(cudaMemcpyAsync(h_wide, wide_cnt.p, sizeof(h_wide), cudaMemcpyDeviceToHost, s));
+  PSI_CK(cudaStreamSynchronize(s));
+  for (int l = bits; l >= 0; --l) {
+    const int64_t cnt = h_wide[l];
     if (!cnt) continue;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cnt, 32), (int64_t)num_sms() * 32));
+    const int g = (int)std::max<int64_t>(
+        1, std::min<int64_t>(ceil_div(cnt, 8 * 4 * kBoxRounds), (int64_t)num_sms() * 32));
     if (D == 2)
-      PSI_LAUNCH_NAMED("k_boxes", k_boxes<2>, g, 256, 0, s, ix->nodes, doff[l], cnt);
+      PSI_LAUNCH_NAMED("k_boxes", k_boxes<2>, g, 256, 0, s, ix->nodes, wide.p + doff[l], cnt);
     else
-      PSI_LAUNCH_NAMED("k_boxes", k_boxes<3>, g, 256, 0, s, ix->nodes, doff[l], cnt);
+      PSI_LAUNCH_NAMED("k_boxes", k_boxes<3>, g, 256, 0, s, ix->nodes, wide.p + doff[l], cnt);
   }
   ix->nnodes = N;
   ix->root = 0;
@@ -1372,16 +1432,23 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
   a.bleaf = bleaf.p;
   a.m = m;
   if (hc > 0) PSI_LAUNCH(k_seg_context, warp_grid(G), 256, 0, s, a);
+  Buf<int32_t> block_leaf;
+  if (global && n > 0) {
+    const int64_t nb = ceil_div(n, kGlobBlock);
+    if ((st = block_leaf.alloc(nb, s))) return st;
+    PSI_LAUNCH(k_block_leaf, grid_for(L), 256, 0, s, E.p, L, nb, block_leaf.p);
+    a.block_leaf = block_leaf.p;
+  }
   if (global && insert) {
     if (D == 2)
-      PSI_LAUNCH_NAMED("k_glob_insert", k_glob_insert<2>, grid_for(n + m), 256, 0, s, a);
+      PSI_LAUNCH_NAMED("k_glob_insert", k_glob_insert<2>, grid_for(n + m, kGlobBlock), kGlobBlock, 0, s, a);
     else
-      PSI_LAUNCH_NAMED("k_glob_insert", k_glob_insert<3>, grid_for(n + m), 256, 0, s, a);
+      PSI_LAUNCH_NAMED("k_glob_insert", k_glob_insert<3>, grid_for(n + m, kGlobBlock), kGlobBlock, 0, s, a);
   } else if (global) {
     if (D == 2)
-      PSI_LAUNCH_NAMED("k_glob_delete", k_glob_delete<2>, grid_for(n), 256, 0, s, a);
+      PSI_LAUNCH_NAMED("k_glob_delete", k_glob_delete<2>, grid_for(n, kGlobBlock), kGlobBlock, 0, s, a);
     else
-      PSI_LAUNCH_NAMED("k_glob_delete", k_glob_delete<3>, grid_for(n), 256, 0, s, a);
+      PSI_LAUNCH_NAMED("k_glob_delete", k_glob_delete<3>, grid_for(n, kGlobBlock), kGlobBlock, 0, s, a);
   } else if (D == 2) {
     PSI_LAUNCH_NAMED("k_seg_small", k_seg_small<2>, warp_grid(ceil_div(L, 32)), 256, 0, s, a);
     PSI_LAUNCH_NAMED("k_seg_big", k_seg_big<2>, num_sms() * 8, 256, 0, s, a);

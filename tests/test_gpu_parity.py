@@ -196,6 +196,8 @@ def test_build_prefix_sort_runs(kind, dim, bits, n):
     launched = psi.profile_dump()
     psi.profile_enable(False)
     assert "k_prefix_runs" in launched and "k_prefix_long" in launched  # the prefix sort was taken
+    # input in random order: the gather reads points and ids from packed records
+    assert any(name.startswith("k_pack_records") for name in launched)
     o = O.Index(p, ids, dim=dim, kind=KIND[kind], phi=32, bits=bits)
     if kind == "porth":
         check_porth_nodes(ix, o)
