@@ -579,45 +579,60 @@ __global__ void k_dirty_flags(const int64_t *ex, int64_t L, int32_t *dirty, int3
   }
 }
 
-// Delete: every stored point of a leaf with a slice whose (key, id) occurs in
-// the slice with the same coordinates is removed (keep[E[x] + s] = 0); rem[x]
-// counts them.  A warp per leaf with a slice.
-template <int D>
-__global__ void k_pdel_marks(PLeaves pl, Pool pool, const int64_t *E, const int32_t *sbeg, const int32_t *send,
-                             int64_t L, const uint64_t *bkeys, const uint32_t *rid, const int32_t *rpt,
-                             int32_t *keep, int32_t *rem, unsigned long long *deleted) {
+// Delete, part 1 (local batches): keep = 1 for every stored point of a leaf
+// with a slice (the others are not read), rem = 0.  The warps walk the sorted
+// batch in chunks of 32 entries and take the leaf of every entry that starts
+// a slice, a lane per point.
+__global__ void k_pdel_fill(PLeaves pl, const int64_t *E, const int32_t *bleaf, int64_t m, int32_t *keep) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  uint32_t removed = 0;
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < L; x += warps) {
-    const int32_t b = sbeg[x], e = send[x];
-    if (e <= b) continue;
-    const uint32_t s0 = pl.ref[x];
-    const int c = pl.cnt[x];
-    int r = 0;
-    for (int s = lane; s < c; s += 32) {
-      const uint64_t k = pool.pkey[s0 + s];
-      const uint32_t id = pool.pid[s0 + s];
-      int32_t lo = b, hi = e;
-      while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (kid_less(bkeys[mid], rid[mid], k, id))
-          lo = mid + 1;
-        else
-          hi = mid;
-      }
-      bool hit = lo < e && bkeys[lo] == k && rid[lo] == id;
-      if (hit) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) hit &= rpt[(int64_t)lo * D + d] == pool.px[d][s0 + s];
-      }
-      keep[E[x] + s] = !hit;
-      r += hit;
+  for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < m; j0 += warps * 32) {
+    const int64_t jl = j0 + lane;
+    const int32_t xl = jl < m ? bleaf[jl] : -1;
+    uint32_t starts = __ballot_sync(0xFFFFFFFFu, jl < m && (jl == 0 || bleaf[jl - 1] != xl));
+    while (starts) {
+      const int64_t x = __shfl_sync(0xFFFFFFFFu, xl, __ffs(starts) - 1);
+      starts &= starts - 1;
+      const int64_t e0 = E[x];
+      const int c = pl.cnt[x];
+      for (int s = lane; s < c; s += 32) keep[e0 + s] = 1;
     }
-    r = __reduce_add_sync(0xFFFFFFFFu, r);
-    if (lane == 0) {
-      rem[x] = r;
-      removed += (uint32_t)r;
+  }
+}
+
+// Delete, part 2: a thread per sorted batch entry finds its (key, id) among
+// its leaf's points, which are in (key, id) order, by binary search; a stored
+// point with the same pair and coordinates is removed (keep = 0, rem[x] + 1).
+// A pair repeated in the batch (adjacent once sorted) deletes once: only its
+// first entry searches.
+template <int D>
+__global__ void k_pdel_marks(PLeaves pl, Pool pool, const int64_t *E, const int32_t *bleaf, int64_t m,
+                             const uint64_t *bkeys, const uint32_t *rid, const int32_t *rpt, int32_t *keep,
+                             int32_t *rem, unsigned long long *deleted) {
+  uint32_t removed = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = bkeys[j];
+    const uint32_t id = rid[j];
+    if (j > 0 && bkeys[j - 1] == k && rid[j - 1] == id) continue;
+    const int32_t x = bleaf[j];
+    const uint32_t s0 = pl.ref[x];
+    int lo = 0, hi = pl.cnt[x];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (kid_less(pool.pkey[s0 + mid], pool.pid[s0 + mid], k, id))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    bool hit = lo < pl.cnt[x] && pool.pkey[s0 + lo] == k && pool.pid[s0 + lo] == id;
+    if (hit) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) hit &= rpt[j * D + d] == pool.px[d][s0 + lo];
+    }
+    if (hit) {
+      keep[E[x] + lo] = 0;
+      atomicAdd(&rem[x], 1);
+      ++removed;
     }
   }
   block_count_add(deleted, removed);
@@ -1328,13 +1343,17 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
   }
   if (!insert) {
     if ((st = keep.alloc(n, s))) return st;
-    if (global) PSI_LAUNCH(k_fill1, grid_for(n), 256, 0, s, keep.p, n);  // every old point of a dirty leaf is read
+    if (global)  // every old point of a dirty leaf is read
+      PSI_LAUNCH(k_fill1, grid_for(n), 256, 0, s, keep.p, n);
+    else  // those of the leaves with a slice
+      PSI_LAUNCH(k_pdel_fill, warp_grid(ceil_div(m, 32)), 256, 0, s, ix->pl, E.p, bleaf.p, m, keep.p);
+    PSI_CK(cudaMemsetAsync(rem.p, 0, sizeof(int32_t) * L, s));
     if (D == 2)
-      PSI_LAUNCH_NAMED("k_pdel_marks", k_pdel_marks<2>, warp_grid(L), 256, 0, s, ix->pl, ix->pool, E.p, sbeg.p,
-                       send.p, L, br.keys, rid.p, rpt.p, keep.p, rem.p, del.p);
+      PSI_LAUNCH_NAMED("k_pdel_marks", k_pdel_marks<2>, grid_for(m), 256, 0, s, ix->pl, ix->pool, E.p, bleaf.p, m,
+                       br.keys, rid.p, rpt.p, keep.p, rem.p, del.p);
     else
-      PSI_LAUNCH_NAMED("k_pdel_marks", k_pdel_marks<3>, warp_grid(L), 256, 0, s, ix->pl, ix->pool, E.p, sbeg.p,
-                       send.p, L, br.keys, rid.p, rpt.p, keep.p, rem.p, del.p);
+      PSI_LAUNCH_NAMED("k_pdel_marks", k_pdel_marks<3>, grid_for(m), 256, 0, s, ix->pl, ix->pool, E.p, bleaf.p, m,
+                       br.keys, rid.p, rpt.p, keep.p, rem.p, del.p);
     PSI_LAUNCH(k_i64_from_u64, 1, 1, 0, s, del.p, tot.p + 3);
     if (d_deleted) PSI_CK(cudaMemcpyAsync(d_deleted, tot.p + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   }
