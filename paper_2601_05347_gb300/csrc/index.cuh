@@ -157,9 +157,12 @@ struct KnnSeed {
 
 // k-NN of nq queries, each starting at qroot[q] (or tv.root when qroot is
 // null), in the given query order; d_stats (or null) receives traversal counts;
-// leaf_limit >= 0 says the leaves are exactly the nodes [0, leaf_limit).
+// leaf_limit >= 0 says the leaves are exactly the nodes [0, leaf_limit);
+// porth says the tree is a P-Orth (nodes mix leaf and internal children,
+// leaves hold few points): popped nodes are re-checked and several small
+// leaves share a k-list merge.
 psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
                          const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status,
                          unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed,
-                         int64_t leaf_limit = -1);
+                         int64_t leaf_limit = -1, bool porth = false);
 }  // namespace psi

@@ -218,7 +218,7 @@ __global__ void k_knn_seed(const KnnSeed sd, const uint32_t *ref, const uint32_t
 // starts (so the order of the later pops matters little), and the search then
 // skips the seed leaves.  Seed (P-Orth): the leaf whose cell holds the query's
 // key (or the last leaf before it in key order), alone.
-template <int D, int KPL, bool STATS>
+template <int D, int KPL, bool STATS, bool BATCH>
 __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
   // internal nodes still to visit: (node, key, first child, children)
   __shared__ uint4 s_stk[QW][KSTACK];
@@ -351,19 +351,87 @@ __global__ __launch_bounds__(QW * 32) void k_knn(KnnArgs a, KnnStats stats) {
           __syncwarp();
         }
       }
-      while (ml) {
-        const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, (ml >> lane) & 1u ? key : 0xFFFFFFFFu);
-        if (mn > kdk) break;  // every remaining leaf is farther than the k-th distance
-        const int src = __ffs(__ballot_sync(0xFFFFFFFFu, ((ml >> lane) & 1u) && key == mn)) - 1;
-        ml &= ~(1u << src);
-        const uint32_t lref = __shfl_sync(0xFFFFFFFFu, cref, src);
-        const int lcnt = __shfl_sync(0xFFFFFFFFu, ccnt, src);
-        knn_scan_slots<D, KPL>(t, lref, lcnt, qc, kl, a.k);
-        kdk = order_key(kl.kd);
-        if (STATS) {
-          ++n_leaf;
-          n_pts += lcnt;
+      // BATCH (P-Orth): leaves in batches, taken nearest first (each still
+      // within the k-th distance of that moment) while their points fit one
+      // round of 32 lanes, then scanned together, so that small leaves (a few
+      // points each in 3D) share one k-list merge; a leaf of more than 32
+      // points is a batch of its own, scanned in rounds.  Otherwise (SPaC,
+      // whose leaves fill a round) a leaf at a time, each re-checked.
+      if constexpr (!BATCH) {
+        while (ml) {
+          const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, (ml >> lane) & 1u ? key : 0xFFFFFFFFu);
+          if (mn > kdk) break;  // every remaining leaf is farther than the k-th distance
+          const int src = __ffs(__ballot_sync(0xFFFFFFFFu, ((ml >> lane) & 1u) && key == mn)) - 1;
+          ml &= ~(1u << src);
+          const uint32_t lref = __shfl_sync(0xFFFFFFFFu, cref, src);
+          const int lcnt = __shfl_sync(0xFFFFFFFFu, ccnt, src);
+          knn_scan_slots<D, KPL>(t, lref, lcnt, qc, kl, a.k);
+          kdk = order_key(kl.kd);
+          if (STATS) {
+            ++n_leaf;
+            n_pts += lcnt;
+          }
         }
+      }
+      while (BATCH && ml) {
+        uint32_t bl = 0;  // the batch's children (lanes)
+        int tot = 0;
+        while (ml) {
+          const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, (ml >> lane) & 1u ? key : 0xFFFFFFFFu);
+          if (mn > kdk) {  // every remaining leaf is farther than the k-th distance
+            ml = 0;
+            break;
+          }
+          const int src = __ffs(__ballot_sync(0xFFFFFFFFu, ((ml >> lane) & 1u) && key == mn)) - 1;
+          const int c = __shfl_sync(0xFFFFFFFFu, ccnt, src);
+          if (bl && tot + c > 32) break;
+          bl |= 1u << src;
+          ml &= ~(1u << src);
+          tot += c;
+          if (STATS) {
+            ++n_leaf;
+            n_pts += c;
+          }
+          if (tot >= 32) break;
+        }
+        if (!bl) break;
+        // batch position of each member leaf's first point (in lane order)
+        const int mine = (bl >> lane) & 1u ? ccnt : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int excl = incl - mine;
+        for (int r = 0; r < tot; r += 32) {
+          const int p = r + lane;
+          uint32_t slot = 0;
+          bool valid = false;
+          for (uint32_t mb = bl; mb; mb &= mb - 1) {
+            const int b = __ffs(mb) - 1;
+            const int eb = __shfl_sync(0xFFFFFFFFu, excl, b);
+            const int cb = __shfl_sync(0xFFFFFFFFu, ccnt, b);
+            const uint32_t rb = __shfl_sync(0xFFFFFFFFu, cref, b);
+            if (p >= eb && p < eb + cb) {
+              valid = true;
+              slot = rb + (uint32_t)(p - eb);
+            }
+          }
+          int64_t d2 = INT64_MAX;
+          uint32_t id = 0xFFFFFFFFu;
+          if (valid) {
+            id = t.pid[slot];
+            d2 = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              const int32_t dd = t.px[d][slot] - qc[d];  // exact: both in [0, 2^31)
+              d2 += (int64_t)dd * dd;
+            }
+          }
+          klist_offer(kl, valid && kl.admits(d2, id), d2, id, a.k);
+        }
+        kdk = order_key(kl.kd);
       }
     };
     if (root >= 0) {
@@ -858,7 +926,8 @@ psi_status query_order(const psi_index *ix, const int32_t *q, int64_t nq, QueryO
 
 psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k, const uint32_t *order,
                          const int32_t *qroot, int D, uint32_t *out_id, int64_t *out_d2, int *status,
-                         unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed, int64_t leaf_limit) {
+                         unsigned long long *d_stats, cudaStream_t s, const KnnSeed &seed, int64_t leaf_limit,
+                         bool porth) {
   if (nq == 0) return PSI_OK;
   KnnArgs a{tv, q, nq, k, order, qroot, seed, leaf_limit, out_id, out_d2, status};
   KnnStats stats{d_stats};
@@ -889,7 +958,7 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
     // leaf and internal children at every depth.  SPaC's seeds make the
     // bounds nearly final before the first push, and there the larger stack
     // entries cost more than the re-check saves.
-    const bool recheck = leaf_limit < 0;
+    const bool recheck = porth;
     if (D == 2) {
       if (recheck) KNN_GROUP(2, true);
       else KNN_GROUP(2, false);
@@ -901,14 +970,22 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
     PSI_CK(cudaGetLastError());
     return PSI_OK;
   }
-#define KNN_CASE(DD, KK)                                                                           \
-  do {                                                                                             \
-    if (d_stats)                                                                                   \
-      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn<DD, KK, true>), resident_query_grid(k_knn<DD, KK, true>, nq), \
-                       QW * 32, 0, s, a, stats);                                                   \
-    else                                                                                           \
-      PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK, false>), resident_query_grid(k_knn<DD, KK, false>, nq),     \
-                       QW * 32, 0, s, a, stats);                                                   \
+#define KNN_CASE1(DD, KK, BB)                                                                          \
+  do {                                                                                                 \
+    if (d_stats)                                                                                       \
+      PSI_LAUNCH_NAMED("k_knn_stats", (k_knn<DD, KK, true, BB>),                                       \
+                       resident_query_grid(k_knn<DD, KK, true, BB>, nq), QW * 32, 0, s, a, stats);     \
+    else                                                                                               \
+      PSI_LAUNCH_NAMED("k_knn", (k_knn<DD, KK, false, BB>), resident_query_grid(k_knn<DD, KK, false, BB>, nq), \
+                       QW * 32, 0, s, a, stats);                                                       \
+  } while (0)
+  // small leaves in batches where leaves are not one round each (P-Orth)
+#define KNN_CASE(DD, KK)                  \
+  do {                                    \
+    if (porth)                            \
+      KNN_CASE1(DD, KK, true);            \
+    else                                  \
+      KNN_CASE1(DD, KK, false);           \
   } while (0)
   if (D == 2) {
     if (kpl == 1) KNN_CASE(2, 1);
@@ -920,6 +997,7 @@ psi_status run_knn_roots(const TreeView &tv, const int32_t *q, int64_t nq, int k
     else KNN_CASE(3, 4);
   }
 #undef KNN_CASE
+#undef KNN_CASE1
   PSI_CK(cudaGetLastError());
   return PSI_OK;
 }
@@ -946,7 +1024,7 @@ psi_status run_knn(const psi_index *ix, const int32_t *q, int64_t nq, int k, uin
     }
   }
   return run_knn_roots(ix->view(), q, nq, k, qo.order, nullptr, ix->D, out_id, out_d2, ix->d_status, d_stats, s,
-                       seed, ix->cfg.kind == PSI_PORTH ? -1 : ix->L);
+                       seed, ix->cfg.kind == PSI_PORTH ? -1 : ix->L, ix->cfg.kind == PSI_PORTH);
 }
 
 psi_status run_range_count(const psi_index *ix, const int32_t *boxes, int64_t nq, int64_t *counts, cudaStream_t s) {
