@@ -137,20 +137,26 @@ class Clocks:
 # per-kernel algorithmic byte model (2D, per launch)
 # ---------------------------------------------------------------------------
 PACK_MIN = 1 << 22  # smallest encoding sort the library packs
+PREFIX_BITS = 48    # top key bits sorted in the library's prefix mode
 
 
-def sort_bytes(items: int, key_bits: int, stored: bool, dim: int = 2, local: bool = False) -> tuple[float, float]:
+def sort_bytes(items: int, key_bits: int, stored: bool, dim: int = 2, local: bool = False,
+               prefix: bool = False) -> tuple[float, float]:
     """Algorithmic HBM bytes of one encoding key sort (8-bit digits): (histogram
     pass, all digit passes).  Mirrors the library's plan: Hilbert keys are
-    computed once in the histogram pass and written (stored); a sort of at
-    least PACK_MIN pairs whose input is locally ordered packs, once a position
-    and the unsorted key bits fit 64 bits, both into one word at pass pk: the
-    middle passes move 8-B words and the last pass writes the pairs again."""
+    computed once in the histogram pass and written (stored); with `prefix`
+    only the top PREFIX_BITS key bits are sorted (the library's prefix mode,
+    then a scan of the sorted keys puts runs of equal top bits in order); a
+    sort of at least PACK_MIN pairs whose input is locally ordered packs, once
+    a position and the unsorted key bits fit 64 bits, both into one word at
+    pass pk: the middle passes move 8-B words and the last pass writes the
+    pairs again."""
     pt = 4 * dim
-    passes = (key_bits + 7) // 8
+    sorted_bits = min(key_bits, PREFIX_BITS) if prefix else key_bits
+    passes = (sorted_bits + 7) // 8
     vbits = max(1, (items - 1).bit_length())
     p = 1
-    while p < passes and vbits + key_bits - 8 * (p + 1) > 64:
+    while p < passes and vbits + sorted_bits - 8 * (p + 1) > 64:
         p += 1
     pk = p if (local and items >= PACK_MIN and p + 2 <= passes - 1) else passes
     hist = pt + (8 if stored else 0)
@@ -169,19 +175,21 @@ def sort_bytes(items: int, key_bits: int, stored: bool, dim: int = 2, local: boo
     return float(hist * items), float(per * items)
 
 
-def kernel_bytes(name: str, w, launches: int) -> float | None:
+def kernel_bytes(name: str, w, launches: int, prefix_build: bool = False) -> float | None:
     """Algorithmic HBM bytes of all launches of a kernel in one step.
 
     k_onesweep, k_sort_hist  the encoding key sorts of the step (`sort_bytes`):
-                 build (walk-ordered: packs), insert batch, delete batch
-                 (60-bit Hilbert keys, below PACK_MIN) and the query order (top
-                 48 key bits, queries in random order: pairs throughout).
+                 build (walk-ordered: packs; `prefix_build`: the step's launches
+                 show that the build took the prefix mode), insert batch, delete
+                 batch (60-bit Hilbert keys, below PACK_MIN and the prefix mode's
+                 minimum) and the query order (top 48 key bits, queries in random
+                 order: pairs throughout).
     k_leaf_gather reads sorted key + position (12 B) and gathers point + id
                  (12 B), writes x, y, id, key (20 B): 44 B per point.
     """
     n, mi, md = w["n"], w["m_ins"], w["m_del"]
-    sorts = [sort_bytes(n, 60, True, local=True), sort_bytes(mi, 60, True), sort_bytes(md, 60, True),
-             sort_bytes(w["n_knn"], 48, True)]
+    sorts = [sort_bytes(n, 60, True, local=True, prefix=prefix_build), sort_bytes(mi, 60, True),
+             sort_bytes(md, 60, True), sort_bytes(w["n_knn"], 48, True)]
     if name == "k_onesweep":
         return sum(b for _, b in sorts)
     if name == "k_sort_hist":
@@ -418,7 +426,7 @@ def run_ours(args):
                            "bytes_per_launch": tr["lts_bytes"],
                            "peak_source": "measured in this run: L2-resident copy (24 MB buffer, read + write bytes)"}
             return r
-        b = kernel_bytes(name, w, cnt // max(args.steps, 1))
+        b = kernel_bytes(name, w, cnt // max(args.steps, 1), prefix_build="k_prefix_runs" in prof)
         if b is None:
             return None
         ach = b / (per_step_ms * 1e-3) / 1e9

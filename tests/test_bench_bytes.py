@@ -40,3 +40,41 @@ def test_query_order_sort_is_six_passes_of_pairs():
     # 1e7 queries in random order, top 48 key bits
     hist, passes = bench.sort_bytes(10_000_000, 48, True)
     assert passes == 10_000_000 * (20 + 5 * 24)
+
+
+def test_prefix_mode_build_sorts_six_digits():
+    # the top 48 of 60 key bits: pass 0 reads the written key and writes a pair (20); with
+    # 27-bit positions 27 + 48 - 8 * 2 <= 64, so pass 1 packs (pairs in 12, words out 8);
+    # passes 2..4 move words (16); pass 5 reads a word, gathers the key and writes a pair (28)
+    n = 100_000_000
+    hist, passes = bench.sort_bytes(n, 60, True, local=True, prefix=True)
+    assert hist == n * 16
+    assert passes == n * (20 + 20 + 3 * 16 + 28)
+
+
+def test_prefix_mode_is_counted_only_when_the_build_took_it():
+    w = {"n": 100_000_000, "m_ins": 1_000_000, "m_del": 1_000_000, "n_knn": 10_000_000}
+    full = bench.kernel_bytes("k_onesweep", w, 28)
+    pref = bench.kernel_bytes("k_onesweep", w, 26, prefix_build=True)
+    assert full - pref == 100_000_000 * ((20 + 24 + 20 + 4 * 16 + 28) - (20 + 20 + 3 * 16 + 28))
+
+
+def test_traffic_records_parse_and_name_their_summaries():
+    import os
+    path = os.path.join(bench.ROOT, "profiles", "traffic.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kernel, digest, workload, dram, lts, src = line.rstrip("\n").split("\t")[:6]
+        assert kernel in bench.KERNEL_SOURCES and len(digest) == 16 and workload
+        assert float(dram) > 0 and (lts == "-" or float(lts) > 0)
+        assert os.path.exists(os.path.join(bench.ROOT, src))
+
+
+def test_source_digest_follows_the_bytes(tmp_path, monkeypatch):
+    a = tmp_path / "a.cu"
+    a.write_text("x")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d1 = bench.source_digest(["a.cu"])
+    a.write_text("y")
+    assert bench.source_digest(["a.cu"]) != d1
