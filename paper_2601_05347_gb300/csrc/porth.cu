@@ -523,12 +523,18 @@ __global__ void k_route(const uint64_t *bkeys, int64_t m, const uint64_t *lkey, 
 }
 
 // Slice [sbeg[x], send[x]) of the sorted batch routed to leaf x.
-__global__ void k_pslices(const int32_t *bleaf, int64_t m, int32_t *sbeg, int32_t *send) {
+__global__ void k_pslices(const int32_t *bleaf, int64_t m, int32_t *sbeg, int32_t *send,
+                          unsigned long long *n_reached) {
+  uint32_t reached = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t j = bleaf[i];
-    if (i == 0 || bleaf[i - 1] != j) sbeg[j] = (int32_t)i;
+    if (i == 0 || bleaf[i - 1] != j) {
+      sbeg[j] = (int32_t)i;
+      ++reached;
+    }
     if (i == m - 1 || bleaf[i + 1] != j) send[j] = (int32_t)(i + 1);
   }
+  block_count_add(n_reached, reached);
 }
 
 // The leaf holding old position p: the last leaf y with E[y] <= p (leaves
@@ -1319,8 +1325,11 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
     return st;
   PSI_CK(cudaMemsetAsync(tot.p, 0, sizeof(int64_t) * 4, s));
   // A batch of more than 1/16 of the points reaches nearly every leaf: it is
-  // merged with all of them into a fresh pool (one segment, no garbage).
-  const bool global = m * 16 > n;
+  // merged with all of them into a fresh pool (one segment, no garbage).  So
+  // is a batch of more than 1/256 of them that reaches (has points routed to)
+  // more than a quarter of the leaves, since the leaves within phi + 1 points
+  // of those make nearly all of them dirty.
+  bool global = m * 16 > n;
   if (D == 2)
     PSI_LAUNCH_NAMED("k_prec", k_prec<2>, grid_for(m), 256, 0, s, br.vals, pts, ids, m, rid.p, rpt.p);
   else
@@ -1332,7 +1341,15 @@ static psi_status porth_update(psi_index *ix, const int32_t *pts, const uint32_t
   PSI_CK(cudaMemsetAsync(nc.p + L, 0, sizeof(int32_t), s));
   if ((st = scan_i32_to_i64(ix->pl.cnt, E.p, L, E.p + L, s))) return st;
   PSI_LAUNCH(k_route, grid_for(m), 256, 0, s, br.keys, m, ix->pl.key, L, bleaf.p);
-  PSI_LAUNCH(k_pslices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p);
+  PSI_CK(cudaMemsetAsync(del.p, 0, sizeof(unsigned long long), s));
+  PSI_LAUNCH(k_pslices, grid_for(m), 256, 0, s, bleaf.p, m, sbeg.p, send.p, del.p);
+  if (!global && m * 256 > n) {
+    unsigned long long reached = 0;
+    PSI_CK(cudaMemcpyAsync(&reached, del.p, sizeof(reached), cudaMemcpyDeviceToHost, s));
+    PSI_CK(cudaStreamSynchronize(s));
+    global = reached * 4 > (unsigned long long)L;
+  }
+  PSI_CK(cudaMemsetAsync(del.p, 0, sizeof(unsigned long long), s));
   if (global) {
     PSI_LAUNCH(k_all_dirty, grid_for(L), 256, 0, s, L, dirty.p, sstart.p);
   } else {
