@@ -199,6 +199,31 @@ def kernel_bytes(name: str, w, launches: int, prefix_build: bool = False) -> flo
     return None
 
 
+def touched_leaves(ix, pts) -> int:
+    """Leaves of a SPaC index that an update batch reaches: each batch point
+    goes to the last leaf whose separator key is at most its curve key (keys
+    from the library's encoder; routing by key alone, so ties between equal
+    keys are approximated).  Setup for the update byte model, untimed."""
+    import torch
+    from paper_2601_05347_gb300 import psi
+    sep = ix.leaves()["sep_key"]
+    keys = psi.encode(pts, kind="spac_h").to(torch.int64)
+    leaf = torch.clamp(torch.searchsorted(sep, keys, right=True) - 1, min=0)
+    return int(torch.unique(leaf).numel())
+
+
+def update_bytes(m: int, L: int, touched: int, phi: int = 32, F: int = 32) -> float:
+    """Algorithmic HBM bytes of a SPaC batch insert or delete of m points into
+    L leaves: the batch's key sort (60-bit keys, `sort_bytes`), 8 B per
+    separator and batch key to locate the slices, every touched leaf's 2 phi
+    slots of (key, id, point) read and written (24 B each), every batch point
+    read once as a record and written (or matched) once (24 + 24 B), and the
+    summary tree above the leaves rebuilt (32 B per node, L F / (F - 1) nodes)."""
+    hist, passes = sort_bytes(m, 60, True)
+    return (hist + passes + 8.0 * (L + m) + touched * 2 * phi * 24 * 2 + m * 24.0 * 2
+            + L * 32.0 * F / (F - 1))
+
+
 def source_digest(files) -> str:
     """Short digest of kernel source files: a stored ncu figure applies only to the source it was taken on."""
     import hashlib
@@ -351,8 +376,12 @@ def run_ours(args):
     phase_ms = {p: t[i + 1] for i, p in enumerate(phases)}
 
     # traversal counters of one instrumented k-NN pass over the same queries
+    # (and, untimed, the leaves each update batch reaches, for the update byte model)
     ixs = psi.Index(d["pts"], d["ids"], kind="spac_h", leaf_size=32)
+    touched = {"insert": touched_leaves(ixs, d["ins"])}
+    n_leaves = ixs.num_leaves
     ixs.insert(d["ins"], d["ins_ids"])
+    touched["delete"] = touched_leaves(ixs, d["del_pts"])
     ixs.delete(d["del_pts"], d["del_ids"], ndel)
     _, _, kstats = ixs.knn_stats(d["q"], k)
     ixs.close()
@@ -486,6 +515,13 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roof,
         "roofline_sort_pass": roof_hbm,
+        "roofline_updates": {
+            ph: {"bound": "hbm", "algorithmic_bytes": round(update_bytes(w[mk], n_leaves, touched[ph])),
+                 "touched_leaves": touched[ph], "leaves": n_leaves,
+                 "achieved": round(update_bytes(w[mk], n_leaves, touched[ph]) / (phase_ms[ph] * 1e-3) / 1e9, 1),
+                 "peak": hbm_peak, "unit": "GB/s",
+                 "frac": round(update_bytes(w[mk], n_leaves, touched[ph]) / (phase_ms[ph] * 1e-3) / 1e9 / hbm_peak, 4)}
+            for ph, mk in (("insert", "m_ins"), ("delete", "m_del"))},
         "kernels": top,
         "knn_traversal_per_query": {kk: round(v / max(kstats["queries"], 1), 3) for kk, v in kstats.items()
                                     if kk != "queries"},

@@ -78,3 +78,11 @@ def test_source_digest_follows_the_bytes(tmp_path, monkeypatch):
     d1 = bench.source_digest(["a.cu"])
     a.write_text("y")
     assert bench.source_digest(["a.cu"]) != d1
+
+
+def test_update_bytes_add_up():
+    # a 1e6-point batch into 3.125e6 leaves touching 5e5 of them, leaves of 32, fan-out 32
+    m, L, t = 1_000_000, 3_125_000, 500_000
+    hist, passes = bench.sort_bytes(m, 60, True)
+    want = hist + passes + 8 * (L + m) + t * 64 * 24 * 2 + m * 48 + L * 32 * 32 / 31
+    assert abs(bench.update_bytes(m, L, t) - want) < 1e-3
