@@ -708,11 +708,17 @@ __device__ __forceinline__ void prefix_network(uint64_t (&k)[kPrefixShort], uint
 // registers with a network sized to the run.
 constexpr int kPrefixU = 4;
 
-// (4 blocks of 256 per SM: 64 registers, no spills; the run path's networks
-// would otherwise take 80)
-__global__ __launch_bounds__(256, 4) void k_prefix_runs(uint64_t *keys, uint32_t *vals, const uint32_t *ids,
-                                                        int64_t n, int low, int64_t *long_runs, uint32_t *n_long,
-                                                        int64_t cap_long) {
+// Run starts of a prefix sort's output: positions i whose top bits (key >>
+// low) equal those of i + 1 but not those of i - 1, listed in no particular
+// order in starts[0, *n_starts) (kPrefixU elements per thread, loads issued
+// together; a block appends the starts of a round with one atomic, its warps'
+// offsets from a scan in shared memory).  A count above cap means the list
+// is incomplete and k_prefix_runs scans every position.
+__global__ __launch_bounds__(256) void k_prefix_starts(const uint64_t *keys, int64_t n, int low, int32_t *starts,
+                                                       unsigned long long *n_starts, int64_t cap) {
+  __shared__ uint32_t wcount[8];
+  __shared__ unsigned long long bbase;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t chunk = (int64_t)blockDim.x * kPrefixU;
   for (int64_t b0 = (int64_t)blockIdx.x * chunk; b0 < n; b0 += (int64_t)gridDim.x * chunk) {
     uint64_t kp[kPrefixU], kc[kPrefixU], kn[kPrefixU];
@@ -723,52 +729,100 @@ __global__ __launch_bounds__(256, 4) void k_prefix_runs(uint64_t *keys, uint32_t
       kp[u] = i > 0 && i < n ? keys[i - 1] : ~0ull;
       kn[u] = i + 1 < n ? keys[i + 1] : ~0ull;
     }
+    uint32_t bal[kPrefixU];
+    bool st[kPrefixU];
+    uint32_t wtot = 0;
 #pragma unroll
     for (int u = 0; u < kPrefixU; ++u) {
       const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
       const uint64_t p = kc[u] >> low;
       const bool with_prev = i > 0 && i < n && (kp[u] >> low) == p;
       const bool with_next = i + 1 < n && (kn[u] >> low) == p;
-      if (!with_next || with_prev) continue;  // not the start of a run of two or more
-      uint64_t k[kPrefixShort];
-      uint32_t v[kPrefixShort];
-      k[0] = kc[u];
-      k[1] = kn[u];
-      v[0] = vals[i];
-      v[1] = vals[i + 1];
-      uint64_t k2 = i + 2 < n ? keys[i + 2] : ~0ull;
-      int len = 2;
-#pragma unroll
-      for (int j = 2; j < kPrefixShort; ++j) {
-        k[j] = ~0ull;  // past the run: above every key, never moved before a member
-        v[j] = 0;
-        if (len == j) {
-          const uint64_t kj = j == 2 ? k2 : (i + j < n ? keys[i + j] : ~0ull);
-          if (i + j < n && (kj >> low) == p) {
-            k[j] = kj;
-            v[j] = vals[i + j];
-            ++len;
-          }
-        }
-      }
-      if (len == kPrefixShort && i + kPrefixShort < n && (keys[i + kPrefixShort] >> low) == p) {
-        const uint32_t slot = atomicAdd(n_long, 1u);
-        if (slot < cap_long) long_runs[slot] = i;
-        continue;
-      }
-      if (len == 2)
-        prefix_network<2>(k, v, len, ids);
-      else if (len <= 4)
-        prefix_network<4>(k, v, len, ids);
-      else
-        prefix_network<kPrefixShort>(k, v, len, ids);
-#pragma unroll
-      for (int j = 0; j < kPrefixShort; ++j)
-        if (j < len) {
-          keys[i + j] = k[j];
-          vals[i + j] = v[j];
-        }
+      st[u] = with_next && !with_prev;
+      bal[u] = __ballot_sync(0xFFFFFFFFu, st[u]);
+      wtot += __popc(bal[u]);
     }
+    if (lane == 0) wcount[w] = wtot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t t = 0;
+      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += wcount[j];
+      bbase = t ? atomicAdd(n_starts, (unsigned long long)t) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long off = bbase;
+    for (int j = 0; j < w; ++j) off += wcount[j];
+#pragma unroll
+    for (int u = 0; u < kPrefixU; ++u) {
+      if (st[u]) {
+        const unsigned long long pos = off + __popc(bal[u] & lanemask_lt());
+        if (pos < (unsigned long long)cap) starts[pos] = (int32_t)(b0 + (int64_t)u * blockDim.x + threadIdx.x);
+      }
+      off += __popc(bal[u]);
+    }
+    __syncthreads();
+  }
+}
+
+// The run of equal top bits starting at position i (a run start): runs of up
+// to kPrefixShort elements are sorted by (key, id) in registers by a network
+// sized to the run; longer ones are listed for k_prefix_long.
+__device__ __forceinline__ void prefix_fix_run(uint64_t *keys, uint32_t *vals, const uint32_t *ids, int64_t n,
+                                               int low, int64_t i, int64_t *long_runs, uint32_t *n_long,
+                                               int64_t cap_long) {
+  const uint64_t p = keys[i] >> low;
+  uint64_t k[kPrefixShort];
+  uint32_t v[kPrefixShort];
+  int len = 0;
+#pragma unroll
+  for (int j = 0; j < kPrefixShort; ++j) {
+    k[j] = ~0ull;  // past the run: above every key, never moved before a member
+    v[j] = 0;
+    if (len == j && i + j < n) {
+      const uint64_t kj = keys[i + j];
+      if ((kj >> low) == p) {
+        k[j] = kj;
+        v[j] = vals[i + j];
+        ++len;
+      }
+    }
+  }
+  if (len == kPrefixShort && i + kPrefixShort < n && (keys[i + kPrefixShort] >> low) == p) {
+    const uint32_t slot = atomicAdd(n_long, 1u);
+    if (slot < cap_long) long_runs[slot] = i;
+    return;
+  }
+  if (len == 2)
+    prefix_network<2>(k, v, len, ids);
+  else if (len <= 4)
+    prefix_network<4>(k, v, len, ids);
+  else
+    prefix_network<kPrefixShort>(k, v, len, ids);
+#pragma unroll
+  for (int j = 0; j < kPrefixShort; ++j)
+    if (j < len) {
+      keys[i + j] = k[j];
+      vals[i + j] = v[j];
+    }
+}
+
+// A thread per listed run start (or, when the list overflowed, per position,
+// taking those that start a run).
+__global__ __launch_bounds__(256) void k_prefix_runs(uint64_t *keys, uint32_t *vals, const uint32_t *ids, int64_t n,
+                                                     int low, const int32_t *starts,
+                                                     const unsigned long long *n_starts, int64_t cap,
+                                                     int64_t *long_runs, uint32_t *n_long, int64_t cap_long) {
+  const unsigned long long ns = *n_starts;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (ns <= (unsigned long long)cap) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < (int64_t)ns; r += stride)
+      prefix_fix_run(keys, vals, ids, n, low, starts[r], long_runs, n_long, cap_long);
+    return;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t p = keys[i] >> low;
+    if (i + 1 < n && (keys[i + 1] >> low) == p && !(i > 0 && (keys[i - 1] >> low) == p))
+      prefix_fix_run(keys, vals, ids, n, low, i, long_runs, n_long, cap_long);
   }
 }
 
@@ -1134,8 +1188,15 @@ psi_status sort_pairs(const EncodeSpec &enc, const uint64_t *keys_in, const uint
       const size_t smem = (size_t)kSmemRun * (sizeof(uint64_t) + 2 * sizeof(uint32_t));
       PSI_CK(cudaFuncSetAttribute(k_prefix_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       const int gr = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256 * kPrefixU), (int64_t)num_sms() * 8));
-      PSI_LAUNCH(k_prefix_runs, gr, 256, 0, s, out->keys, out->vals, tie_ids, n, out->prefix_low, runs.p, nlong.p,
-                 cap_plong);
+      // the run starts first (a light scan), then a thread per run
+      const int64_t cap_starts = n / 4 + 1;
+      Buf<int32_t> starts;
+      Buf<unsigned long long> nst;
+      if ((st = starts.alloc(cap_starts, s)) || (st = nst.alloc(1, s))) return st;
+      PSI_CK(cudaMemsetAsync(nst.p, 0, sizeof(unsigned long long), s));
+      PSI_LAUNCH(k_prefix_starts, gr, 256, 0, s, out->keys, n, out->prefix_low, starts.p, nst.p, cap_starts);
+      PSI_LAUNCH(k_prefix_runs, num_sms() * 8, 256, 0, s, out->keys, out->vals, tie_ids, n, out->prefix_low, starts.p,
+                 nst.p, cap_starts, runs.p, nlong.p, cap_plong);
       PSI_LAUNCH(k_prefix_long, num_sms(), 1024, smem, s, out->keys, out->vals, tie_ids, n, out->prefix_low, runs.p,
                  nlong.p, cap_plong);
     } else {
