@@ -710,9 +710,9 @@ constexpr int kPrefixU = 4;
 
 // Run starts of a prefix sort's output: positions i whose top bits (key >>
 // low) equal those of i + 1 but not those of i - 1, listed in no particular
-// order in starts[0, *n_starts) (kPrefixU elements per thread, loads issued
-// together; a block appends the starts of a round with one atomic, its warps'
-// offsets from a scan in shared memory).  A count above cap means the list
+// order in starts[0, *n_starts) (kPrefixU consecutive elements per thread;
+// a block appends the starts of a round with one atomic, its warps' offsets
+// from a scan in shared memory).  A count above cap means the list
 // is incomplete and k_prefix_runs scans every position.
 __global__ __launch_bounds__(256) void k_prefix_starts(const uint64_t *keys, int64_t n, int low, int32_t *starts,
                                                        unsigned long long *n_starts, int64_t cap) {
@@ -721,23 +721,32 @@ __global__ __launch_bounds__(256) void k_prefix_starts(const uint64_t *keys, int
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t chunk = (int64_t)blockDim.x * kPrefixU;
   for (int64_t b0 = (int64_t)blockIdx.x * chunk; b0 < n; b0 += (int64_t)gridDim.x * chunk) {
-    uint64_t kp[kPrefixU], kc[kPrefixU], kn[kPrefixU];
+    // kPrefixU consecutive keys per thread (two 16-byte loads) and one
+    // neighbour on each side
+    const int64_t i0 = b0 + (int64_t)threadIdx.x * kPrefixU;
+    uint64_t kc[kPrefixU + 2];
+    if ((reinterpret_cast<uintptr_t>(keys) & 15) == 0 && i0 + kPrefixU <= n) {
+      const ulonglong2 *v = reinterpret_cast<const ulonglong2 *>(keys + i0);
+      const ulonglong2 a = v[0], b = v[1];
+      kc[1] = a.x;
+      kc[2] = a.y;
+      kc[3] = b.x;
+      kc[4] = b.y;
+    } else {
 #pragma unroll
-    for (int u = 0; u < kPrefixU; ++u) {
-      const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
-      kc[u] = i < n ? keys[i] : ~0ull;
-      kp[u] = i > 0 && i < n ? keys[i - 1] : ~0ull;
-      kn[u] = i + 1 < n ? keys[i + 1] : ~0ull;
+      for (int u = 0; u < kPrefixU; ++u) kc[u + 1] = i0 + u < n ? keys[i0 + u] : ~0ull;
     }
+    kc[0] = i0 > 0 && i0 < n ? keys[i0 - 1] : ~0ull;
+    kc[kPrefixU + 1] = i0 + kPrefixU < n ? keys[i0 + kPrefixU] : ~0ull;
     uint32_t bal[kPrefixU];
     bool st[kPrefixU];
     uint32_t wtot = 0;
 #pragma unroll
     for (int u = 0; u < kPrefixU; ++u) {
-      const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
-      const uint64_t p = kc[u] >> low;
-      const bool with_prev = i > 0 && i < n && (kp[u] >> low) == p;
-      const bool with_next = i + 1 < n && (kn[u] >> low) == p;
+      const int64_t i = i0 + u;
+      const uint64_t p = kc[u + 1] >> low;
+      const bool with_prev = i > 0 && i < n && (kc[u] >> low) == p;
+      const bool with_next = i + 1 < n && (kc[u + 2] >> low) == p;
       st[u] = with_next && !with_prev;
       bal[u] = __ballot_sync(0xFFFFFFFFu, st[u]);
       wtot += __popc(bal[u]);
@@ -756,7 +765,7 @@ __global__ __launch_bounds__(256) void k_prefix_starts(const uint64_t *keys, int
     for (int u = 0; u < kPrefixU; ++u) {
       if (st[u]) {
         const unsigned long long pos = off + __popc(bal[u] & lanemask_lt());
-        if (pos < (unsigned long long)cap) starts[pos] = (int32_t)(b0 + (int64_t)u * blockDim.x + threadIdx.x);
+        if (pos < (unsigned long long)cap) starts[pos] = (int32_t)(i0 + u);
       }
       off += __popc(bal[u]);
     }
