@@ -124,6 +124,55 @@ __device__ __forceinline__ uint64_t hilbert2_key(const uint8_t *tab8, uint32_t x
 // Bytes of shared memory for the curve tables of either dimension.
 constexpr int kCurveTabBytes = 2048;
 
+// Five levels per step (used where a block can spare 8 KB of shared memory):
+// (state, 5 x-bits, 5 y-bits) -> (10 key bits, next state << 10) as uint16,
+// 4096 entries; call with all threads, then sync.
+constexpr int kHilbert5TabBytes = 4096 * 2;
+__device__ __forceinline__ void hilbert5_table_init(uint8_t *tab8) {
+  uint16_t *tab = reinterpret_cast<uint16_t *>(tab8);
+  for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
+    uint32_t st = (uint32_t)e >> 10, xb = ((uint32_t)e >> 5) & 31u, yb = (uint32_t)e & 31u, d = 0;
+    for (int l = 4; l >= 0; --l) d = (d << 2) | hilbert_step(st, (xb >> l) & 1u, (yb >> l) & 1u);
+    tab[e] = (uint16_t)(d | (st << 10));
+  }
+}
+
+// The key of hilbert2_key, five levels per step: walked as a curve of P = 30
+// levels (six steps) when bits <= 30, else of 35 levels (seven steps; the
+// top bits that fall off the 64-bit key are digits of padding levels, 0),
+// with x and y exchanged when P - bits is odd (each padding level is quadrant
+// 0, which exchanges the axes).
+__device__ __forceinline__ uint64_t hilbert2_key5(const uint8_t *tab8, uint32_t x, uint32_t y, int bits) {
+  const uint16_t *tab = reinterpret_cast<const uint16_t *>(tab8);
+  const uint32_t m = (1u << bits) - 1u;  // bits <= 31
+  x &= m;
+  y &= m;
+  const int P = bits <= 30 ? 30 : 35;
+  if ((P - bits) & 1) {
+    const uint32_t t = x;
+    x = y;
+    y = t;
+  }
+  uint64_t key = 0;
+  uint32_t st = 0;  // state << 10
+  if (P == 30) {
+#pragma unroll
+    for (int s = 25; s >= 0; s -= 5) {
+      const uint32_t e = tab[st | (((x >> s) & 31u) << 5) | ((y >> s) & 31u)];
+      key = (key << 10) | (e & 1023u);
+      st = e & 0xC00u;
+    }
+  } else {
+#pragma unroll
+    for (int s = 30; s >= 0; s -= 5) {
+      const uint32_t e = tab[st | (((x >> s) & 31u) << 5) | ((y >> s) & 31u)];
+      key = (key << 10) | (e & 1023u);
+      st = e & 0xC00u;
+    }
+  }
+  return key;
+}
+
 // The 3D automaton state: perm index (0..5) x 16 + reflections x 2 + parity;
 // permutations in lexicographic order (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0).
 __device__ __forceinline__ void perm3_of(int idx, int *p) {

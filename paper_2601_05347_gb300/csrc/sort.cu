@@ -171,11 +171,17 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   const int secs = passes + (ex.hist_alt ? 1 : 0);
   uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][secs][RADIX]
   uint8_t *htab = smem_raw + sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX;
-  uint32_t *shll = reinterpret_cast<uint32_t *>(htab + kCurveTabBytes);  // [kHllRegs] when ex.hll
+  // 2D Hilbert keys five levels per table step (8 KB table), others as in point_key
+  constexpr bool H5 = MODE == 1 && D == 2 && CURVE == 1;
+  constexpr int TAB = H5 ? kHilbert5TabBytes : kCurveTabBytes;
+  uint32_t *shll = reinterpret_cast<uint32_t *>(htab + TAB);  // [kHllRegs] when ex.hll
   for (int i = threadIdx.x; i < R::HIST_PARTS * secs * R::RADIX; i += blockDim.x) shp[i] = 0;
   if (ex.hll)
     for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) shll[i] = 0;
-  if (MODE == 1) curve_table_init<D, CURVE>(htab);
+  if (H5)
+    hilbert5_table_init(htab);
+  else if (MODE == 1)
+    curve_table_init<D, CURVE>(htab);
   __syncthreads();
   bool bad_any = false;
   uint32_t n_near = 0;  // input neighbours (i, i + 1) whose keys agree above near_shift
@@ -205,7 +211,13 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
 #pragma unroll
       for (int u = 0; u < HIST_U; ++u) {
         bool bad;
-        k[u] = point_key<D, CURVE>(htab, c[u], bits, bad) >> key_shift;
+        if constexpr (H5) {
+          const uint32_t lim = 1u << bits;  // bits <= 31
+          bad = (uint32_t)c[u][0] >= lim || (uint32_t)c[u][D - 1] >= lim;
+          k[u] = hilbert2_key5(htab, (uint32_t)c[u][0], (uint32_t)c[u][D - 1], bits) >> key_shift;
+        } else {
+          k[u] = point_key<D, CURVE>(htab, c[u], bits, bad) >> key_shift;
+        }
         if (ok[u]) {
           bad_any |= bad;
           if (kst) kst[i0 + (int64_t)u * blockDim.x + threadIdx.x] = k[u];
@@ -910,7 +922,8 @@ static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_
                               unsigned long long *near = nullptr, int near_shift = 0, HistExtra ex = HistExtra()) {
   using R = Radix<RB>;
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
-  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX + kCurveTabBytes +
+  const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX +
+                      (MODE == 1 && D == 2 && CURVE == 1 ? kHilbert5TabBytes : kCurveTabBytes) +
                       (ex.hll ? sizeof(uint32_t) * kHllRegs : 0);
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // all blocks resident at once (the grid-stride rounds stay balanced)
