@@ -236,6 +236,47 @@ __device__ __forceinline__ uint64_t hilbert3_key(const uint8_t *tab8, uint32_t x
   return d;
 }
 
+// Two levels per step (where a block can spare 13.5 KB of shared memory):
+// the one-level table (768 entries) followed by a table of 96 states x 64
+// octant pairs, (next state after both levels << 6 | the two digits), built
+// from it.  Call with all threads (it syncs inside), then sync.
+constexpr int kHilbert3x2TabBytes = 768 * 2 + 96 * 64 * 2;
+__device__ __forceinline__ void hilbert3x2_table_init(uint8_t *tab8) {
+  hilbert3_table_init(tab8);
+  __syncthreads();
+  const uint16_t *t1 = reinterpret_cast<const uint16_t *>(tab8);
+  uint16_t *t2 = reinterpret_cast<uint16_t *>(tab8) + 768;
+  for (int e = threadIdx.x; e < 96 * 64; e += blockDim.x) {
+    const int st = e >> 6, o1 = (e >> 3) & 7, o2 = e & 7;
+    const uint32_t a = t1[st * 8 + o1];
+    const uint32_t b = t1[(a >> 6) * 8 + o2];
+    t2[e] = (uint16_t)(((b >> 6) << 6) | ((a & 7u) << 3) | (b & 7u));
+  }
+}
+
+// hilbert3_key with the two-level table: an odd top level alone, then pairs.
+__device__ __forceinline__ uint64_t hilbert3_key2(const uint8_t *tab8, uint32_t x, uint32_t y, uint32_t z,
+                                                  int bits) {
+  const uint16_t *t1 = reinterpret_cast<const uint16_t *>(tab8);
+  const uint16_t *t2 = t1 + 768;
+  const uint64_t m = morton3_key(x, y, z);
+  uint32_t st = 0;  // state
+  uint64_t d = 0;
+  int l = bits - 1;
+  if (bits & 1) {
+    const uint32_t e = t1[st * 8 + (uint32_t)((m >> (3 * l)) & 7u)];
+    d = e & 7u;
+    st = e >> 6;
+    --l;
+  }
+  for (; l > 0; l -= 2) {  // levels l and l - 1
+    const uint32_t e = t2[st * 64 + (uint32_t)((m >> (3 * (l - 1))) & 63u)];
+    d = (d << 6) | (e & 63u);
+    st = e >> 6;
+  }
+  return d;
+}
+
 // Curve table of the (D, CURVE) key; call with all threads, then sync.
 template <int D, int CURVE>
 __device__ __forceinline__ void curve_table_init(uint8_t *tab) {

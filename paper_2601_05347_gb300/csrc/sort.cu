@@ -171,15 +171,19 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
   const int secs = passes + (ex.hist_alt ? 1 : 0);
   uint32_t *shp = reinterpret_cast<uint32_t *>(smem_raw);  // [HIST_PARTS][secs][RADIX]
   uint8_t *htab = smem_raw + sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX;
-  // 2D Hilbert keys five levels per table step (8 KB table), others as in point_key
+  // Hilbert keys with larger tables than point_key's: 2D five levels per step
+  // (8 KB), 3D two levels per step (13.5 KB)
   constexpr bool H5 = MODE == 1 && D == 2 && CURVE == 1;
-  constexpr int TAB = H5 ? kHilbert5TabBytes : kCurveTabBytes;
+  constexpr bool H3 = MODE == 1 && D == 3 && CURVE == 1;
+  constexpr int TAB = H5 ? kHilbert5TabBytes : H3 ? kHilbert3x2TabBytes : kCurveTabBytes;
   uint32_t *shll = reinterpret_cast<uint32_t *>(htab + TAB);  // [kHllRegs] when ex.hll
   for (int i = threadIdx.x; i < R::HIST_PARTS * secs * R::RADIX; i += blockDim.x) shp[i] = 0;
   if (ex.hll)
     for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) shll[i] = 0;
   if (H5)
     hilbert5_table_init(htab);
+  else if (H3)
+    hilbert3x2_table_init(htab);
   else if (MODE == 1)
     curve_table_init<D, CURVE>(htab);
   __syncthreads();
@@ -215,6 +219,10 @@ __global__ __launch_bounds__(256) void k_sort_hist(const uint64_t *kin, const in
           const uint32_t lim = 1u << bits;  // bits <= 31
           bad = (uint32_t)c[u][0] >= lim || (uint32_t)c[u][D - 1] >= lim;
           k[u] = hilbert2_key5(htab, (uint32_t)c[u][0], (uint32_t)c[u][D - 1], bits) >> key_shift;
+        } else if constexpr (H3) {
+          const uint32_t lim = 1u << bits;
+          bad = (uint32_t)c[u][0] >= lim || (uint32_t)c[u][1] >= lim || (uint32_t)c[u][D - 1] >= lim;
+          k[u] = hilbert3_key2(htab, (uint32_t)c[u][0], (uint32_t)c[u][1], (uint32_t)c[u][D - 1], bits) >> key_shift;
         } else {
           k[u] = point_key<D, CURVE>(htab, c[u], bits, bad) >> key_shift;
         }
@@ -923,7 +931,8 @@ static psi_status launch_hist(const uint64_t *kin, const EncodeSpec &enc, int64_
   using R = Radix<RB>;
   auto kern = k_sort_hist<MODE, D, CURVE, RB>;
   const size_t smem = sizeof(uint32_t) * R::HIST_PARTS * (passes + 1) * R::RADIX +
-                      (MODE == 1 && D == 2 && CURVE == 1 ? kHilbert5TabBytes : kCurveTabBytes) +
+                      (MODE == 1 && CURVE == 1 ? (D == 2 ? kHilbert5TabBytes : kHilbert3x2TabBytes)
+                                               : kCurveTabBytes) +
                       (ex.hll ? sizeof(uint32_t) * kHllRegs : 0);
   if (smem > 48 * 1024) PSI_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // all blocks resident at once (the grid-stride rounds stay balanced)
