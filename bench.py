@@ -209,7 +209,9 @@ def touched_leaves(ix, pts) -> int:
     sep = ix.leaves()["sep_key"]
     keys = psi.encode(pts, kind="spac_h").to(torch.int64)
     leaf = torch.clamp(torch.searchsorted(sep, keys, right=True) - 1, min=0)
-    return int(torch.unique(leaf).numel())
+    hit = torch.zeros(sep.numel(), dtype=torch.int32, device=sep.device)
+    hit[leaf] = 1  # a scatter, not a sort: every reached leaf once
+    return int(hit.sum())
 
 
 def update_bytes(m: int, L: int, touched: int, phi: int = 32, F: int = 32) -> float:
