@@ -81,17 +81,27 @@ psi_status psi_build(const psi_config *cfg, const int32_t *d_pts, const uint32_t
  * key-sorted and each point is routed to the leaf whose key range holds it.
  * SPaC: a leaf whose points fit its block (2*leaf_size slots) takes them
  * unsorted; an overflowing leaf is merged with its slice and re-wrapped into
- * leaves of at most leaf_size.  P-Orth: a leaf that exceeds leaf_size is split
- * by the next key bits, so the tree equals a fresh build of the same points.
- * Synchronises `stream` once to size the new leaf list. */
+ * leaves of at most leaf_size.  P-Orth: the leaves within leaf_size + 1
+ * points (in key order) of an inserted point are rebuilt, a leaf that exceeds
+ * leaf_size being split by the next key bits, and the nodes re-derived, so the
+ * tree equals a fresh build of the same points (a batch above n/16, or above
+ * n/256 reaching more than a quarter of the leaves, rebuilds every leaf).
+ * Synchronises `stream`: SPaC once, to size the new leaf list; P-Orth a few
+ * times, to size the rebuilt leaf and node lists. */
 psi_status psi_insert_batch(psi_index *ix, const int32_t *d_pts, const uint32_t *d_ids, int64_t m,
                             void *stream);
 
 /* Batch deletion (Sec 4.2 deletion paragraph; Sec 3.2).  Removes every live
  * point whose coordinates AND id equal a batch entry; absent entries are
- * ignored.  d_num_deleted (device int64, may be NULL) receives the number of
- * points removed.  Empty leaves are dropped; P-Orth subtrees left with at most
- * leaf_size points are flattened into one leaf.  Synchronises `stream` once. */
+ * ignored, a repeated entry deletes once.  d_num_deleted (device int64, may be
+ * NULL) receives the number of points removed.  SPaC: touched leaves are
+ * compacted and empty ones dropped; then every run of consecutive leaves
+ * holding fewer than max(1, leaf_size / 2) points is joined with the leaf
+ * after it (a run at the end with nothing after it, alone) and re-wrapped
+ * into balanced leaves, so every leaf but the last keeps at least that many.
+ * P-Orth: subtrees left with at most leaf_size points are flattened into one
+ * leaf (the tree equals a fresh build).  Synchronises `stream`: SPaC once, or
+ * twice when leaves are re-wrapped; P-Orth a few times. */
 psi_status psi_delete_batch(psi_index *ix, const int32_t *d_pts, const uint32_t *d_ids, int64_t m,
                             int64_t *d_num_deleted, void *stream);
 
