@@ -36,7 +36,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // (key, id) lexicographic order
 // Adds the sum of v over all threads of the block to *ctr with one global
