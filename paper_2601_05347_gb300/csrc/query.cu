@@ -776,9 +776,16 @@ __device__ __forceinline__ bool point_in(const TreeView &t, uint32_t slot, const
 }
 
 // EMIT = false: count; EMIT = true: write ids.
+// One warp per box.  The internal nodes the box reaches wait on a stack as
+// (first child, children | INSIDE), taken from their parent's expansion, so a
+// pop reads no node record.  Expanding a node loads every child's record and
+// box in one round of loads; internal children are pushed, and leaf children
+// are scanned at once (slot range and count already in registers): a leaf
+// costs one dependent load of its points instead of a trip through the stack.
+// The count pass adds the count of a node inside the box without descending.
 template <int D, bool EMIT>
 __global__ __launch_bounds__(QW * 32) void k_range(RangeArgs a) {
-  __shared__ uint32_t s_node[QW][STACK];
+  __shared__ uint2 s_node[QW][STACK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nw = (int64_t)gridDim.x * QW;
   const TreeView &t = a.t;
@@ -791,59 +798,110 @@ __global__ __launch_bounds__(QW * 32) void k_range(RangeArgs a) {
     }
     int64_t acc = 0;                               // count pass: per-lane partial
     int64_t cursor = EMIT ? a.offsets[q] : 0;      // emit pass: warp-uniform
+    // the root enters as the one child of a virtual node
     int sp = 0;
     if (t.root >= 0) {
-      const int rel = box_relation<D>(t, (uint32_t)t.root, blo, bhi);
-      if (rel == 2 && !EMIT) {
-        if (lane == 0) acc += t.cnt[t.root];
-      } else if (rel != 0) {
-        if (lane == 0) s_node[w][0] = (uint32_t)t.root | (rel == 2 ? INSIDE : 0u);
-        sp = 1;
-      }
+      if (lane == 0) s_node[w][0] = make_uint2((uint32_t)t.root, 1u);
+      sp = 1;
     }
     __syncwarp();
     while (sp > 0) {
       --sp;
-      const uint32_t e = s_node[w][sp];
+      const uint2 e = s_node[w][sp];
       __syncwarp();
-      const uint32_t node = e & ~INSIDE;
-      const bool inside = (e & INSIDE) != 0;
-      const int nk = t.kids[node];
-      if (nk == 0) {
-        const uint32_t s0 = t.ref[node];
-        const int cnt = t.cnt[node];
-        for (int b = 0; b < cnt; b += 32) {
-          const int s = b + lane;
-          const bool hit = s < cnt && (inside || point_in<D>(t, s0 + (uint32_t)s, blo, bhi));
-          if (!EMIT) {
-            acc += hit;
-          } else {
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
-            if (hit) a.out_ids[cursor + __popc(m & lanemask_lt())] = t.pid[s0 + s];
-            cursor += __popc(m);
+      const uint32_t c0 = e.x;
+      const int nk = (int)(e.y & ~INSIDE);
+      const bool inside = (e.y & INSIDE) != 0;
+      // children per node: at most 32 (SPaC fanout <= 32, P-Orth 2^D <= 8)
+      if (nk > 32 && lane == 0) atomicOr(a.status, ST_STACK);
+      bool ok = false, lf = false;
+      int rel = 0, ccnt = 0, ck = 0;
+      uint32_t cref = 0;
+      if (lane < nk) {
+        const uint32_t c = c0 + (uint32_t)lane;
+        ck = t.kids[c];
+        cref = t.ref[c];
+        ccnt = t.cnt[c];
+        rel = inside ? 2 : box_relation<D>(t, c, blo, bhi);
+        lf = ck == 0;
+        if (rel == 2 && !EMIT)
+          acc += ccnt;
+        else
+          ok = rel != 0;
+      }
+      // internal children: pushed
+      const bool push = ok && !lf;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, push);
+      if (sp + __popc(m) > STACK) {
+        if (lane == 0) atomicOr(a.status, ST_STACK);
+        break;
+      }
+      if (push) s_node[w][sp + __popc(m & lanemask_lt())] = make_uint2(cref, (uint32_t)ck | (rel == 2 ? INSIDE : 0u));
+      sp += __popc(m);
+      __syncwarp();
+      // leaf children: scanned now
+      uint32_t ml = __ballot_sync(0xFFFFFFFFu, ok && lf);
+      if constexpr (!EMIT) {
+        while (ml) {
+          const int src = __ffs(ml) - 1;
+          ml &= ml - 1;
+          const uint32_t s0 = __shfl_sync(0xFFFFFFFFu, cref, src);
+          const int cnt = __shfl_sync(0xFFFFFFFFu, ccnt, src);
+          const bool lin = __shfl_sync(0xFFFFFFFFu, rel, src) == 2;  // leaf box inside the query box
+          for (int b = 0; b < cnt; b += 32) {
+            const int s = b + lane;
+            acc += s < cnt && (lin || point_in<D>(t, s0 + (uint32_t)s, blo, bhi));
           }
         }
-        continue;
-      }
-      const uint32_t c0 = t.ref[node];
-      for (int cb = 0; cb < nk; cb += 32) {
-        uint32_t push = 0xFFFFFFFFu;
-        if (cb + lane < nk) {
-          const uint32_t c = c0 + (uint32_t)(cb + lane);
-          const int rel = inside ? 2 : box_relation<D>(t, c, blo, bhi);
-          if (rel == 2 && !EMIT)
-            acc += t.cnt[c];
-          else if (rel != 0)
-            push = c | (rel == 2 ? INSIDE : 0u);
+      } else {
+        // two leaves per round, each lane's points and ids loaded together, so
+        // that the loads of both leaves are in flight at once
+        while (ml) {
+          const int sa = __ffs(ml) - 1;
+          ml &= ml - 1;
+          const bool two = ml != 0;
+          const int sb = two ? __ffs(ml) - 1 : sa;
+          if (two) ml &= ml - 1;
+          const uint32_t s0a = __shfl_sync(0xFFFFFFFFu, cref, sa), s0b = __shfl_sync(0xFFFFFFFFu, cref, sb);
+          const int cna = __shfl_sync(0xFFFFFFFFu, ccnt, sa);
+          const int cnb = two ? __shfl_sync(0xFFFFFFFFu, ccnt, sb) : 0;
+          const bool lina = __shfl_sync(0xFFFFFFFFu, rel, sa) == 2, linb = __shfl_sync(0xFFFFFFFFu, rel, sb) == 2;
+          // the first 32 slots of both leaves
+          const bool va = lane < cna, vb = lane < cnb;
+          int32_t pa[D], pb[D];
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            pa[d] = va && !lina ? t.px[d][s0a + lane] : 0;
+            pb[d] = vb && !linb ? t.px[d][s0b + lane] : 0;
+          }
+          const uint32_t ia = va ? t.pid[s0a + lane] : 0u, ib = vb ? t.pid[s0b + lane] : 0u;
+          bool ha = va, hb = vb;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            ha &= lina || (pa[d] >= blo[d] && pa[d] <= bhi[d]);
+            hb &= linb || (pb[d] >= blo[d] && pb[d] <= bhi[d]);
+          }
+          const uint32_t ma = __ballot_sync(0xFFFFFFFFu, ha);
+          if (ha) a.out_ids[cursor + __popc(ma & lanemask_lt())] = ia;
+          cursor += __popc(ma);
+          const uint32_t mb = __ballot_sync(0xFFFFFFFFu, hb);
+          if (hb) a.out_ids[cursor + __popc(mb & lanemask_lt())] = ib;
+          cursor += __popc(mb);
+          // leaves of more than 32 points: their remaining slots
+#pragma unroll 1
+          for (int u = 0; u < 2; ++u) {
+            const uint32_t s0 = u ? s0b : s0a;
+            const int cnt = u ? cnb : cna;
+            const bool lin = u ? linb : lina;
+            for (int b = 32; b < cnt; b += 32) {
+              const int s = b + lane;
+              const bool hit = s < cnt && (lin || point_in<D>(t, s0 + (uint32_t)s, blo, bhi));
+              const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
+              if (hit) a.out_ids[cursor + __popc(hm & lanemask_lt())] = t.pid[s0 + s];
+              cursor += __popc(hm);
+            }
+          }
         }
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, push != 0xFFFFFFFFu);
-        if (sp + __popc(m) > STACK) {
-          if (lane == 0) atomicOr(a.status, ST_STACK);
-          break;
-        }
-        if (push != 0xFFFFFFFFu) s_node[w][sp + __popc(m & lanemask_lt())] = push;
-        sp += __popc(m);
-        __syncwarp();
       }
     }
     if (!EMIT) {
