@@ -420,6 +420,15 @@ def test_updates_match_oracle(kind, dim, bits, phi):
         assert (U32(gi) == oi2).all() and (gd.cpu().numpy() == od2).all()
         boxes = gen.square_boxes(300, dim, bits, 1 << (bits - 7), 9 + step)
         assert (ix.range_count(T(boxes)).cpu().numpy() == o.range_count(boxes)).all()
+        # range lists (and counts) of boxes centred on live points, over leaves of up
+        # to 2 phi points (more than one 32-lane round)
+        if len(live_p):
+            rb = gen.centred_boxes(live_p[gen.sample_with_replacement(len(live_p), 60, 29 + step)], 1 << (bits - 6),
+                                   bits)
+            assert (ix.range_count(T(rb)).cpu().numpy() == o.range_count(rb)).all()
+            off, rid = ix.range_report(T(rb), sort=True)
+            ooff, orid = o.range_report(rb)
+            assert (off.cpu().numpy() == ooff).all() and (U32(rid) == orid).all()
         if kind == "porth":
             check_porth_nodes(ix, o)
 
