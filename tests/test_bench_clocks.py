@@ -1,5 +1,6 @@
-"""The bench's clock record (host logic, no GPU): median SM clock under load,
-the maximum, and every throttle reason seen active in the samples."""
+"""The bench's host-side records (no GPU): the clock record (median SM clock
+under load, the maximum, every throttle reason seen active in the samples) and
+the host cores the CPU baseline may use."""
 import tempfile
 import types
 
@@ -38,3 +39,11 @@ def test_slowdowns_are_reported_and_unreadable_rows_skipped():
 def test_no_samples_gives_no_record():
     assert record([]) is None
     assert bench.Clocks(0).stop() is None  # never started
+
+
+def test_host_cores_lists_the_affinity_as_ranges(monkeypatch):
+    monkeypatch.setattr(bench.os, "sched_getaffinity", lambda pid: {0, 1, 2, 5, 7, 8}, raising=False)
+    monkeypatch.setattr(bench.os, "cpu_count", lambda: 16)
+    assert bench.host_cores() == (16, 6, "0-2,5,7-8")
+    monkeypatch.setattr(bench.os, "sched_getaffinity", lambda pid: {3}, raising=False)
+    assert bench.host_cores() == (16, 1, "3")
